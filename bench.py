@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Benchmark of the Lomb-Scargle NUFFT hot path on one or more GB300s.
+
+Workload (default): the large single series -- N_d = 1,000,000 times over a
+10-year baseline with seasonal gaps, N_f = 12,000,000 frequencies
+(f0 = 1/3650, df = 1/18250), FP32 spread/FFT at eps = 1e-6 (relative l2
+error <= 1e-5 against the FP64 oracle).  A step is one periodogram: every
+kernel of the path (preprocess, bin sort, pass A, pass B) over one series.
+
+Prints one JSON line (rank 0).  ``value`` = periodograms/s with the inputs
+resident in HBM (device time of K steps, CUDA events, L2 flushed between
+steps outside the timed events); ``e2e`` = the same metric through the
+C-ABI with pinned host buffers (copies in and out inside the timed region);
+``roofline`` = the dominant kernel's algorithmic bytes over its live
+event-timed duration against the measured HBM copy bandwidth;
+``cpu_baseline`` = the FP64 oracle timed on this host's cores on a bounded
+sample of the same workload.
+
+``--impl reference`` times the oracle as the reference arm (host cores only).
+Multi-GPU (torchrun): every rank computes its own periodograms (independent
+series, no collective on the data path); value = all ranks' periodograms
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("periodograms/s and p50/p99 latency at rel err <=1e-5; "
+          "spread+FFT HBM GB/s vs peak")
+UNIT = "periodograms/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default="single_large", choices=["single_large", "single_small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def workload(name: str, rank: int):
+    from paper_2409_08090_gb300 import workloads as W
+    if name == "single_small":
+        s = W.single_small(seed=W.BASE_SEED + 1000 * rank)
+        desc = "single_small: Nd=1e3 over [0,100) d, Nf=1.2e4, f0=0.01, df=0.002"
+    else:
+        s = W.single_large(seed=W.BASE_SEED + 1 + 1000 * rank)
+        desc = ("single_large: Nd=1e6 over [0,3650) d with 120-d seasonal gaps, 3 sinusoids, "
+                "lognormal dy; Nf=1.2e7, f0=1/3650, df=1/18250")
+    return s, desc
+
+
+def eps_for(precision: str) -> float:
+    return 1e-6 if precision == "fp32" else 1e-9
+
+
+# --------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_08090_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, precision: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (same digest); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(f"{kernel}:{precision}")
+    if not ent or ent.get("source_digest") != source_digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(info, nd: int, nf: int, precision: str) -> dict:
+    """Bytes each kernel must move (per launch, per periodogram)."""
+    rs = 4 if precision == "fp32" else 8
+    cx = 2 * rs
+    n = info.n
+    pts = 3 * nd * (4 + rs + cx)          # cell, offset, strength per transform
+    return {
+        "pass_a_spread_fft": 3 * n * cx + pts,          # H written once
+        "pass_b_fft_deconv_power": 3 * n * cx + 8 * nf + rs * (nf // 2 + 1),
+        "preprocess": 24 * nd + 3 * nd * (4 + rs + cx) + nd * (4 + rs + cx),
+        "bin_sort": 2 * (3 * nd * (4 + rs + cx)) // 1,
+    }
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = False
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        pg = True
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, pg, device) -> float:
+    if not pg:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(s, seconds: float, seed: int = 4242):
+    """Time the FP64 oracle on seeded random frequencies of the workload; the
+    count is scaled from a short pilot so the sample takes about `seconds`."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    pilot = 16
+    k = rng.choice(s.nf, pilot, replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    dt = time.perf_counter() - t0
+    nk = int(max(pilot, min(s.nf, pilot * seconds / max(dt, 1e-6))))
+    k = rng.choice(s.nf, nk, replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    dt = time.perf_counter() - t0
+    return nk, dt, oracle.threads()
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    s, desc = workload(args.workload, 0)
+    rng = np.random.default_rng(99)
+    # one step = the oracle on a bounded frequency sample of the same series
+    pilot = rng.choice(s.nf, 8, replace=False).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, pilot)
+    per_freq = (time.perf_counter() - t0) / 8
+    budget_s = 150.0 / max(1, args.steps + args.warmup)
+    nk = int(max(8, min(s.nf, budget_s / max(per_freq, 1e-9))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        k = rng.choice(s.nf, nk, replace=False).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    frac = nk / s.nf
+    value = args.steps * frac / sum(times)
+    cores = oracle.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "precision": "fp64 direct sums", "nd": s.nd, "nf": s.nf},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nk} seeded random frequencies of the {s.nf}-frequency "
+                                   f"grid per step (all {s.nd} points)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local, pg = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    import paper_2409_08090_gb300 as nl
+    nl.build.build()
+    nl.load_library()
+
+    s, desc = workload(args.workload, rank)
+    eps = eps_for(args.precision)
+    plan = nl.Plan(s.nd, s.nf, eps, args.precision, device=local)
+    info = plan.info
+    t = torch.tensor(s.t, dtype=torch.float64, device=device)
+    y = torch.tensor(s.y, dtype=torch.float64, device=device)
+    dy = torch.tensor(s.dy, dtype=torch.float64, device=device)
+    out = torch.empty(s.nf, dtype=torch.float64, device=device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)   # 256 MB > L2
+
+    for _ in range(args.warmup):
+        plan.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
+    st = nl.ls_sync(plan.handle)
+    if st != 0:
+        raise SystemExit(f"device status after warm-up: {nl.ls_status_str(st)}")
+
+    nl.ls_timing_enable(plan.handle, True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))                 # evict L2 (outside the step's events)
+        ev0[i].record()
+        plan.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
+        ev1[i].record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    st = nl.ls_sync(plan.handle)
+    if st != 0:
+        raise SystemExit(f"device status after timing: {nl.ls_status_str(st)}")
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    stage_ms, nexec = nl.ls_timing_report(plan.handle)
+    nl.ls_timing_enable(plan.handle, False)
+    total_ms = allreduce_max(sum(step_ms), pg, device)
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # -- dominant kernel roofline (spread + FFT passes), live event timing
+    avg = {name: stage_ms[i] / max(nexec, 1) for i, name in enumerate(nl.STAGE_NAMES)}
+    alg = algorithmic_bytes(info, s.nd, s.nf, args.precision)
+    dom = max(("pass_a_spread_fft", "pass_b_fft_deconv_power"), key=lambda k: avg[k])
+    peak, peak_kind = measured_hbm_peak()
+    kern_gbs = {k: alg[k] / (avg[k] * 1e-3) / 1e9 for k in alg if avg.get(k, 0) > 0}
+    kname = "k_passA" if dom == "pass_a_spread_fft" else "k_passB"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": kern_gbs[dom], "peak": peak,
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",
+                "frac": kern_gbs[dom] / peak,
+                "traffic": recorded_traffic(kname, args.precision),
+                "algorithmic_bytes": alg[dom], "avg_ms": avg[dom]}
+    spread_fft_ms = avg["pass_a_spread_fft"] + avg["pass_b_fft_deconv_power"]
+    spread_fft_bytes = alg["pass_a_spread_fft"] + alg["pass_b_fft_deconv_power"]
+
+    # -- end to end through the C-ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        th = torch.from_numpy(s.t).pin_memory().numpy()
+        yh = torch.from_numpy(s.y).pin_memory().numpy()
+        dyh = torch.from_numpy(s.dy).pin_memory().numpy()
+        ph = torch.empty(s.nf, dtype=torch.float64).pin_memory().numpy()
+        nsteps = max(3, min(args.steps, 10))
+        plan.execute_host(th, yh, dyh, s.f0, s.df, out=ph)
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            plan.execute_host(th, yh, dyh, s.f0, s.df, out=ph)
+        dt = allreduce_max(time.perf_counter() - t0, pg, device)
+        e2e = {"value": world * nsteps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * s.nd, "d2h_bytes_per_step": 8 * s.nf,
+               "steps": nsteps, "host_buffers": "pinned"}
+    plan.close()
+
+    # -- the plain single-series FP64 path on the same series (context)
+    fp64 = None
+    if not args.no_fp64_path and args.precision == "fp32":
+        p64 = nl.Plan(s.nd, s.nf, 1e-9, "fp64", device=local)
+        for _ in range(2):
+            p64.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
+        nl.ls_timing_enable(p64.handle, True)
+        n64 = 3
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
+        for i in range(n64):
+            flush.fill_(float(i))
+            a[i].record()
+            p64.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
+            b[i].record()
+        torch.cuda.synchronize()
+        ms64 = [x.elapsed_time(z) for x, z in zip(a, b)]
+        sm64, c64 = nl.ls_timing_report(p64.handle)
+        fp64 = {"value": n64 / (sum(ms64) * 1e-3), "unit": UNIT, "eps": 1e-9,
+                "ms_per_step": sum(ms64) / n64,
+                "stage_ms": {nm: sm64[i] / max(c64, 1) for i, nm in enumerate(nl.STAGE_NAMES)}}
+        p64.close()
+
+    if rank != 0:
+        if pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        nk, dt, cores = oracle_sample(s, args.cpu_seconds)
+        cpu = {"value": (nk / s.nf) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nk} seeded random frequencies of the {s.nf}-frequency grid, all "
+                         f"{s.nd} points, FP64 direct sums ({dt:.1f} s)"}
+
+    ms_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / len(step_ms),
+        "p50_ms": statistics.median(step_ms),
+        "p99_ms": ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "nd": s.nd, "nf": s.nf, "eps": eps,
+                   "precision": args.precision, "n": info.n, "n1": info.n1, "n2": info.n2,
+                   "width": info.width, "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": f"independent series per GPU x{world}"},
+        "roofline": roofline,
+        "spread_fft": {"ms": spread_fft_ms, "algorithmic_bytes": spread_fft_bytes,
+                       "achieved_gbs": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9,
+                       "frac_of_peak": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9 / peak},
+        "stage_ms": avg, "stage_gbs": kern_gbs,
+        "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * nifty_ls.h -- C-ABI of the GB300 Lomb-Scargle library (method of nifty-ls,
+ * Garrison, Foreman-Mackey, Shih & Barnett, arXiv 2409.08090).
+ *
+ * The library computes the floating-mean, standard-normalised Lomb-Scargle
+ * periodogram on the uniform grid f_k = f0 + k df, k = 0 .. nf-1, from the
+ * weighted trigonometric sums of Eq. 1 (Sec. 1), evaluated as type-1
+ * (nonuniform to uniform) NUFFTs (Eq. 2, Sec. 1): exponential-of-semicircle
+ * spreading onto an upsampled fine grid, an FFT of that grid and a diagonal
+ * deconvolution (Sec. 1, the finufft paragraph), with width and grid size
+ * chosen from the tolerance eps.  Three transforms are taken per series:
+ * w^(y - ybar) and w^ at f, w^ at 2f (w_j = 1/dy_j^2, w^ = w / sum w); the
+ * sums then give P_k = (YC_tau^2/CC_tau + YS_tau^2/SS_tau)/YY (generalised
+ * periodogram, standard normalisation; the paper cites VanderPlas 2018 for it).
+ *
+ * Memory: every pointer argument may be device memory or host memory (pageable
+ * or pinned); the library asks the CUDA runtime which.  Device inputs are read
+ * in place and the call returns once the work is queued on the plan's stream.
+ * Host inputs are copied into plan-owned device buffers, and a host output is
+ * copied back before the call returns (the call then synchronises the stream).
+ * All arrays are FP64, contiguous, caller-owned; the plan owns its workspace.
+ *
+ * Errors: argument errors are returned immediately.  Errors found on the
+ * device (a non-finite t/y/dy, dy <= 0, a constant series) are recorded in a
+ * per-plan status word that ls_sync() returns; an execution with host output
+ * reports them directly.  No entry point aborts, traps or prints.
+ *
+ * Threading: a plan is not thread-safe; use one plan per host thread or
+ * serialise calls.  Plans on different devices are independent.
+ */
+#ifndef NIFTY_LS_H
+#define NIFTY_LS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ls_plan_s *ls_plan_t;
+
+typedef enum {
+    LS_OK = 0,
+    LS_ERR_ARG = 1,         /* invalid argument or invalid input values          */
+    LS_ERR_NOMEM = 2,       /* device or host allocation failed                  */
+    LS_ERR_CUDA = 3,        /* a CUDA runtime call failed                        */
+    LS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                */
+    LS_ERR_DEGENERATE = 5,  /* the weighted variance of y is zero (YY == 0)      */
+    LS_ERR_UNSUPPORTED = 6  /* valid request outside what this build implements  */
+} ls_status;
+
+typedef enum { LS_NORM_STANDARD = 0 } ls_norm;
+
+/* Arithmetic of the spread, the fine-grid FFT and the deconvolution.  In both
+ * precisions the phase reduction t*df mod 1, the pre-phase exp(2 pi i fc t),
+ * the weighted mean and the final power ratio are FP64. */
+typedef enum { LS_FP64 = 0, LS_FP32 = 1 } ls_prec;
+
+/* Parameters a plan chose; filled by ls_plan_describe. */
+typedef struct {
+    int64_t nf;            /* frequencies the plan was made for               */
+    int64_t max_nd;        /* largest series it accepts                       */
+    int64_t n;             /* fine-grid size per transform (2,3,5-smooth)     */
+    int32_t n1, n2;        /* four-step split n = n1 * n2                     */
+    int32_t width;         /* kernel width w (fine-grid cells)                */
+    int32_t prec;          /* ls_prec                                         */
+    double beta;           /* ES kernel shape parameter                       */
+    double eps;            /* tolerance the plan was made for                 */
+    double sigma;          /* upsampling factor n / nf                        */
+    int64_t workspace_bytes;
+} ls_plan_info;
+
+/*
+ * ls_plan: choose the NUFFT parameters for tolerance eps and nf frequencies
+ * (Sec. 1: "width and fine grid size ... chosen to match the user tolerance"),
+ * allocate the workspace on `device` and build the twiddle and deconvolution
+ * tables.  Kernel: exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1, upsampling 2,
+ * w = ceil(log10(1/eps)) + 1 cells, beta = 2.30 w.
+ *   out      receives the plan handle (NULL on failure).
+ *   max_nd   largest number of observations a later execute may pass (>= 2).
+ *   nf       number of frequencies (>= 1); executes may use any nf' <= nf.
+ *   eps      requested relative tolerance, 1e-14 <= eps <= 1e-1; LS_FP32
+ *            needs eps >= 1e-7.
+ *   prec     ls_prec.
+ *   stream   cudaStream_t the plan launches on (NULL: the legacy default stream).
+ * Returns LS_ERR_ARG, LS_ERR_UNSUPPORTED (grid beyond the two-pass FFT's size
+ * limit), LS_ERR_NOMEM or LS_ERR_CUDA on failure.  Synchronises the device
+ * once (table construction).
+ */
+ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec,
+                  int device, void *stream);
+
+/* Replace the stream later calls launch on (NULL: legacy default stream). */
+ls_status ls_set_stream(ls_plan_t plan, void *stream);
+
+/*
+ * ls_execute: the periodogram of one series.
+ *   t, y     nd observation times and values.
+ *   dy       nd uncertainties (> 0), or NULL for unit weights.
+ *   nd       2 <= nd <= the plan's max_nd.
+ *   f0, df   grid f_k = f0 + k df; df > 0; both finite.
+ *   nf       1 <= nf <= the plan's nf.
+ *   eps      >= the plan's eps (the plan's accuracy is then sufficient).
+ *   norm     LS_NORM_STANDARD (others: LS_ERR_UNSUPPORTED).
+ *   power    nf outputs, P_k in [0, 1].
+ * The inputs are taken as exact reals: phases are reduced in double-double,
+ * so a time offset does not cost accuracy.
+ */
+ls_status ls_execute(ls_plan_t plan, const double *t, const double *y, const double *dy,
+                     int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
+                     double *power);
+
+/*
+ * ls_execute_sums: as ls_execute, and also writes the six deconvolved sums of
+ * Eq. 1 for every frequency, sums[6*k + {0..5}] = (Ch, Sh, C, S, C2, S2) with
+ * Ch + i Sh = sum_j w^_j (y_j - ybar) e^{2 pi i f_k t_j},
+ * C + i S = sum_j w^_j e^{2 pi i f_k t_j}, C2 + i S2 = sum_j w^_j e^{4 pi i f_k t_j}.
+ * `power` may be NULL.  Meant for validating the NUFFT stage.
+ */
+ls_status ls_execute_sums(ls_plan_t plan, const double *t, const double *y, const double *dy,
+                          int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
+                          double *power, double *sums);
+
+/* Wait for the plan's stream; return and clear the device-side status of every
+ * execute since the previous ls_sync (LS_ERR_ARG for invalid values,
+ * LS_ERR_DEGENERATE for a constant series, else LS_OK). */
+ls_status ls_sync(ls_plan_t plan);
+
+/*
+ * Stage timing with CUDA events recorded on the plan's stream around the
+ * pipeline's kernels (tracing for roofline measurements).
+ * ls_timing_enable(plan, 1) creates the events and starts accumulating; 0
+ * destroys them.  Every later execute records one event set (a ring of 64;
+ * an older set is drained first when the ring is full).
+ * ls_timing_report waits for the recorded sets, writes the summed device
+ * time in ms of each stage into ms[0 .. LS_NUM_STAGES-1] and the number of
+ * executes into *count, and resets the sums.  Stages, in order:
+ *   0 preprocess (weights, mean, phase reduction, point records),
+ *   1 bin sort (scan + scatter), 2 pass A (spread + column FFTs),
+ *   3 pass B (row FFTs + deconvolution + power).
+ */
+#define LS_NUM_STAGES 4
+ls_status ls_timing_enable(ls_plan_t plan, int enable);
+ls_status ls_timing_report(ls_plan_t plan, double *ms, int64_t *count);
+
+/* Fill *info with the plan's parameters. */
+ls_status ls_plan_describe(ls_plan_t plan, ls_plan_info *info);
+
+/* Release the plan and its device memory (synchronises its stream). */
+ls_status ls_destroy(ls_plan_t plan);
+
+/* Static description of a status code. */
+const char *ls_status_str(ls_status s);
+
+/*
+ * Host-only queries (no GPU needed), used to check the plan's arithmetic.
+ * ls_choose_params: the (w, beta, n, n1, n2) ls_plan would choose.
+ * ls_kernel_ft: phi_hat(k) = int phi(x) e^{i k x} dx of the ES kernel for
+ * grid size n, in grid units: (w/2) int_{-1}^{1} psi(z) cos(pi k w z / n) dz,
+ * by the same Gauss-Legendre rule the plan uses.
+ */
+ls_status ls_choose_params(int64_t nf, double eps, int prec, int32_t *width, double *beta,
+                           int64_t *n, int32_t *n1, int32_t *n2);
+double ls_kernel_ft(double k, int64_t n, int32_t width, double beta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NIFTY_LS_H */

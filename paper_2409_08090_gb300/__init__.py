@@ -1,1 +1,285 @@
-"""GB300-native nifty-ls hot path (placeholder; binding added with the CUDA library)."""
+"""GB300-native Lomb-Scargle periodograms via type-1 NUFFT (method of nifty-ls,
+arXiv 2409.08090).
+
+The compute path is the CUDA library ``libnifty_ls.so`` (``csrc/``, C-ABI in
+``include/nifty_ls.h``).  This module is a thin ctypes binding with the same
+entry-point names (``ls_plan``, ``ls_execute``, ...) plus a small convenience
+layer (``Plan``, ``lombscargle``) that marshals torch tensors or numpy arrays.
+Every step of the periodogram runs in the library's kernels; there is no CPU
+fallback: if the library is missing, calls raise ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+__all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
+           "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
+           "ls_destroy", "ls_set_stream", "ls_plan_describe", "ls_status_str",
+           "ls_choose_params", "ls_kernel_ft", "PlanInfo", "ls_timing_enable",
+           "ls_timing_report", "STAGE_NAMES"]
+
+LS_FP64, LS_FP32 = 0, 1
+LS_NORM_STANDARD = 0
+LS_OK, LS_ERR_ARG, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT, LS_ERR_DEGENERATE, \
+    LS_ERR_UNSUPPORTED = range(7)
+
+_c_void_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_dbl = ctypes.c_double
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("nf", _i64), ("max_nd", _i64), ("n", _i64), ("n1", _i32), ("n2", _i32),
+                ("width", _i32), ("prec", _i32), ("beta", _dbl), ("eps", _dbl),
+                ("sigma", _dbl), ("workspace_bytes", _i64)]
+
+
+class LSError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        msg = ls_status_str(status)
+        super().__init__(f"{where}: {msg} (status {status})" if where else msg)
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "ls_plan": (ctypes.c_int, [ctypes.POINTER(_c_void_p), _i64, _i64, _dbl, ctypes.c_int,
+                               ctypes.c_int, _c_void_p]),
+    "ls_set_stream": (ctypes.c_int, [_c_void_p, _c_void_p]),
+    "ls_execute": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _dbl, _dbl,
+                                  _i64, _dbl, ctypes.c_int, _c_void_p]),
+    "ls_execute_sums": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _dbl,
+                                       _dbl, _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
+    "ls_sync": (ctypes.c_int, [_c_void_p]),
+    "ls_plan_describe": (ctypes.c_int, [_c_void_p, ctypes.POINTER(PlanInfo)]),
+    "ls_destroy": (ctypes.c_int, [_c_void_p]),
+    "ls_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "ls_choose_params": (ctypes.c_int, [_i64, _dbl, ctypes.c_int, ctypes.POINTER(_i32),
+                                        ctypes.POINTER(_dbl), ctypes.POINTER(_i64),
+                                        ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "ls_kernel_ft": (_dbl, [_dbl, _i64, _i32, _dbl]),
+    "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
+    "ls_timing_report": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+}
+
+LS_NUM_STAGES = 4
+STAGE_NAMES = ("preprocess", "bin_sort", "pass_a_spread_fft", "pass_b_fft_deconv_power")
+
+
+def load_library(path: str | None = None):
+    """Load libnifty_ls.so (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library not built ({path} missing); run "
+                "`python -m paper_2409_08090_gb300.build` (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != LS_OK:
+        raise LSError(status, where)
+
+
+# ---- raw C-ABI mirrors (same names, plain integers/pointers) ----------------
+
+def ls_status_str(status: int) -> str:
+    return load_library().ls_status_str(int(status)).decode()
+
+
+def ls_plan(max_nd: int, nf: int, eps: float, prec: int = LS_FP64, device: int = 0,
+            stream: int = 0) -> int:
+    h = _c_void_p()
+    _check(load_library().ls_plan(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
+                                  int(device), _c_void_p(stream or None)), "ls_plan")
+    return h.value
+
+
+def ls_set_stream(plan: int, stream: int) -> None:
+    _check(load_library().ls_set_stream(_c_void_p(plan), _c_void_p(stream or None)),
+           "ls_set_stream")
+
+
+def ls_execute(plan: int, t: int, y: int, dy: int | None, nd: int, f0: float, df: float,
+               nf: int, eps: float, norm: int, power: int) -> int:
+    return load_library().ls_execute(_c_void_p(plan), _c_void_p(t), _c_void_p(y),
+                                     _c_void_p(dy or None), int(nd), float(f0), float(df),
+                                     int(nf), float(eps), int(norm), _c_void_p(power))
+
+
+def ls_execute_sums(plan: int, t: int, y: int, dy: int | None, nd: int, f0: float, df: float,
+                    nf: int, eps: float, norm: int, power: int | None, sums: int) -> int:
+    return load_library().ls_execute_sums(_c_void_p(plan), _c_void_p(t), _c_void_p(y),
+                                          _c_void_p(dy or None), int(nd), float(f0), float(df),
+                                          int(nf), float(eps), int(norm),
+                                          _c_void_p(power or None), _c_void_p(sums))
+
+
+def ls_sync(plan: int) -> int:
+    return load_library().ls_sync(_c_void_p(plan))
+
+
+def ls_destroy(plan: int) -> int:
+    return load_library().ls_destroy(_c_void_p(plan))
+
+
+def ls_plan_describe(plan: int) -> PlanInfo:
+    info = PlanInfo()
+    _check(load_library().ls_plan_describe(_c_void_p(plan), ctypes.byref(info)),
+           "ls_plan_describe")
+    return info
+
+
+def ls_choose_params(nf: int, eps: float, prec: int = LS_FP64) -> dict:
+    w, b, n, n1, n2 = _i32(), _dbl(), _i64(), _i32(), _i32()
+    _check(load_library().ls_choose_params(int(nf), float(eps), int(prec), ctypes.byref(w),
+                                           ctypes.byref(b), ctypes.byref(n), ctypes.byref(n1),
+                                           ctypes.byref(n2)), "ls_choose_params")
+    return {"width": w.value, "beta": b.value, "n": n.value, "n1": n1.value, "n2": n2.value}
+
+
+def ls_timing_enable(plan: int, enable: bool = True) -> None:
+    _check(load_library().ls_timing_enable(_c_void_p(plan), int(bool(enable))),
+           "ls_timing_enable")
+
+
+def ls_timing_report(plan: int) -> tuple[list, int]:
+    """Summed device ms per stage (STAGE_NAMES) and the number of executes."""
+    ms = (_dbl * LS_NUM_STAGES)()
+    cnt = _i64()
+    _check(load_library().ls_timing_report(_c_void_p(plan), ms, ctypes.byref(cnt)),
+           "ls_timing_report")
+    return list(ms), cnt.value
+
+
+def ls_kernel_ft(k: float, n: int, width: int, beta: float) -> float:
+    return float(load_library().ls_kernel_ft(float(k), int(n), int(width), float(beta)))
+
+
+# ---- convenience layer ---------------------------------------------------------
+
+def _prec_code(precision) -> int:
+    if precision in (LS_FP64, "fp64", "float64", "f64", "double"):
+        return LS_FP64
+    if precision in (LS_FP32, "fp32", "float32", "f32", "single"):
+        return LS_FP32
+    raise ValueError(f"unknown precision {precision!r}")
+
+
+class Plan:
+    """Owns one ``ls_plan`` (workspace + tables for ``nf`` frequencies at ``eps``)."""
+
+    def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
+                 device: int = 0):
+        self.prec = _prec_code(precision)
+        self.device = int(device)
+        self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0)
+        self.info = ls_plan_describe(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ls_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self) -> int:
+        import torch
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def execute(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
+                out=None, sums=None, sync: bool = True):
+        """Periodogram of one series.  ``t, y, dy`` are float64 CUDA tensors on the
+        plan's device (``dy`` may be None); returns ``out`` (float64, nf)."""
+        import torch
+        nf = int(self.info.nf if nf is None else nf)
+        eps = float(self.info.eps if eps is None else eps)
+        for a in (t, y) + ((dy,) if dy is not None else ()):
+            if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+                raise ValueError("t, y, dy must be contiguous float64 CUDA tensors")
+        if out is None:
+            out = torch.empty(nf, dtype=torch.float64, device=t.device)
+        ls_set_stream(self.handle, self._stream())
+        nd = int(t.numel())
+        dyp = dy.data_ptr() if dy is not None else None
+        if sums is not None:
+            st = ls_execute_sums(self.handle, t.data_ptr(), y.data_ptr(), dyp, nd, f0, df, nf,
+                                 eps, LS_NORM_STANDARD, out.data_ptr(), sums.data_ptr())
+        else:
+            st = ls_execute(self.handle, t.data_ptr(), y.data_ptr(), dyp, nd, f0, df, nf, eps,
+                            LS_NORM_STANDARD, out.data_ptr())
+        _check(st, "ls_execute")
+        if sync:
+            _check(ls_sync(self.handle), "ls_execute (device status)")
+        return out
+
+    def execute_host(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
+                     out=None):
+        """Same, with host (numpy float64) buffers: the library copies in and out."""
+        import numpy as np
+        nf = int(self.info.nf if nf is None else nf)
+        eps = float(self.info.eps if eps is None else eps)
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        dyp = None
+        if dy is not None:
+            dy = np.ascontiguousarray(dy, dtype=np.float64)
+            dyp = dy.ctypes.data
+        if out is None:
+            out = np.empty(nf, dtype=np.float64)
+        ls_set_stream(self.handle, self._stream())
+        st = ls_execute(self.handle, t.ctypes.data, y.ctypes.data, dyp, t.shape[0], f0, df, nf,
+                        eps, LS_NORM_STANDARD, out.ctypes.data)
+        _check(st, "ls_execute")
+        return out
+
+
+_plan_cache: dict = {}
+
+
+def lombscargle(t, y, dy=None, *, f0: float, df: float, nf: int, eps: float = 1e-9,
+                precision="fp64", device: int = 0):
+    """Floating-mean, standard-normalised Lomb-Scargle power at f0 + k df, k < nf.
+
+    Accepts float64 CUDA tensors (result: CUDA tensor) or array-likes (result:
+    numpy array, host buffers copied by the library).  Plans are cached per
+    (device, nf, eps, precision) and grown when a longer series arrives.
+    """
+    prec = _prec_code(precision)
+    try:
+        import torch
+        is_tensor = isinstance(t, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_tensor = False
+    nd = int(t.numel() if is_tensor else len(t))
+    key = (device, int(nf), float(eps), prec)
+    plan = _plan_cache.get(key)
+    if plan is None or plan.info.max_nd < nd:
+        if plan is not None:
+            plan.close()
+        plan = Plan(max(nd, 2), nf, eps, prec, device)
+        _plan_cache[key] = plan
+    if is_tensor:
+        return plan.execute(t, y, dy, f0, df, nf, eps)
+    return plan.execute_host(t, y, dy, f0, df, nf, eps)

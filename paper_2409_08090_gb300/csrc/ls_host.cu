@@ -1,0 +1,692 @@
+// Host side of the Lomb-Scargle NUFFT library: plan construction (parameter
+// choice from the tolerance, fine-grid size, four-step split, tables),
+// workspace ownership and the C-ABI entry points declared in nifty_ls.h.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "ls_internal.cuh"
+
+using namespace nls;
+
+struct ls_plan_s {
+    int device;
+    cudaStream_t stream;
+    int prec;
+    int64_t max_nd;
+    int64_t nf;
+    double eps;
+    Geometry g;
+    Workspace ws;
+    int nred;
+    int64_t deconv_count;
+    std::vector<void *> allocations;
+    int64_t bytes;
+    // staging for host-memory arguments (allocated on first use)
+    double *stage_in;     // 3 * max_nd
+    double *stage_out;    // nf
+    double *stage_sums;   // 6 * nf
+    // stage timing (ls_timing_enable)
+    bool timing;
+    std::vector<cudaEvent_t> tev;   // kTimingRing * (LS_NUM_STAGES + 1)
+    int t_head, t_pending;
+    double t_acc[LS_NUM_STAGES];
+    int64_t t_count;
+};
+
+namespace {
+
+constexpr int kTimingRing = 64;
+constexpr int kEvPerSet = LS_NUM_STAGES + 1;
+
+constexpr int kN1MaxF32 = 4608, kN2MaxF32 = 25600;
+constexpr int kN1MaxF64 = 2400, kN2MaxF64 = 12800;
+constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool factor_radices(int L, Radices *r)
+{
+    r->L = L;
+    r->count = 0;
+    int x = L;
+    auto push = [&](int R) {
+        if (r->count >= kMaxRadices) return false;
+        r->rad[r->count++] = R;
+        x /= R;
+        return true;
+    };
+    while (x % 8 == 0) if (!push(8)) return false;
+    while (x % 4 == 0) if (!push(4)) return false;
+    while (x % 2 == 0) if (!push(2)) return false;
+    while (x % 5 == 0) if (!push(5)) return false;
+    while (x % 3 == 0) if (!push(3)) return false;
+    return x == 1;
+}
+
+bool smooth235(int64_t x)
+{
+    if (x < 1) return false;
+    for (int p : {2, 3, 5})
+        while (x % p == 0) x /= p;
+    return x == 1;
+}
+
+// ES kernel width and shape for tolerance eps (upsampling factor 2): the
+// error of the ES kernel falls roughly tenfold per extra cell of width.
+void es_params(double eps, int *w, double *beta)
+{
+    int ww = (int)ceil(log10(1.0 / eps) - 1e-9) + 1;
+    if (ww < 2) ww = 2;
+    if (ww > 16) ww = 16;
+    double bo = 2.30;
+    if (ww == 2) bo = 2.20;
+    else if (ww == 3) bo = 2.26;
+    else if (ww == 4) bo = 2.38;
+    *w = ww;
+    *beta = bo * ww;
+}
+
+// Fine grid: the smallest 2,3,5-smooth n >= max(2 nf, 2 w) that splits as
+// n = N1 * N2 within the shared-memory limits of the two passes; N1 is the
+// largest admissible divisor not above sqrt(n).
+ls_status choose_grid(int64_t nf, int w, int prec, int64_t *n_out, int *n1_out, int *n2_out)
+{
+    const int n1max = prec == LS_FP32 ? kN1MaxF32 : kN1MaxF64;
+    const int n2max = prec == LS_FP32 ? kN2MaxF32 : kN2MaxF64;
+    int64_t n = 2 * nf;
+    if (n < 2 * w) n = 2 * w;
+    if (n < 16) n = 16;
+    const int64_t nlimit = (int64_t)n1max * n2max;
+    for (; n <= nlimit; ++n) {
+        if (!smooth235(n)) continue;
+        const int64_t root = (int64_t)floor(sqrt((double)n));
+        int best = -1;
+        // largest divisor <= min(n1max, sqrt n) with cofactor <= n2max
+        for (int64_t d = root < n1max ? root : n1max; d >= 1; --d) {
+            if (n % d) continue;
+            if (n / d > n2max) break;
+            best = (int)d;
+            break;
+        }
+        if (best < 0) {
+            // cofactor too large: the smallest divisor above sqrt(n) within limits
+            for (int64_t d = root + 1; d <= n1max; ++d) {
+                if (n % d) continue;
+                if (n / d <= n2max) { best = (int)d; break; }
+            }
+        }
+        if (best < 0) continue;
+        Radices r1, r2;
+        if (!factor_radices(best, &r1) || !factor_radices((int)(n / best), &r2)) continue;
+        *n_out = n;
+        *n1_out = best;
+        *n2_out = (int)(n / best);
+        return LS_OK;
+    }
+    return LS_ERR_UNSUPPORTED;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_q).
+void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt)
+{
+    x.assign(q, 0.0);
+    wt.assign(q, 0.0);
+    for (int i = 0; i < q; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (q + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= q; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= q; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = q * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int quad_nodes(int w) { return 2 * w + 24; }
+
+// Nodes on [0, 1] (the even integrand is folded) and weights times psi(z).
+// The substitution z = sin(theta) removes the square-root endpoint behaviour of
+// psi at z = 1 (sqrt(1 - z^2) = cos theta, dz = cos theta dtheta), so the
+// Gauss-Legendre rule on theta in [0, pi/2] converges geometrically.
+void es_quadrature(int w, double beta, std::vector<double> &z, std::vector<double> &wpsi)
+{
+    const int q = quad_nodes(w);
+    std::vector<double> x, wt;
+    gauss_legendre(q, x, wt);
+    z.resize(q);
+    wpsi.resize(q);
+    for (int i = 0; i < q; ++i) {
+        const double th = 0.25 * M_PI * (x[i] + 1.0);
+        const double c = cos(th);
+        z[i] = sin(th);
+        wpsi[i] = 0.25 * M_PI * wt[i] * c * exp(beta * (c - 1.0));
+    }
+}
+
+// exp(2 pi i p / L) for p in [0, L), from an exact integer reduction.
+void root_of_unity(int64_t p, int64_t L, double *re, double *im)
+{
+    p %= L;
+    const double a = 2.0 * M_PI * ((double)p / (double)L);
+    *re = cos(a);
+    *im = sin(a);
+}
+
+template <typename T>
+void fill_root_table(std::vector<T> &out, int64_t L, int split_bits)
+{
+    const int64_t lo = (int64_t)1 << split_bits;
+    const int64_t hi = (L + lo - 1) / lo;
+    out.resize(2 * (lo + hi));
+    for (int64_t i = 0; i < lo; ++i) {
+        double re, im;
+        root_of_unity(i, L, &re, &im);
+        out[2 * i] = (T)re;
+        out[2 * i + 1] = (T)im;
+    }
+    for (int64_t i = 0; i < hi; ++i) {
+        double re, im;
+        root_of_unity((i * lo) % L, L, &re, &im);
+        out[2 * (lo + i)] = (T)re;
+        out[2 * (lo + i) + 1] = (T)im;
+    }
+}
+
+ls_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return LS_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return LS_ERR_NOMEM;
+    }
+    return LS_ERR_CUDA;
+}
+
+ls_status plan_alloc(ls_plan_s *p, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return cuda_status(e);
+    }
+    p->allocations.push_back(*ptr);
+    p->bytes += (int64_t)bytes;
+    return LS_OK;
+}
+
+void plan_free(ls_plan_s *p)
+{
+    for (void *a : p->allocations) cudaFree(a);
+    p->allocations.clear();
+}
+
+template <typename T>
+ls_status upload_tables(ls_plan_s *p)
+{
+    const Geometry &g = p->g;
+    std::vector<T> tA, tB, t4;
+    fill_root_table(tA, g.N2, 6);
+    fill_root_table(tB, g.N1, 6);
+    fill_root_table(t4, g.n, kTw4Bits);
+    ls_status s;
+    if ((s = plan_alloc(p, &p->ws.twA, tA.size() * sizeof(T))) != LS_OK) return s;
+    if ((s = plan_alloc(p, &p->ws.twB, tB.size() * sizeof(T))) != LS_OK) return s;
+    if ((s = plan_alloc(p, &p->ws.tw4, t4.size() * sizeof(T))) != LS_OK) return s;
+    cudaError_t e;
+    if ((e = cudaMemcpy(p->ws.twA, tA.data(), tA.size() * sizeof(T), cudaMemcpyHostToDevice)))
+        return cuda_status(e);
+    if ((e = cudaMemcpy(p->ws.twB, tB.data(), tB.size() * sizeof(T), cudaMemcpyHostToDevice)))
+        return cuda_status(e);
+    if ((e = cudaMemcpy(p->ws.tw4, t4.data(), t4.size() * sizeof(T), cudaMemcpyHostToDevice)))
+        return cuda_status(e);
+
+    // deconvolution table 1/phi_hat(k'), k' = 0 .. nf/2
+    p->deconv_count = p->nf / 2 + 1;
+    if ((s = plan_alloc(p, &p->ws.deconv, (size_t)p->deconv_count * sizeof(T))) != LS_OK) return s;
+    std::vector<double> z, wpsi;
+    es_quadrature(g.w, g.beta, z, wpsi);
+    void *dq = nullptr;
+    if ((e = cudaMalloc(&dq, 2 * z.size() * sizeof(double)))) return cuda_status(e);
+    double *dz = static_cast<double *>(dq), *dw = dz + z.size();
+    cudaMemcpy(dz, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(dw, wpsi.data(), wpsi.size() * sizeof(double), cudaMemcpyHostToDevice);
+    e = launch_deconv_table<T>(g, p->ws.deconv, p->deconv_count, dz, dw, (int)z.size(), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(dq);
+    return cuda_status(e);
+}
+
+template <typename T>
+ls_status plan_workspace(ls_plan_s *p)
+{
+    const Geometry &g = p->g;
+    const size_t cx = sizeof(typename Cx<T>::type);
+    ls_status s;
+    if ((s = plan_alloc(p, &p->ws.H, 3 * (size_t)g.n * cx)) != LS_OK) return s;
+    const size_t rec = (point_record_bytes<T>() + 64) * (size_t)p->max_nd + 4096;
+    for (int i = 0; i < 2; ++i) {
+        if ((s = plan_alloc(p, &p->ws.pts_raw[i], rec)) != LS_OK) return s;
+        if ((s = plan_alloc(p, &p->ws.pts_sorted[i], rec)) != LS_OK) return s;
+    }
+    void *v;
+    if ((s = plan_alloc(p, &v, sizeof(int) * 2 * (size_t)g.nbins)) != LS_OK) return s;
+    p->ws.hist = static_cast<int *>(v);
+    if ((s = plan_alloc(p, &v, sizeof(int) * 2 * ((size_t)g.nbins + 1))) != LS_OK) return s;
+    p->ws.binstart = static_cast<int *>(v);
+    if ((s = plan_alloc(p, &v, sizeof(int) * 2 * (size_t)g.nbins)) != LS_OK) return s;
+    p->ws.cursor = static_cast<int *>(v);
+    if ((s = plan_alloc(p, &v, sizeof(double) * 2 * (size_t)p->nred)) != LS_OK) return s;
+    p->ws.partials = static_cast<double *>(v);
+    if ((s = plan_alloc(p, &v, 256)) != LS_OK) return s;
+    p->ws.counter = static_cast<unsigned int *>(v);
+    p->ws.status = reinterpret_cast<int *>(static_cast<char *>(v) + 64);
+    if ((s = plan_alloc(p, &v, sizeof(Stats))) != LS_OK) return s;
+    p->ws.stats = static_cast<Stats *>(v);
+    cudaError_t e = cudaMemset(p->ws.counter, 0, 256);
+    if (e != cudaSuccess) return cuda_status(e);
+    return upload_tables<T>(p);
+}
+
+bool is_device_pointer(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ls_status ensure_staging(ls_plan_s *p, double **buf, size_t count)
+{
+    if (*buf) return LS_OK;
+    void *v;
+    ls_status s = plan_alloc(p, &v, count * sizeof(double));
+    if (s == LS_OK) *buf = static_cast<double *>(v);
+    return s;
+}
+
+// fc = f0 + K0 df as a double-double (two-product and two-sum).
+void centre_frequency(double f0, double df, int64_t K0, double *hi, double *lo)
+{
+    const double k = (double)K0;
+    const double ph = k * df;
+    const double pl = fma(k, df, -ph);
+    const double s = f0 + ph;
+    const double bb = s - f0;
+    const double e = (f0 - (s - bb)) + (ph - bb);
+    const double l = e + pl;
+    *hi = s + l;
+    *lo = l - (*hi - s);
+}
+
+// Accumulate the oldest pending event set (waits for it).
+cudaError_t drain_one_timing(ls_plan_s *p)
+{
+    const int idx = (p->t_head - p->t_pending + kTimingRing) % kTimingRing;
+    cudaEvent_t *ev = p->tev.data() + (size_t)idx * kEvPerSet;
+    cudaError_t e = cudaEventSynchronize(ev[kEvPerSet - 1]);
+    if (e != cudaSuccess) return e;
+    for (int s = 0; s < LS_NUM_STAGES; ++s) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+        if (e != cudaSuccess) return e;
+        p->t_acc[s] += ms;
+    }
+    p->t_count += 1;
+    p->t_pending -= 1;
+    return cudaSuccess;
+}
+
+void destroy_timing(ls_plan_s *p)
+{
+    for (cudaEvent_t e : p->tev) cudaEventDestroy(e);
+    p->tev.clear();
+    p->timing = false;
+    p->t_pending = 0;
+}
+
+ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const double *dy,
+                       int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
+                       double *power, double *sums)
+{
+    if (!p) return LS_ERR_ARG;
+    if (!t || !y || (!power && !sums)) return LS_ERR_ARG;
+    if (nd < 2 || nd > p->max_nd) return LS_ERR_ARG;
+    if (nf < 1 || nf > p->nf) return LS_ERR_ARG;
+    if (!(df > 0.0) || !isfinite(df) || !isfinite(f0)) return LS_ERR_ARG;
+    if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
+    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    cudaStream_t st = p->stream;
+    cudaError_t e;
+    ls_status s;
+
+    const double *in[3] = {t, y, dy};
+    const double *dev_in[3] = {t, y, dy};
+    for (int i = 0; i < 3; ++i) {
+        if (!in[i] || is_device_pointer(in[i])) continue;
+        if ((s = ensure_staging(p, &p->stage_in, 3 * (size_t)p->max_nd)) != LS_OK) return s;
+        double *dst = p->stage_in + (size_t)i * p->max_nd;
+        e = cudaMemcpyAsync(dst, in[i], sizeof(double) * (size_t)nd, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e);
+        dev_in[i] = dst;
+    }
+    const bool host_power = power && !is_device_pointer(power);
+    const bool host_sums = sums && !is_device_pointer(sums);
+    double *dpow = power, *dsums = sums;
+    if (host_power) {
+        if ((s = ensure_staging(p, &p->stage_out, (size_t)p->nf)) != LS_OK) return s;
+        dpow = p->stage_out;
+    }
+    if (host_sums) {
+        if ((s = ensure_staging(p, &p->stage_sums, 6 * (size_t)p->nf)) != LS_OK) return s;
+        dsums = p->stage_sums;
+    }
+
+    ExecParams ep;
+    ep.t = dev_in[0];
+    ep.y = dev_in[1];
+    ep.dy = dev_in[2];
+    ep.nd = nd;
+    ep.df = df;
+    ep.nf = nf;
+    ep.K0 = nf / 2;
+    centre_frequency(f0, df, ep.K0, &ep.fc_hi, &ep.fc_lo);
+    ep.power = dpow;
+    ep.sums = dsums;
+    int nred = (int)((nd + 255) / 256);
+    if (nred > p->nred) nred = p->nred;
+    cudaEvent_t *ev = nullptr;
+    if (p->timing) {
+        if (p->t_pending == kTimingRing) {
+            e = drain_one_timing(p);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        ev = p->tev.data() + (size_t)p->t_head * kEvPerSet;
+        p->t_head = (p->t_head + 1) % kTimingRing;
+        p->t_pending += 1;
+    }
+    e = (p->prec == LS_FP32) ? launch_pipeline<float>(p->g, p->ws, p->max_nd, ep, nred, st, ev)
+                             : launch_pipeline<double>(p->g, p->ws, p->max_nd, ep, nred, st, ev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (host_power || host_sums) {
+        if (host_power) {
+            e = cudaMemcpyAsync(power, dpow, sizeof(double) * (size_t)nf, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        if (host_sums) {
+            e = cudaMemcpyAsync(sums, dsums, 6 * sizeof(double) * (size_t)nf,
+                                cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return ls_sync(p);
+    }
+    return LS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ls_status_str(ls_status s)
+{
+    switch (s) {
+    case LS_OK: return "ok";
+    case LS_ERR_ARG: return "invalid argument or input values";
+    case LS_ERR_NOMEM: return "out of memory";
+    case LS_ERR_CUDA: return "CUDA runtime error";
+    case LS_ERR_TIMEOUT: return "device-side wait timed out";
+    case LS_ERR_DEGENERATE: return "degenerate input: the weighted variance of y is zero";
+    case LS_ERR_UNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+ls_status ls_choose_params(int64_t nf, double eps, int prec, int32_t *width, double *beta,
+                           int64_t *n, int32_t *n1, int32_t *n2)
+{
+    if (nf < 1 || !(eps >= 1e-14 && eps <= 1e-1)) return LS_ERR_ARG;
+    if (prec != LS_FP32 && prec != LS_FP64) return LS_ERR_ARG;
+    if (prec == LS_FP32 && eps < 1e-7) return LS_ERR_ARG;
+    int w;
+    double b;
+    es_params(eps, &w, &b);
+    int64_t nn;
+    int a1, a2;
+    ls_status s = choose_grid(nf, w, prec, &nn, &a1, &a2);
+    if (s != LS_OK) return s;
+    if (width) *width = w;
+    if (beta) *beta = b;
+    if (n) *n = nn;
+    if (n1) *n1 = a1;
+    if (n2) *n2 = a2;
+    return LS_OK;
+}
+
+double ls_kernel_ft(double k, int64_t n, int32_t width, double beta)
+{
+    std::vector<double> z, wpsi;
+    es_quadrature(width, beta, z, wpsi);
+    double s = 0.0;
+    for (size_t i = 0; i < z.size(); ++i) s += wpsi[i] * cos(M_PI * k * width * z[i] / (double)n);
+    return width * s;
+}
+
+ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec, int device,
+                  void *stream)
+{
+    if (!out) return LS_ERR_ARG;
+    *out = nullptr;
+    if (max_nd < 2 || max_nd > ((int64_t)1 << 30)) return LS_ERR_ARG;
+    int w;
+    double beta;
+    int64_t n;
+    int n1, n2;
+    ls_status s = ls_choose_params(nf, eps, prec, &w, &beta, &n, &n1, &n2);
+    if (s != LS_OK) return s;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? LS_ERR_ARG : LS_ERR_CUDA;
+    }
+    DeviceGuard guard(device);
+    if (!guard.ok) return LS_ERR_CUDA;
+
+    ls_plan_s *p = new (std::nothrow) ls_plan_s();
+    if (!p) return LS_ERR_NOMEM;
+    p->device = device;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->prec = prec;
+    p->max_nd = max_nd;
+    p->nf = nf;
+    p->eps = eps;
+    p->bytes = 0;
+    p->stage_in = p->stage_out = p->stage_sums = nullptr;
+    p->timing = false;
+    p->t_head = p->t_pending = 0;
+    for (double &a : p->t_acc) a = 0.0;
+    p->t_count = 0;
+    Geometry &g = p->g;
+    g.n = n;
+    g.N1 = n1;
+    g.N2 = n2;
+    g.w = w;
+    g.beta = beta;
+    factor_radices(n2, &g.radA);
+    factor_radices(n1, &g.radB);
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    int BA = 1;
+    for (int cand : {8, 4, 2}) {
+        if (n1 % cand == 0 && (size_t)cand * n2 * cx <= kSmemPairBudget && n1 / cand >= 2) {
+            BA = cand;
+            break;
+        }
+    }
+    g.BA = BA;
+    g.nbins = n1 / BA;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    if (nsm <= 0) nsm = 152;
+    p->nred = 8 * nsm;
+    s = (prec == LS_FP32) ? plan_workspace<float>(p) : plan_workspace<double>(p);
+    if (s != LS_OK) {
+        plan_free(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return LS_OK;
+}
+
+ls_status ls_set_stream(ls_plan_t p, void *stream)
+{
+    if (!p) return LS_ERR_ARG;
+    p->stream = static_cast<cudaStream_t>(stream);
+    return LS_OK;
+}
+
+ls_status ls_execute(ls_plan_t p, const double *t, const double *y, const double *dy, int64_t nd,
+                     double f0, double df, int64_t nf, double eps, int norm, double *power)
+{
+    if (!power) return LS_ERR_ARG;
+    return execute_impl(p, t, y, dy, nd, f0, df, nf, eps, norm, power, nullptr);
+}
+
+ls_status ls_execute_sums(ls_plan_t p, const double *t, const double *y, const double *dy,
+                          int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
+                          double *power, double *sums)
+{
+    if (!sums) return LS_ERR_ARG;
+    return execute_impl(p, t, y, dy, nd, f0, df, nf, eps, norm, power, sums);
+}
+
+ls_status ls_sync(ls_plan_t p)
+{
+    if (!p) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    e = cudaMemcpy(&h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (h) {
+        e = cudaMemset(p->ws.status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (h & kStatBadInput) return LS_ERR_ARG;
+    if (h & kStatDegenerate) return LS_ERR_DEGENERATE;
+    return LS_OK;
+}
+
+ls_status ls_plan_describe(ls_plan_t p, ls_plan_info *info)
+{
+    if (!p || !info) return LS_ERR_ARG;
+    info->nf = p->nf;
+    info->max_nd = p->max_nd;
+    info->n = p->g.n;
+    info->n1 = p->g.N1;
+    info->n2 = p->g.N2;
+    info->width = p->g.w;
+    info->prec = p->prec;
+    info->beta = p->g.beta;
+    info->eps = p->eps;
+    info->sigma = (double)p->g.n / (double)p->nf;
+    info->workspace_bytes = p->bytes;
+    return LS_OK;
+}
+
+ls_status ls_timing_enable(ls_plan_t p, int enable)
+{
+    if (!p) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (!enable) {
+        destroy_timing(p);
+        return LS_OK;
+    }
+    if (p->timing) return LS_OK;
+    p->tev.assign((size_t)kTimingRing * kEvPerSet, nullptr);
+    for (auto &e : p->tev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            destroy_timing(p);
+            return LS_ERR_CUDA;
+        }
+    }
+    p->timing = true;
+    p->t_head = p->t_pending = 0;
+    for (double &a : p->t_acc) a = 0.0;
+    p->t_count = 0;
+    return LS_OK;
+}
+
+ls_status ls_timing_report(ls_plan_t p, double *ms, int64_t *count)
+{
+    if (!p || !ms) return LS_ERR_ARG;
+    if (!p->timing) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    while (p->t_pending > 0) {
+        cudaError_t e = drain_one_timing(p);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    for (int s = 0; s < LS_NUM_STAGES; ++s) {
+        ms[s] = p->t_acc[s];
+        p->t_acc[s] = 0.0;
+    }
+    if (count) *count = p->t_count;
+    p->t_count = 0;
+    return LS_OK;
+}
+
+ls_status ls_destroy(ls_plan_t p)
+{
+    if (!p) return LS_ERR_ARG;
+    {
+        DeviceGuard guard(p->device);
+        cudaStreamSynchronize(p->stream);
+        destroy_timing(p);
+        plan_free(p);
+    }
+    delete p;
+    return LS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the host code and the kernels of the
+// Lomb-Scargle NUFFT library (method of arXiv 2409.08090, Sec. 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nifty_ls.h"
+
+namespace nls {
+
+constexpr int kMaxRadices = 24;   // stages of one sub-FFT
+constexpr int kTwSplit = 64;      // two-level root table: W^p = lo[p % 64] * hi[p / 64]
+constexpr int kTw4Bits = 12;      // four-step twiddle table split: 4096
+constexpr int kThreadsA = 512;
+constexpr int kThreadsB = 512;
+
+// Device status word bits (sticky until ls_sync).
+constexpr int kStatBadInput = 1;
+constexpr int kStatDegenerate = 2;
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using type = float2; };
+template <> struct Cx<double> { using type = double2; };
+
+// Radix schedule of one sub-FFT length L = prod(rad[s]).
+struct Radices {
+    int L;
+    int count;
+    int rad[kMaxRadices];
+};
+
+// The fine grid and its four-step split: n = N1 * N2, cell m = a + N1 * b.
+// Pass A takes length-N2 transforms over b (one per column a), pass B
+// length-N1 transforms over a (one per row d).
+struct Geometry {
+    int64_t n;
+    int N1, N2;
+    int BA;        // columns per pass-A block
+    int nbins;     // N1 / BA
+    int w;
+    double beta;
+    Radices radA;  // length N2
+    Radices radB;  // length N1
+};
+
+// Point records: one set per spread geometry (x and 2x).  `cell` is the first
+// fine-grid cell the kernel touches (in [0, n)), `roff` the offset such that the
+// kernel argument of cell cell+i is z = (roff - w/2 + i) * 2/w.
+template <typename T> struct PointSet {
+    int *cell;
+    T *roff;
+    typename Cx<T>::type *s[2];   // strengths (geometry x: s1, s2; geometry 2x: s3)
+};
+
+struct Stats {            // FP64 reductions, in device memory
+    double W;             // sum of w_j
+    double WY;            // sum of w_j y_j
+    double ybar;          // weighted mean
+    double YY;            // sum of w^_j (y_j - ybar)^2
+    double Y2;            // sum of w^_j y_j^2 (scale for the degeneracy test)
+    double pad[3];
+};
+
+struct Workspace {
+    void *H;              // 3 grids of n complex T, layout [grid][d][a]
+    void *pts_raw[2];     // unsorted point records (two geometries), see PointSet
+    void *pts_sorted[2];
+    int *hist;            // 2 * nbins counts
+    int *binstart;        // 2 * (nbins + 1)
+    int *cursor;          // 2 * nbins
+    double *partials;     // reduction partials
+    unsigned int *counter;// last-block tickets (2)
+    Stats *stats;
+    int *status;          // device status word
+    void *twA;            // root tables for N2: lo (64) then hi (ceil(N2/64))
+    void *twB;            // root tables for N1
+    void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
+    void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
+};
+
+// Launch the whole single-series pipeline (defined in ls_kernels.cu).
+struct ExecParams {
+    const double *t, *y, *dy;
+    int64_t nd;
+    double df;
+    double fc_hi, fc_lo;  // centre frequency f0 + K0 df as a double-double
+    int64_t nf, K0;
+    double *power;        // may be null
+    double *sums;         // may be null
+};
+
+// `ev`, if not null, holds LS_NUM_STAGES + 1 events recorded at the stage
+// boundaries.
+template <typename T>
+cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_nd,
+                            const ExecParams &p, int nred_blocks, cudaStream_t st,
+                            cudaEvent_t *ev);
+
+template <typename T>
+cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
+                                const double *gl_z, const double *gl_wpsi, int q,
+                                cudaStream_t st);
+
+template <typename T>
+size_t point_record_bytes();
+
+size_t passA_smem_bytes(const Geometry &g, size_t cx_bytes);
+size_t passB_smem_bytes(const Geometry &g, size_t cx_bytes);
+
+}  // namespace nls

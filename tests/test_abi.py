@@ -1,0 +1,86 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/nifty_ls.h; host-only queries return the parameters the
+plan math promises."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nifty_ls.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_08090_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(ls_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ls_plan", "ls_execute", "ls_destroy", "ls_sync", "ls_status_str"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    import paper_2409_08090_gb300 as nl
+    assert nl.ls_status_str(0) == "ok"
+    assert "degenerate" in nl.ls_status_str(5)
+    assert nl.ls_status_str(99) == "unknown status"
+
+
+@pytest.mark.parametrize("nf,eps,prec,w,n", [
+    (12_000, 1e-12, 0, 13, 24_000),
+    (12_000, 1e-9, 0, 10, 24_000),
+    (12_000, 1e-6, 1, 7, 24_000),
+    (12_000_000, 1e-6, 1, 7, 24_000_000),
+    (12_000_000, 1e-9, 0, 10, 24_000_000),
+    (120_000, 1e-6, 1, 7, 240_000),
+])
+def test_choose_params(nf, eps, prec, w, n):
+    import paper_2409_08090_gb300 as nl
+    p = nl.ls_choose_params(nf, eps, prec)
+    assert p["width"] == w
+    assert p["n"] == n
+    assert p["n1"] * p["n2"] == p["n"]
+    assert abs(p["beta"] - 2.30 * w) < 1e-12
+    # split limits of the two passes
+    assert p["n1"] <= (4608 if prec == 1 else 2400)
+    assert p["n2"] <= (25600 if prec == 1 else 12800)
+
+
+def test_choose_params_rejects():
+    import paper_2409_08090_gb300 as nl
+    with pytest.raises(nl.LSError):
+        nl.ls_choose_params(0, 1e-6, 0)
+    with pytest.raises(nl.LSError):
+        nl.ls_choose_params(100, 1e-9, 1)   # FP32 cannot reach 1e-9
+    with pytest.raises(nl.LSError):
+        nl.ls_choose_params(100, 0.5, 0)
+
+
+def test_grid_sizes_are_smooth_and_cover_oversampling():
+    import paper_2409_08090_gb300 as nl
+    for nf in (1, 2, 7, 100, 999, 4097, 65_537, 1_234_567):
+        p = nl.ls_choose_params(nf, 1e-9, 0)
+        n = p["n"]
+        assert n >= 2 * nf and n >= 2 * p["width"]
+        m = n
+        for q in (2, 3, 5):
+            while m % q == 0:
+                m //= q
+        assert m == 1

@@ -1,0 +1,200 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: FP64 at eps = 1e-12: max |dP| <= 1e-9; FP32 at eps = 1e-6:
+relative l2 error ||dP|| / ||P|| <= 1e-5; FP64 at eps = 1e-9 (large series):
+relative l2 <= 1e-7 and max |dP| <= 1e-6.  The six sums (Eq. 1) must agree
+with the direct sums to the NUFFT error model |dg| <= C eps sum |h_j|.
+"""
+import numpy as np
+import pytest
+
+from paper_2409_08090_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2409_08090_gb300 as m
+    m.build.build()
+    m.load_library()
+    return m
+
+
+def gpu_run(nl, s, eps, precision, nf=None, plan_nf=None, want_sums=False, max_nd=None):
+    import torch
+    nf = s.nf if nf is None else nf
+    plan = nl.Plan(max_nd or s.nd, plan_nf or nf, eps, precision)
+    dev = torch.device("cuda:0")
+    t = torch.tensor(s.t, dtype=torch.float64, device=dev)
+    y = torch.tensor(s.y, dtype=torch.float64, device=dev)
+    dy = None if s.dy is None else torch.tensor(s.dy, dtype=torch.float64, device=dev)
+    sums = torch.empty((nf, 6), dtype=torch.float64, device=dev) if want_sums else None
+    P = plan.execute(t, y, dy, s.f0, s.df, nf, eps, sums=sums)
+    torch.cuda.synchronize()
+    out = P.cpu().numpy()
+    plan.close()
+    if want_sums:
+        return out, sums.cpu().numpy()
+    return out
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_single_small_fp64_full_grid(nl, oracle_mod):
+    s = W.single_small()
+    k = np.arange(s.nf)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    P = gpu_run(nl, s, 1e-12, "fp64")
+    assert np.max(np.abs(P - P_o)) <= 1e-9
+    assert np.argmax(P) == np.argmax(P_o) == 180   # 0.37 cycles/day
+
+
+def test_single_small_fp32(nl, oracle_mod):
+    s = W.single_small()
+    k = np.arange(s.nf)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    P = gpu_run(nl, s, 1e-6, "fp32")
+    assert rel_l2(P, P_o) <= 1e-5
+    assert np.max(np.abs(P - P_o)) <= 1e-4
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp64", 1e-9), ("fp32", 1e-6)])
+def test_sums_follow_nufft_error_model(nl, oracle_mod, prec, eps):
+    s = W.single_small()
+    k = np.arange(s.nf)
+    _, S_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k, return_sums=True)
+    _, S = gpu_run(nl, s, eps, prec, want_sums=True)
+    w = 1 / s.dy ** 2
+    wh = w / w.sum()
+    h1 = np.sum(wh * np.abs(s.y - np.sum(wh * s.y)))
+    floor = 3e-7 if prec == "fp32" else 0.0
+    err = np.max(np.abs(S - S_o[:, :6]), axis=0)
+    assert np.all(err[:2] <= 10 * (eps + floor) * h1), err
+    assert np.all(err[2:] <= 10 * (eps + floor)), err
+
+
+CASES = [
+    # seed, nd, nf, sort, unit_dy, df_t
+    (1, 2, 1, True, False, 0.2),
+    (2, 3, 2, True, True, 0.2),
+    (3, 17, 7, False, False, 0.2),
+    (4, 500, 1000, False, False, 0.2),
+    (5, 4097, 4099, True, False, 0.2),
+    (6, 1000, 3001, True, True, 0.9),     # coordinates cover almost the whole period
+    (7, 2000, 5000, False, False, 1.7),   # df * T > 1: coordinates wrap
+    (8, 3000, 20_011, True, False, 0.2),  # prime nf, ragged last tile
+]
+
+
+@pytest.mark.parametrize("seed,nd,nf,sort,unit_dy,df_t", CASES)
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_random_cases(nl, oracle_mod, seed, nd, nf, sort, unit_dy, df_t, prec, eps):
+    s = W.random_case(seed, nd, nf, sort=sort, unit_dy=unit_dy, df_t=df_t)
+    k = np.arange(nf)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    P = gpu_run(nl, s, eps, prec)
+    assert np.all(np.isfinite(P))
+    if prec == "fp64":
+        assert np.max(np.abs(P - P_o)) <= 1e-9
+    else:
+        if nd >= 500:
+            assert rel_l2(P, P_o) <= 1e-5
+        assert np.max(np.abs(P - P_o)) <= 1e-4
+
+
+def test_time_offset_costs_no_accuracy(nl, oracle_mod):
+    # times near MJD 60000: the double-double phase reduction keeps eps accuracy
+    s = W.random_case(31, 800, 6000)
+    s.t = s.t + 60000.123
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(s.nf))
+    P = gpu_run(nl, s, 1e-12, "fp64")
+    assert np.max(np.abs(P - P_o)) <= 1e-9
+
+
+def test_fewer_frequencies_than_planned(nl, oracle_mod):
+    s = W.random_case(41, 700, 3001)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(s.nf))
+    P = gpu_run(nl, s, 1e-12, "fp64", plan_nf=5000, max_nd=2000)
+    assert np.max(np.abs(P - P_o)) <= 1e-9
+
+
+def test_host_buffers_match_device_buffers(nl):
+    s = W.random_case(51, 900, 4000)
+    plan = nl.Plan(s.nd, s.nf, 1e-12, "fp64")
+    P_host = plan.execute_host(s.t, s.y, s.dy, s.f0, s.df)
+    plan.close()
+    P_dev = gpu_run(nl, s, 1e-12, "fp64")
+    assert np.max(np.abs(P_host - P_dev)) <= 1e-12
+
+
+def test_repeat_calls_reuse_plan(nl):
+    import torch
+    s = W.random_case(61, 1200, 5000)
+    plan = nl.Plan(s.nd, s.nf, 1e-9, "fp64")
+    dev = torch.device("cuda:0")
+    t = torch.tensor(s.t, device=dev)
+    y = torch.tensor(s.y, device=dev)
+    dy = torch.tensor(s.dy, device=dev)
+    a = plan.execute(t, y, dy, s.f0, s.df).cpu().numpy()
+    b = plan.execute(t, y, dy, s.f0, s.df).cpu().numpy()
+    plan.close()
+    assert np.max(np.abs(a - b)) <= 1e-13
+
+
+def test_degenerate_and_invalid_inputs(nl):
+    import torch
+    dev = torch.device("cuda:0")
+    t = torch.linspace(0, 10, 50, dtype=torch.float64, device=dev)
+    plan = nl.Plan(50, 100, 1e-9, "fp64")
+    with pytest.raises(nl.LSError) as ei:
+        plan.execute(t, torch.full_like(t, 3.0), None, 0.1, 0.01)
+    assert ei.value.status == nl.LS_ERR_DEGENERATE
+    y = torch.sin(t)
+    y_nan = y.clone()
+    y_nan[7] = float("nan")
+    with pytest.raises(nl.LSError) as ei:
+        plan.execute(t, y_nan, None, 0.1, 0.01)
+    assert ei.value.status == nl.LS_ERR_ARG
+    dy0 = torch.ones_like(t)
+    dy0[3] = 0.0
+    with pytest.raises(nl.LSError) as ei:
+        plan.execute(t, y, dy0, 0.1, 0.01)
+    assert ei.value.status == nl.LS_ERR_ARG
+    # argument errors are reported before any launch
+    with pytest.raises(nl.LSError):
+        plan.execute(t, y, None, 0.1, -0.01)
+    with pytest.raises(nl.LSError):
+        plan.execute(t, y, None, 0.1, 0.01, nf=101)
+    # the plan is still usable afterwards
+    P = plan.execute(t, y, None, 0.1, 0.01).cpu().numpy()
+    assert np.all((P >= -1e-12) & (P <= 1 + 1e-12))
+    plan.close()
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-9)])
+def test_single_large_sampled(nl, oracle_mod, prec, eps):
+    # Full-size large series (N_d = 1e6, N_f = 1.2e7) in the launch configuration
+    # the benchmark times, checked on seeded random frequencies plus properties.
+    s = W.single_large()
+    P = gpu_run(nl, s, eps, prec)
+    rng = np.random.default_rng(777)
+    k = np.sort(rng.choice(s.nf, 1500, replace=False)).astype(np.int64)
+    # include the three injected periods' bins
+    for per in (0.5, 3.7, 41.0):
+        k = np.append(k, int(round((1 / per - s.f0) / s.df)))
+    k = np.unique(k)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    assert np.all(np.isfinite(P))
+    assert P.min() >= -1e-7 and P.max() <= 1 + 1e-7
+    if prec == "fp64":
+        assert rel_l2(P[k], P_o) <= 1e-7
+        assert np.max(np.abs(P[k] - P_o)) <= 1e-6
+    else:
+        assert rel_l2(P[k], P_o) <= 1e-5
+    top = np.argmax(P)
+    assert abs(1 / (s.f0 + top * s.df) - 0.5) < 1e-3
