@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--workload", default="single_large", choices=["single_large", "single_small"])
+    ap.add_argument("--workload", default="single_large",
+                    choices=["single_large", "single_medium", "single_small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
@@ -60,6 +61,11 @@ def parse_args():
 
 def workload(name: str, rank: int):
     from paper_2409_08090_gb300 import workloads as W
+    if name == "single_medium":
+        s = W.single_large(seed=W.BASE_SEED + 1 + 1000 * rank, nd=300_000, nf=4_000_000)
+        desc = ("single_medium (profiling size): Nd=3e5 over [0,3650) d with seasonal gaps; "
+                "Nf=4e6, f0=1/3650, df=1/18250")
+        return s, desc
     if name == "single_small":
         s = W.single_small(seed=W.BASE_SEED + 1000 * rank)
         desc = "single_small: Nd=1e3 over [0,100) d, Nf=1.2e4, f0=0.01, df=0.002"

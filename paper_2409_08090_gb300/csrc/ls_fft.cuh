@@ -4,10 +4,12 @@
 // sign of the type-1 transform (Eq. 2), so Re g = C and Im g = S.
 //
 // Each transform runs in place as a decimation-in-frequency (Gentleman-Sande)
-// sequence of radix-R stages, R in {2, 3, 4, 5, 8}: the output is left in
-// digit-reversed order and read back through digit_rev().  Every butterfly
-// reads and writes the same R slots, so one buffer suffices and a stage needs
-// only a barrier at its end.
+// sequence of radix-R stages, R in {3, 5} first and then {16, 8, 4, 2}, each
+// butterfly an R-point DFT in registers.  Every butterfly reads and writes the
+// same R slots, so one buffer suffices and a stage needs only a barrier at its
+// end.  The output is left in digit-reversed order; a per-length table maps a
+// frequency index to its slot.  Twiddles exp(2 pi i j k / Ls) come from
+// per-stage tables (row j holds k = 1 .. R-1), exactly rounded from FP64.
 #pragma once
 
 #include "ls_internal.cuh"
@@ -22,11 +24,12 @@ template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk2(a
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
     return mk2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-// (+i) * a
+// (+i) * a and (-i) * a
 template <typename V> __device__ __forceinline__ V mul_i(V a) { return mk2(-a.y, a.x); }
+template <typename V> __device__ __forceinline__ V mul_mi(V a) { return mk2(a.y, -a.x); }
 template <typename V, typename T> __device__ __forceinline__ V cscale(V a, T s) { return mk2(a.x * s, a.y * s); }
 
-// R-point DFT with the + sign, in registers.
+// R-point DFT with the + sign, in registers, natural order in and out.
 template <int R> struct Dft;
 
 template <> struct Dft<2> {
@@ -103,75 +106,108 @@ template <> struct Dft<8> {
     }
 };
 
-// exp(+2 pi i p / L) from the two-level root table of length L.
-template <typename V>
-__device__ __forceinline__ V root(const V *twlo, const V *twhi, int p) {
-    return cmul(twlo[p & (kTwSplit - 1)], twhi[p >> 6]);
+// 16 = 4 x 4: x index n = 4 n1 + n2, output k = k1 + 4 k2.
+template <> struct Dft<16> {
+    template <typename V> __device__ __forceinline__ static void run(V *v) {
+        using T = decltype(v[0].x);
+        const T c = T(0.92387953251128675613);   // cos(pi / 8)
+        const T s = T(0.38268343236508977173);   // sin(pi / 8)
+        const T r = T(0.70710678118654752440);   // cos(pi / 4)
+        V y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            V a[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+            Dft<4>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+        }
+        // y[n2][k1] *= exp(+2 pi i n2 k1 / 16)
+        y[1][1] = cmul(y[1][1], mk2(c, s));
+        y[1][2] = mk2((y[1][2].x - y[1][2].y) * r, (y[1][2].x + y[1][2].y) * r);
+        y[1][3] = cmul(y[1][3], mk2(s, c));
+        y[2][1] = mk2((y[2][1].x - y[2][1].y) * r, (y[2][1].x + y[2][1].y) * r);
+        y[2][2] = mul_i(y[2][2]);
+        y[2][3] = mk2(-(y[2][3].x + y[2][3].y) * r, (y[2][3].x - y[2][3].y) * r);
+        y[3][1] = cmul(y[3][1], mk2(s, c));
+        y[3][2] = mk2(-(y[3][2].x + y[3][2].y) * r, (y[3][2].x - y[3][2].y) * r);
+        y[3][3] = cmul(y[3][3], mk2(-c, -s));
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            V b[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<4>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+        }
+    }
+};
+
+// floor(a / b) for 0 <= a < 2^22 by a float reciprocal and one correction.
+__device__ __forceinline__ int small_div(int a, int b, float inv_b)
+{
+    int q = __float2int_rz((float)a * inv_b);
+    const int r = a - q * b;
+    if (r < 0) --q;
+    else if (r >= b) ++q;
+    return q;
 }
 
-// One DIF stage of radix R on `ncol` transforms of length L (stride colstride
-// between transforms), current sub-transform length Ls.
+template <typename V> __device__ __forceinline__ V ldg_c(const V *p) { return __ldg(p); }
+
+// One DIF stage of radix R over `ncol` transforms (stride colstride).
 template <int R, typename V>
-__device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, int L, int Ls,
-                                          const V *twlo, const V *twhi)
+__device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const FftStage &st,
+                                          const V *__restrict__ tw)
 {
-    const int m = Ls / R;
-    const int nb = L / R;
-    const int tmul = L / Ls;
+    const int nb = st.nb;
     const int total = ncol * nb;
+    const int m = st.m;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int col = e / nb;
-        const int bi = e - col * nb;
-        const int q = bi / m;
-        const int j = bi - q * m;
-        V *p = buf + col * colstride + q * Ls + j;
+        int col = 0, bi = e;
+        if (ncol > 1) {
+            col = small_div(e, nb, st.inv_nb);
+            bi = e - col * nb;
+        }
+        int q, j;
+        if (st.shift >= 0) {
+            q = bi >> st.shift;
+            j = bi & (m - 1);
+        } else {
+            q = small_div(bi, m, st.inv_m);
+            j = bi - q * m;
+        }
+        V *p = buf + col * colstride + q * st.Ls + j;
         V v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = p[r * m];
         Dft<R>::run(v);
-        if (j != 0) {
+        if (st.tw >= 0 && j != 0) {
+            const V *t = tw + st.tw + j * (R - 1);
 #pragma unroll
-            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], root(twlo, twhi, j * k * tmul));
+            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ldg_c(t + k - 1));
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) p[r * m] = v[r];
     }
 }
 
-// In-place DIF FFT of `ncol` transforms of length rd.L held in shared memory.
-// Ends with a barrier; output in digit-reversed order.
+// In-place DIF FFT of `ncol` transforms of length fp.L in shared memory.
+// Ends with a barrier; output in digit-reversed order (see rev table).
 template <typename V>
-__device__ void fft_dif(V *buf, int ncol, int colstride, const Radices &rd, const V *twlo,
-                        const V *twhi)
+__device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp,
+                        const V *__restrict__ tw)
 {
-    int Ls = rd.L;
-    for (int s = 0; s < rd.count; ++s) {
-        const int R = rd.rad[s];
-        switch (R) {
-        case 8: dif_stage<8>(buf, ncol, colstride, rd.L, Ls, twlo, twhi); break;
-        case 5: dif_stage<5>(buf, ncol, colstride, rd.L, Ls, twlo, twhi); break;
-        case 4: dif_stage<4>(buf, ncol, colstride, rd.L, Ls, twlo, twhi); break;
-        case 3: dif_stage<3>(buf, ncol, colstride, rd.L, Ls, twlo, twhi); break;
-        default: dif_stage<2>(buf, ncol, colstride, rd.L, Ls, twlo, twhi); break;
+    for (int s = 0; s < fp.nstages; ++s) {
+        const FftStage &st = fp.st[s];
+        switch (st.R) {
+        case 16: dif_stage<16>(buf, ncol, colstride, st, tw); break;
+        case 8: dif_stage<8>(buf, ncol, colstride, st, tw); break;
+        case 4: dif_stage<4>(buf, ncol, colstride, st, tw); break;
+        case 5: dif_stage<5>(buf, ncol, colstride, st, tw); break;
+        case 3: dif_stage<3>(buf, ncol, colstride, st, tw); break;
+        default: dif_stage<2>(buf, ncol, colstride, st, tw); break;
         }
-        Ls /= R;
         __syncthreads();
     }
-}
-
-// Slot of output k after fft_dif: the first stage's digit (k mod R_0) selects
-// the block of length L/R_0, and so on down the stages.
-__device__ __forceinline__ int digit_rev(int k, const Radices &rd)
-{
-    int pos = 0, m = rd.L;
-    for (int s = 0; s < rd.count; ++s) {
-        const int R = rd.rad[s];
-        m /= R;
-        const int q = k / R;
-        pos += (k - q * R) * m;
-        k = q;
-    }
-    return pos;
 }
 
 }  // namespace nls

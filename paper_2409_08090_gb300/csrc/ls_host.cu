@@ -42,8 +42,8 @@ namespace {
 constexpr int kTimingRing = 64;
 constexpr int kEvPerSet = LS_NUM_STAGES + 1;
 
-constexpr int kN1MaxF32 = 4608, kN2MaxF32 = 25600;
-constexpr int kN1MaxF64 = 2400, kN2MaxF64 = 12800;
+constexpr int kN1MaxF32 = 4096, kN2MaxF32 = 25600;
+constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
 
 struct DeviceGuard {
@@ -58,31 +58,24 @@ struct DeviceGuard {
     }
 };
 
-bool factor_radices(int L, Radices *r)
+int ilog2_exact(int64_t x)
 {
-    r->L = L;
-    r->count = 0;
-    int x = L;
-    auto push = [&](int R) {
-        if (r->count >= kMaxRadices) return false;
-        r->rad[r->count++] = R;
-        x /= R;
-        return true;
-    };
-    while (x % 8 == 0) if (!push(8)) return false;
-    while (x % 4 == 0) if (!push(4)) return false;
-    while (x % 2 == 0) if (!push(2)) return false;
-    while (x % 5 == 0) if (!push(5)) return false;
-    while (x % 3 == 0) if (!push(3)) return false;
-    return x == 1;
+    int k = 0;
+    while (((int64_t)1 << k) < x) ++k;
+    return ((int64_t)1 << k) == x ? k : -1;
 }
 
-bool smooth235(int64_t x)
+// Radix schedule of a sub-FFT of length L = c 2^k (c = 3^a 5^b): the odd
+// radices first, then 16s, then one stage of 8, 4 or 2.
+bool radix_schedule(int L, std::vector<int> &rad)
 {
-    if (x < 1) return false;
-    for (int p : {2, 3, 5})
-        while (x % p == 0) x /= p;
-    return x == 1;
+    rad.clear();
+    int x = L;
+    while (x % 3 == 0) { rad.push_back(3); x /= 3; }
+    while (x % 5 == 0) { rad.push_back(5); x /= 5; }
+    while (x % 16 == 0) { rad.push_back(16); x /= 16; }
+    if (x == 8 || x == 4 || x == 2) { rad.push_back(x); x = 1; }
+    return x == 1 && (int)rad.size() <= kMaxStages;
 }
 
 // ES kernel width and shape for tolerance eps (upsampling factor 2): the
@@ -100,44 +93,50 @@ void es_params(double eps, int *w, double *beta)
     *beta = bo * ww;
 }
 
-// Fine grid: the smallest 2,3,5-smooth n >= max(2 nf, 2 w) that splits as
-// n = N1 * N2 within the shared-memory limits of the two passes; N1 is the
-// largest admissible divisor not above sqrt(n).
+// Fine grid: the smallest n = c 2^k >= max(2 nf, 2 w, 64), c in the odd
+// 5-smooth set {1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125}, that splits as
+// n = N1 * N2 with N1 = 2^k1 a power of two in [kMinN1, n1max] and
+// N2 = n / N1 <= n2max (the odd factor lives in N2); among the splits the
+// most balanced one is taken.
 ls_status choose_grid(int64_t nf, int w, int prec, int64_t *n_out, int *n1_out, int *n2_out)
 {
+    static const int odd[] = {1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125};
     const int n1max = prec == LS_FP32 ? kN1MaxF32 : kN1MaxF64;
     const int n2max = prec == LS_FP32 ? kN2MaxF32 : kN2MaxF64;
-    int64_t n = 2 * nf;
-    if (n < 2 * w) n = 2 * w;
-    if (n < 16) n = 16;
-    const int64_t nlimit = (int64_t)n1max * n2max;
-    for (; n <= nlimit; ++n) {
-        if (!smooth235(n)) continue;
-        const int64_t root = (int64_t)floor(sqrt((double)n));
-        int best = -1;
-        // largest divisor <= min(n1max, sqrt n) with cofactor <= n2max
-        for (int64_t d = root < n1max ? root : n1max; d >= 1; --d) {
-            if (n % d) continue;
-            if (n / d > n2max) break;
-            best = (int)d;
-            break;
-        }
-        if (best < 0) {
-            // cofactor too large: the smallest divisor above sqrt(n) within limits
-            for (int64_t d = root + 1; d <= n1max; ++d) {
-                if (n % d) continue;
-                if (n / d <= n2max) { best = (int)d; break; }
+    int64_t nmin = 2 * nf;
+    if (nmin < 2 * w) nmin = 2 * w;
+    if (nmin < 64) nmin = 64;
+    int64_t best_n = -1;
+    int best_n1 = 0;
+    for (int c : odd) {
+        int64_t n = c;
+        while (n < nmin) n *= 2;
+        for (; n <= (int64_t)n1max * n2max; n *= 2) {
+            // most balanced admissible split of this n
+            int pick = -1;
+            double bal = 1e300;
+            for (int k1 = ilog2_exact(kMinN1); ((int64_t)1 << k1) <= n1max; ++k1) {
+                const int64_t N1 = (int64_t)1 << k1;
+                if (n % N1) break;
+                const int64_t N2 = n / N1;
+                if (N2 > n2max || N2 < 2) continue;
+                const double b = fabs(log((double)N1) - log((double)N2));
+                if (b < bal) { bal = b; pick = (int)N1; }
+            }
+            if (pick > 0) {
+                if (best_n < 0 || n < best_n || (n == best_n && pick > best_n1)) {
+                    best_n = n;
+                    best_n1 = pick;
+                }
+                break;
             }
         }
-        if (best < 0) continue;
-        Radices r1, r2;
-        if (!factor_radices(best, &r1) || !factor_radices((int)(n / best), &r2)) continue;
-        *n_out = n;
-        *n1_out = best;
-        *n2_out = (int)(n / best);
-        return LS_OK;
     }
-    return LS_ERR_UNSUPPORTED;
+    if (best_n < 0) return LS_ERR_UNSUPPORTED;
+    *n_out = best_n;
+    *n1_out = best_n1;
+    *n2_out = (int)(best_n / best_n1);
+    return LS_OK;
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_q).
@@ -252,25 +251,83 @@ void plan_free(ls_plan_s *p)
     p->allocations.clear();
 }
 
+// Stage descriptors, twiddle rows (exp(2 pi i j k / Ls), row j, k = 1..R-1,
+// exactly rounded from FP64) and the digit-reversal slots of a length-L FFT.
+template <typename T>
+bool build_fft(int L, FftPlan *fp, std::vector<T> &tw, std::vector<int> &rev)
+{
+    std::vector<int> rad;
+    if (!radix_schedule(L, rad)) return false;
+    fp->L = L;
+    fp->nstages = (int)rad.size();
+    tw.clear();
+    int Ls = L;
+    for (int s = 0; s < fp->nstages; ++s) {
+        FftStage &st = fp->st[s];
+        const int R = rad[s];
+        st.R = R;
+        st.Ls = Ls;
+        st.m = Ls / R;
+        st.nb = L / R;
+        st.shift = ilog2_exact(st.m);
+        st.inv_m = 1.0f / (float)st.m;
+        st.inv_nb = 1.0f / (float)st.nb;
+        if (st.m > 1) {
+            st.tw = (int)(tw.size() / 2);
+            for (int j = 0; j < st.m; ++j) {
+                for (int k = 1; k < R; ++k) {
+                    double re, im;
+                    root_of_unity((int64_t)j * k, Ls, &re, &im);
+                    tw.push_back((T)re);
+                    tw.push_back((T)im);
+                }
+            }
+        } else {
+            st.tw = -1;
+        }
+        Ls = st.m;
+    }
+    rev.assign(L, 0);
+    for (int k = 0; k < L; ++k) {
+        int pos = 0, m = L, kk = k;
+        for (int s = 0; s < fp->nstages; ++s) {
+            const int R = rad[s];
+            m /= R;
+            pos += (kk % R) * m;
+            kk /= R;
+        }
+        rev[k] = pos;
+    }
+    if (tw.empty()) { tw.push_back(T(1)); tw.push_back(T(0)); }
+    return true;
+}
+
+template <typename T>
+ls_status upload(ls_plan_s *p, void **dst, const void *src, size_t bytes)
+{
+    ls_status s = plan_alloc(p, dst, bytes);
+    if (s != LS_OK) return s;
+    return cuda_status(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+}
+
 template <typename T>
 ls_status upload_tables(ls_plan_s *p)
 {
-    const Geometry &g = p->g;
+    Geometry &g = p->g;
     std::vector<T> tA, tB, t4;
-    fill_root_table(tA, g.N2, 6);
-    fill_root_table(tB, g.N1, 6);
+    std::vector<int> rA, rB;
+    if (!build_fft<T>(g.N2, &g.fa, tA, rA) || !build_fft<T>(g.N1, &g.fb, tB, rB))
+        return LS_ERR_UNSUPPORTED;
     fill_root_table(t4, g.n, kTw4Bits);
     ls_status s;
-    if ((s = plan_alloc(p, &p->ws.twA, tA.size() * sizeof(T))) != LS_OK) return s;
-    if ((s = plan_alloc(p, &p->ws.twB, tB.size() * sizeof(T))) != LS_OK) return s;
-    if ((s = plan_alloc(p, &p->ws.tw4, t4.size() * sizeof(T))) != LS_OK) return s;
-    cudaError_t e;
-    if ((e = cudaMemcpy(p->ws.twA, tA.data(), tA.size() * sizeof(T), cudaMemcpyHostToDevice)))
-        return cuda_status(e);
-    if ((e = cudaMemcpy(p->ws.twB, tB.data(), tB.size() * sizeof(T), cudaMemcpyHostToDevice)))
-        return cuda_status(e);
-    if ((e = cudaMemcpy(p->ws.tw4, t4.data(), t4.size() * sizeof(T), cudaMemcpyHostToDevice)))
-        return cuda_status(e);
+    void *v;
+    if ((s = upload<T>(p, &p->ws.twA, tA.data(), tA.size() * sizeof(T))) != LS_OK) return s;
+    if ((s = upload<T>(p, &p->ws.twB, tB.data(), tB.size() * sizeof(T))) != LS_OK) return s;
+    if ((s = upload<T>(p, &v, rA.data(), rA.size() * sizeof(int))) != LS_OK) return s;
+    p->ws.revA = static_cast<int *>(v);
+    if ((s = upload<T>(p, &v, rB.data(), rB.size() * sizeof(int))) != LS_OK) return s;
+    p->ws.revB = static_cast<int *>(v);
+    if ((s = upload<T>(p, &p->ws.tw4, t4.data(), t4.size() * sizeof(T))) != LS_OK) return s;
 
     // deconvolution table 1/phi_hat(k'), k' = 0 .. nf/2
     p->deconv_count = p->nf / 2 + 1;
@@ -278,6 +335,7 @@ ls_status upload_tables(ls_plan_s *p)
     std::vector<double> z, wpsi;
     es_quadrature(g.w, g.beta, z, wpsi);
     void *dq = nullptr;
+    cudaError_t e;
     if ((e = cudaMalloc(&dq, 2 * z.size() * sizeof(double)))) return cuda_status(e);
     double *dz = static_cast<double *>(dq), *dw = dz + z.size();
     cudaMemcpy(dz, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -307,7 +365,7 @@ ls_status plan_workspace(ls_plan_s *p)
     p->ws.binstart = static_cast<int *>(v);
     if ((s = plan_alloc(p, &v, sizeof(int) * 2 * (size_t)g.nbins)) != LS_OK) return s;
     p->ws.cursor = static_cast<int *>(v);
-    if ((s = plan_alloc(p, &v, sizeof(double) * 2 * (size_t)p->nred)) != LS_OK) return s;
+    if ((s = plan_alloc(p, &v, sizeof(double) * 3 * (size_t)p->nred)) != LS_OK) return s;
     p->ws.partials = static_cast<double *>(v);
     if ((s = plan_alloc(p, &v, 256)) != LS_OK) return s;
     p->ws.counter = static_cast<unsigned int *>(v);
@@ -548,8 +606,6 @@ ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int pr
     g.N2 = n2;
     g.w = w;
     g.beta = beta;
-    factor_radices(n2, &g.radA);
-    factor_radices(n1, &g.radB);
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     int BA = 1;
     for (int cand : {8, 4, 2}) {
@@ -559,6 +615,7 @@ ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int pr
         }
     }
     g.BA = BA;
+    g.logBA = ilog2_exact(BA);
     g.nbins = n1 / BA;
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);

@@ -9,11 +9,11 @@
 
 namespace nls {
 
-constexpr int kMaxRadices = 24;   // stages of one sub-FFT
-constexpr int kTwSplit = 64;      // two-level root table: W^p = lo[p % 64] * hi[p / 64]
-constexpr int kTw4Bits = 12;      // four-step twiddle table split: 4096
-constexpr int kThreadsA = 512;
-constexpr int kThreadsB = 512;
+constexpr int kMaxStages = 16;    // stages of one sub-FFT
+constexpr int kTw4Bits = 12;      // four-step twiddle table split: W^p = lo[p % 4096] * hi[p / 4096]
+constexpr int kThreadsA = 256;
+constexpr int kThreadsB = 256;
+constexpr int kMinN1 = 32;        // keeps every kernel footprint (w <= 16) within two columns
 
 // Device status word bits (sticky until ls_sync).
 constexpr int kStatBadInput = 1;
@@ -23,11 +23,20 @@ template <typename T> struct Cx;
 template <> struct Cx<float> { using type = float2; };
 template <> struct Cx<double> { using type = double2; };
 
-// Radix schedule of one sub-FFT length L = prod(rad[s]).
-struct Radices {
+// One in-place DIF stage: sub-transforms of length Ls = R * m; butterfly
+// (q, j) touches slots q*Ls + j + r*m, r < R.  nb = L / R butterflies.
+struct FftStage {
+    int R, Ls, m, nb;
+    int shift;      // log2(m) if m is a power of two, else -1
+    float inv_m;    // 1/m and 1/nb for small exact divisions
+    float inv_nb;
+    int tw;         // offset of this stage's twiddle rows (row j: k = 1..R-1), -1 if none
+};
+
+struct FftPlan {
     int L;
-    int count;
-    int rad[kMaxRadices];
+    int nstages;
+    FftStage st[kMaxStages];
 };
 
 // The fine grid and its four-step split: n = N1 * N2, cell m = a + N1 * b.
@@ -36,19 +45,20 @@ struct Radices {
 struct Geometry {
     int64_t n;
     int N1, N2;
-    int BA;        // columns per pass-A block
+    int BA;        // columns per pass-A block (power of two)
+    int logBA;
     int nbins;     // N1 / BA
     int w;
     double beta;
-    Radices radA;  // length N2
-    Radices radB;  // length N1
+    FftPlan fa;    // length N2
+    FftPlan fb;    // length N1
 };
 
-// Point records: one set per spread geometry (x and 2x).  `cell` is the first
-// fine-grid cell the kernel touches (in [0, n)), `roff` the offset such that the
-// kernel argument of cell cell+i is z = (roff - w/2 + i) * 2/w.
+// Point records, one set per spread geometry (x and 2x).  `ab` packs the
+// first covered cell c0 = a + N1 b as a | (b << 16); `roff` is such that the
+// kernel argument of cell c0 + i is z = (roff - w/2 + i) * 2/w.
 template <typename T> struct PointSet {
-    int *cell;
+    uint32_t *ab;
     T *roff;
     typename Cx<T>::type *s[2];   // strengths (geometry x: s1, s2; geometry 2x: s3)
 };
@@ -56,10 +66,12 @@ template <typename T> struct PointSet {
 struct Stats {            // FP64 reductions, in device memory
     double W;             // sum of w_j
     double WY;            // sum of w_j y_j
+    double WY2;           // sum of w_j y_j^2
     double ybar;          // weighted mean
-    double YY;            // sum of w^_j (y_j - ybar)^2
+    double invW;
+    double scale;         // ~1/std(y): strengths are formed from scale * (y - ybar)
+    double YY;            // sum of w^_j (scale (y_j - ybar))^2, the power's denominator
     double Y2;            // sum of w^_j y_j^2 (scale for the degeneracy test)
-    double pad[3];
 };
 
 struct Workspace {
@@ -73,13 +85,14 @@ struct Workspace {
     unsigned int *counter;// last-block tickets (2)
     Stats *stats;
     int *status;          // device status word
-    void *twA;            // root tables for N2: lo (64) then hi (ceil(N2/64))
-    void *twB;            // root tables for N1
+    void *twA;            // stage twiddle rows for length N2
+    void *twB;            // stage twiddle rows for length N1
+    int *revA;            // digit-reversal slots for length N2
+    int *revB;            // digit-reversal slots for length N1
     void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
 };
 
-// Launch the whole single-series pipeline (defined in ls_kernels.cu).
 struct ExecParams {
     const double *t, *y, *dy;
     int64_t nd;

@@ -68,57 +68,85 @@ __device__ bool last_block(unsigned int *counter)
     return is_last;
 }
 
+// 1/x in FP64 from an FP32 reciprocal and two Newton steps (the FP64 divide is
+// a long instruction sequence on this part).  Falls back to the divide when x
+// is outside the FP32 normal range.
+__device__ __forceinline__ double rcp_fp64(double x)
+{
+    if (!(x > 1e-37 && x < 1e37)) return 1.0 / x;
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
 // ---------------------------------------------------------------------------
-// K1a: weights and weighted mean (FP64).  W = sum 1/dy^2, WY = sum y/dy^2.
+// K1a: weights and weighted mean (FP64).  W = sum 1/dy^2, WY = sum y/dy^2,
+// WY2 = sum y^2/dy^2.  The one-pass variance WY2/W - ybar^2 only sets the
+// scale of the strengths (the power does not depend on it); the exact YY
+// comes from the second pass.
 // ---------------------------------------------------------------------------
 __global__ void k_stats(const double *__restrict__ t, const double *__restrict__ y,
                         const double *__restrict__ dy, int64_t nd, double *partials,
                         unsigned int *counter, Stats *st, int *status)
 {
     __shared__ double sh[32];
-    double sw = 0.0, swy = 0.0;
+    double sw = 0.0, swy = 0.0, swy2 = 0.0;
     int bad = 0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double d = dy ? dy[j] : 1.0;
         const double yj = y[j];
-        const double w = 1.0 / (d * d);
+        const double w = rcp_fp64(d * d);
         bad |= !(d > 0.0) || !isfinite(d) || !isfinite(yj) || !isfinite(t[j]) || !isfinite(w);
         sw += w;
         swy += w * yj;
+        swy2 += w * yj * yj;
     }
     if (bad) atomicOr(status, kStatBadInput);
     double a = block_sum(sw, sh);
     double b = block_sum(swy, sh);
+    double c = block_sum(swy2, sh);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = b;
+        partials[3 * blockIdx.x] = a;
+        partials[3 * blockIdx.x + 1] = b;
+        partials[3 * blockIdx.x + 2] = c;
     }
     if (last_block(counter)) {
         if (threadIdx.x == 0) {
-            double W = 0.0, WY = 0.0;
+            double W = 0.0, WY = 0.0, WY2 = 0.0;
             for (unsigned int i = 0; i < gridDim.x; ++i) {
-                W += __ldcg(partials + 2 * i);
-                WY += __ldcg(partials + 2 * i + 1);
+                W += __ldcg(partials + 3 * i);
+                WY += __ldcg(partials + 3 * i + 1);
+                WY2 += __ldcg(partials + 3 * i + 2);
             }
             st->W = W;
             st->WY = WY;
+            st->WY2 = WY2;
             st->ybar = WY / W;
+            st->invW = 1.0 / W;
+            const double m2 = WY2 / W;
+            const double var = fmax(m2 - st->ybar * st->ybar, 1e-20 * m2);
+            st->scale = (var > 0.0 && isfinite(var)) ? 1.0 / sqrt(var) : 1.0;
             *counter = 0u;
         }
     }
 }
 
 // Split a fine-grid position u in [0, n] (cells) into the first covered cell
-// c0 = ceil(u - w/2) (wrapped into [0, n)) and roff = c0 - u + w/2 in [0, 1].
-__device__ __forceinline__ void split_cell(double u, int64_t n, int w, int &c0, double &roff)
+// c0 = ceil(u - w/2), wrapped into [0, n) and packed as a | (b << 16) with
+// c0 = a + N1 b, and roff = c0 - u + w/2 in [0, 1].
+__device__ __forceinline__ void split_cell(double u, const Geometry &g, uint32_t &ab,
+                                           double &roff)
 {
-    const double lo = ceil(u - 0.5 * w);
-    roff = lo - u + 0.5 * w;
-    int64_t c = (int64_t)lo;
-    if (c < 0) c += n;
-    if (c >= n) c -= n;
-    c0 = (int)c;
+    const double lo = ceil(u - 0.5 * g.w);
+    roff = lo - u + 0.5 * g.w;
+    int c = (int)lo;
+    if (c < 0) c += (int)g.n;
+    if (c >= (int)g.n) c -= (int)g.n;
+    const int b = c / g.N1;
+    ab = (uint32_t)(c - b * g.N1) | ((uint32_t)b << 16);
 }
 
 // frac(a * t) for a double-double a = a_hi + a_lo, accurate to ~1e-16 cycles
@@ -127,35 +155,38 @@ __device__ __forceinline__ double frac_dd(double a_hi, double a_lo, double t)
 {
     const double p = a_hi * t;
     const double e = fma(a_hi, t, -p);
-    double r = (p - floor(p)) + (e + a_lo * t);
+    double r = (p - floor(p)) + fma(a_lo, t, e);
     return r - floor(r);
 }
 
-// exp(2 pi i c) for a cycle count c in [0, 1) (FP64 phase).
-template <typename T> __device__ __forceinline__ void cis_cycles(double c, double &re, double &im);
+// exp(2 pi i c) for a cycle count c reduced in FP64.
+template <typename T> struct Cis;
 
-template <> __device__ __forceinline__ void cis_cycles<double>(double c, double &re, double &im)
-{
-    sincospi(2.0 * c, &im, &re);
-}
+template <> struct Cis<double> {
+    __device__ __forceinline__ static double2 of(double c) {
+        double s, co;
+        sincospi(2.0 * c, &s, &co);
+        return make_double2(co, s);
+    }
+};
 
-// FP32 path: the reduced phase is split as c = cf + dc (cf the nearest float);
-// sincospif(2 cf) is corrected to first order in 2 pi dc (|dc| < 3e-8, so the
-// neglected term is < 1e-14).  The result is rounded to FP32 by the caller.
-template <> __device__ __forceinline__ void cis_cycles<float>(double c, double &re, double &im)
-{
-    const double cr = c - rint(c);
-    const float cf = (float)cr;
-    const double dc = 6.283185307179586477 * (cr - (double)cf);
-    float sf, cfv;
-    sincospif(2.0f * cf, &sf, &cfv);
-    re = (double)cfv - dc * (double)sf;
-    im = (double)sf + dc * (double)cfv;
-}
+// FP32 path: c is split as cf + dc (cf the nearest float of c - rint(c));
+// sincospif(2 cf) is corrected to first order in 2 pi dc (|dc| < 3e-8, the
+// neglected term is < 1e-14); everything after the FP64 reduction is FP32.
+template <> struct Cis<float> {
+    __device__ __forceinline__ static float2 of(double c) {
+        const double cr = c - rint(c);
+        const float cf = (float)cr;
+        const float dc = 6.2831853071795865f * (float)(cr - (double)cf);
+        float sf, co;
+        sincospif(2.0f * cf, &sf, &co);
+        return make_float2(fmaf(-dc, sf, co), fmaf(dc, co, sf));
+    }
+};
 
 // ---------------------------------------------------------------------------
-// K1b: per-point records (FP64 arithmetic, stored in T) + bin histogram +
-// YY reduction.
+// K1b: per-point records + bin histogram + YY reduction.  Phase reduction,
+// weights and the mean-subtracted data are FP64; strengths are stored in T.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
@@ -163,44 +194,46 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
                          double fc_lo, Geometry g, PointSet<T> px, PointSet<T> p2, int *hist,
                          double *partials, unsigned int *counter, Stats *st, int *status)
 {
+    using V = Cplx<T>;
     __shared__ double sh[32];
-    const double W = st->W;
+    const double invW = st->invW;
     const double ybar = st->ybar;
+    const double scale = st->scale;
     const double n_d = (double)g.n;
     double syy = 0.0, sy2 = 0.0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double tj = t[j], yj = y[j];
         const double d = dy ? dy[j] : 1.0;
-        const double wh = 1.0 / (d * d * W);
+        const double wh = rcp_fp64(d * d) * invW;
         const double yc = yj - ybar;
+        const double a = wh * yc * scale;
         syy += wh * yc * yc;
         sy2 += wh * yj * yj;
         // NUFFT coordinates in cycles: frac(df t) and frac(2 df t), exact product.
         const double ph = frac_dd(df, 0.0, tj);
-        double ph2 = 2.0 * ph;
+        double ph2 = ph + ph;
         ph2 -= floor(ph2);
-        int c1, c2;
+        uint32_t ab1, ab2;
         double r1, r2;
-        split_cell(ph * n_d, g.n, g.w, c1, r1);
-        split_cell(ph2 * n_d, g.n, g.w, c2, r2);
+        split_cell(ph * n_d, g, ab1, r1);
+        split_cell(ph2 * n_d, g, ab2, r2);
         // Pre-phase p = exp(2 pi i fc t) and p^2.
         const double pc = frac_dd(fc_hi, fc_lo, tj);
-        double pc2 = 2.0 * pc;
+        double pc2 = pc + pc;
         pc2 -= floor(pc2);
-        double pr, pi, qr, qi;
-        cis_cycles<T>(pc, pr, pi);
-        cis_cycles<T>(pc2, qr, qi);
-        const double a = wh * yc;
-        px.cell[j] = c1;
+        const V p = Cis<T>::of(pc);
+        const V q = Cis<T>::of(pc2);
+        const T at = (T)a, wt = (T)wh;
+        px.ab[j] = ab1;
         px.roff[j] = (T)r1;
-        px.s[0][j] = mk2((T)(a * pr), (T)(a * pi));
-        px.s[1][j] = mk2((T)(wh * pr), (T)(wh * pi));
-        p2.cell[j] = c2;
+        px.s[0][j] = mk2(at * p.x, at * p.y);
+        px.s[1][j] = mk2(wt * p.x, wt * p.y);
+        p2.ab[j] = ab2;
         p2.roff[j] = (T)r2;
-        p2.s[0][j] = mk2((T)(wh * qr), (T)(wh * qi));
-        atomicAdd(&hist[(c1 % g.N1) / g.BA], 1);
-        atomicAdd(&hist[g.nbins + (c2 % g.N1) / g.BA], 1);
+        p2.s[0][j] = mk2(wt * q.x, wt * q.y);
+        atomicAdd(&hist[(ab1 & 0xFFFFu) >> g.logBA], 1);
+        atomicAdd(&hist[g.nbins + ((ab2 & 0xFFFFu) >> g.logBA)], 1);
     }
     double a = block_sum(syy, sh);
     double b = block_sum(sy2, sh);
@@ -215,7 +248,7 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
                 YY += __ldcg(partials + 2 * i);
                 Y2 += __ldcg(partials + 2 * i + 1);
             }
-            st->YY = YY;
+            st->YY = YY * st->scale * st->scale;
             st->Y2 = Y2;
             // A constant series: variance zero up to the rounding of the mean.
             if (!(YY > 1e-24 * Y2)) atomicOr(status, kStatDegenerate);
@@ -241,7 +274,6 @@ __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, i
         for (int i = lo; i < hi; ++i) s += h[i];
         chunk_tot[threadIdx.x] = s;
         __syncthreads();
-        // inclusive scan of chunk totals (Hillis-Steele)
         for (int off = 1; off < (int)blockDim.x; off <<= 1) {
             int v = (threadIdx.x >= (unsigned)off) ? chunk_tot[threadIdx.x - off] : 0;
             __syncthreads();
@@ -268,18 +300,26 @@ __global__ void k_scatter(int64_t nd, Geometry g, PointSet<T> rx, PointSet<T> r2
 {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const int c1 = rx.cell[j];
-        const int d1 = atomicAdd(&cursor[(c1 % g.N1) / g.BA], 1);
-        sx.cell[d1] = c1;
+        const uint32_t c1 = rx.ab[j];
+        const int d1 = atomicAdd(&cursor[(c1 & 0xFFFFu) >> g.logBA], 1);
+        sx.ab[d1] = c1;
         sx.roff[d1] = rx.roff[j];
         sx.s[0][d1] = rx.s[0][j];
         sx.s[1][d1] = rx.s[1][j];
-        const int c2 = r2.cell[j];
-        const int d2 = atomicAdd(&cursor[g.nbins + (c2 % g.N1) / g.BA], 1);
-        s2.cell[d2] = c2;
+        const uint32_t c2 = r2.ab[j];
+        const int d2 = atomicAdd(&cursor[g.nbins + ((c2 & 0xFFFFu) >> g.logBA)], 1);
+        s2.ab[d2] = c2;
         s2.roff[d2] = r2.roff[j];
         s2.s[0][d2] = r2.s[0][j];
     }
+}
+
+// exp(2 pi i p / n) from the two-level four-step table, p in [0, n).
+template <typename V>
+__device__ __forceinline__ V tw4_root(const V *__restrict__ tw4, int64_t p)
+{
+    return cmul(__ldg(tw4 + (p & ((1 << kTw4Bits) - 1))),
+                __ldg(tw4 + (1 << kTw4Bits) + (p >> kTw4Bits)));
 }
 
 // ---------------------------------------------------------------------------
@@ -293,8 +333,9 @@ struct PassAArgs {
     Geometry g;
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
-    const Cplx<T> *twA;    // N2 root table (lo, hi)
-    const Cplx<T> *tw4;    // n four-step table (lo 4096, hi)
+    const Cplx<T> *twA;    // stage twiddles, length N2
+    const int *revA;       // digit-reversal slots, length N2
+    const Cplx<T> *tw4;    // four-step table (lo 4096, hi)
     Cplx<T> *H;
 };
 
@@ -312,24 +353,32 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = A.g;
     const int N1 = g.N1, N2 = g.N2, BA = g.BA;
+    const int nhi = (N2 + 63) >> 6;
     V *buf = reinterpret_cast<V *>(smem_raw);
-    V *twlo = buf + (size_t)BA * N2;
-    V *twhi = twlo + kTwSplit;
-    const int nhi = (N2 + kTwSplit - 1) / kTwSplit;
+    V *alo = buf + (size_t)BA * N2;        // W_n^{a dl}, dl < 64, per column
+    V *ahi = alo + BA * 64;                // W_n^{64 a dh}, per column
 
     const int grid = blockIdx.y;
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
 
-    for (int i = threadIdx.x; i < kTwSplit + nhi; i += blockDim.x) twlo[i] = A.twA[i];
     for (int i = threadIdx.x; i < BA * N2; i += blockDim.x) buf[i] = mk2(T(0), T(0));
+    for (int i = threadIdx.x; i < BA * 64; i += blockDim.x) {
+        const int col = i >> 6;
+        alo[i] = tw4_root(A.tw4, (int64_t)(a0 + col) * (i & 63));
+    }
+    for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
+        const int col = i / nhi;
+        const int dh = i - col * nhi;
+        ahi[i] = tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * dh) % g.n);
+    }
     __syncthreads();
 
     // ---- spread ----
     const PointSet<T> &P = (grid < 2) ? A.px : A.p2;
     const V *str = (grid == 1) ? A.px.s[1] : P.s[0];
     const int *bs = A.binstart + ((grid < 2) ? 0 : (g.nbins + 1));
-    const int nbb = (g.w - 1 + BA - 1) / BA;   // bins before this one that reach it
+    const int nbb = (g.w - 1 + BA - 1) >> g.logBA;   // bins before this one that reach it
     int r0s, r0e, r1s = 0, r1e = 0;
     if (nbb + 1 >= g.nbins) {
         r0s = bs[0];
@@ -350,82 +399,60 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     const T beta = T(g.beta);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
-        const int c0 = P.cell[j];
+        const uint32_t ab = P.ab[j];
+        const int aj = (int)(ab & 0xFFFFu);
+        const int bj = (int)(ab >> 16);
+        // footprint columns aj .. aj+w-1 (mod N1) against block a0 .. a0+BA-1
+        int o = aj - a0;
+        if (o < 0) o += N1;
+        int i0, cs;
+        if (o < BA) { i0 = 0; cs = o; }
+        else { i0 = N1 - o; cs = 0; }
+        const int cnt = min(BA - cs, g.w - i0);
+        if (cnt <= 0) continue;
         const T roff = P.roff[j];
         const V s = str[j];
-        int aa = c0 % N1;
-        int bb = c0 / N1;
-        for (int i = 0; i < g.w; ++i) {
-            const int ca = aa - a0;
-            if (ca >= 0 && ca < BA) {
-                const T z = (roff - halfw + T(i)) * zscale;
-                const T v = es_kernel(z, beta);
-                V *dst = buf + (size_t)ca * N2 + bb;
-                atomicAdd(&dst->x, s.x * v);
-                atomicAdd(&dst->y, s.y * v);
-            }
-            if (++aa == N1) {
-                aa = 0;
-                if (++bb == N2) bb = 0;
-            }
+        for (int u = 0; u < cnt; ++u) {
+            const int i = i0 + u;
+            int b = bj + ((aj + i >= N1) ? 1 : 0);
+            if (b >= N2) b -= N2;
+            const T z = (roff - halfw + T(i)) * zscale;
+            const T v = es_kernel(z, beta);
+            V *dst = buf + (size_t)(cs + u) * N2 + b;
+            atomicAdd(&dst->x, s.x * v);
+            atomicAdd(&dst->y, s.y * v);
         }
     }
     __syncthreads();
 
     // ---- column FFTs over b ----
-    fft_dif(buf, BA, N2, g.radA, twlo, twhi);
+    fft_dif(buf, BA, N2, g.fa, A.twA);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a] ----
-    const V *t4lo = A.tw4;
-    const V *t4hi = A.tw4 + (1 << kTw4Bits);
     V *H = A.H + (size_t)grid * (size_t)g.n;
     for (int e = threadIdx.x; e < BA * N2; e += blockDim.x) {
-        const int c = e % BA;
-        const int d = e / BA;
-        const int a = a0 + c;
-        V v = buf[(size_t)c * N2 + digit_rev(d, g.radA)];
-        const int64_t p = (int64_t)a * d;   // < n
-        const V tw = cmul(t4lo[p & ((1 << kTw4Bits) - 1)], t4hi[p >> kTw4Bits]);
-        H[(size_t)d * N1 + a] = cmul(v, tw);
+        const int col = e & (BA - 1);
+        const int d = e >> g.logBA;
+        const V v = buf[(size_t)col * N2 + __ldg(A.revA + d)];
+        const V tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
+        H[(size_t)d * N1 + a0 + col] = cmul(v, tw);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Pass B: for row d, FFT the three grids over a (length N1), deconvolve the
-// needed modes and evaluate the power in FP64.
+// Power.  Generalised (floating-mean) periodogram, standard normalisation,
+// from the six sums and YY.  With CC = sum w^ cos^2 - C^2 = (1 + C2)/2 - C^2,
+// SS = (1 - C2)/2 - S^2, CS = S2/2 - C S, the rotation through w tau
+// (tan 2 w tau = (S2 - 2CS)/(C2 - (C^2 - S^2))) diagonalises M = [[CC, CS],
+// [CS, SS]], so YC_tau^2/CC_tau + YS_tau^2/SS_tau = v^T M^-1 v with v = (Ch, Sh):
+// P = (Ch^2 SS - 2 Ch Sh CS + Sh^2 CC) / ((CC SS - CS^2) YY).
 // ---------------------------------------------------------------------------
-template <typename T>
-struct PassBArgs {
-    Geometry g;
-    const Cplx<T> *twB;
-    const Cplx<T> *H;
-    const T *deconv;       // 1/phi_hat(|k'|)
-    const Stats *st;
-    int64_t nf, K0;
-    double *power;
-    double *sums;
-};
 
-// Generalised (floating-mean) power, standard normalisation, from the six sums
-// and YY (FP64).  With CC = sum w^ cos^2 - C^2 = (1 + C2)/2 - C^2,
-// SS = (1 - C2)/2 - S^2, CS = S2/2 - C S, the 2x2 system M = [[CC, CS], [CS, SS]]
-// is diagonalised by the rotation through w tau (tan 2 w tau =
-// (S2 - 2CS)/(C2 - (C^2 - S^2))), so YC_tau^2/CC_tau + YS_tau^2/SS_tau =
-// v^T M^-1 v with v = (Ch, Sh).  The closed form needs no trigonometry; a
-// nearly singular M (all phases equal mod pi) falls back to the explicit tau
-// rotation, dropping a vanishing CC_tau or SS_tau term.
-__device__ __forceinline__ double ls_power(double Ch, double Sh, double C, double S, double C2,
-                                           double S2, double YY)
+// Explicit tau rotation (FP64), used for a nearly singular M (all phases equal
+// mod pi): a vanishing CC_tau or SS_tau term is dropped.
+__device__ double ls_power_tau(double Ch, double Sh, double C, double S, double C2, double S2,
+                               double YY)
 {
-    const double CC = 0.5 * (1.0 + C2) - C * C;
-    const double SS = 0.5 * (1.0 - C2) - S * S;
-    const double CS = 0.5 * S2 - C * S;
-    const double D = CC * SS - CS * CS;
-    if (D > 1e-12 * (CC * CC + SS * SS) && D > 1e-30) {
-        const double N = Ch * Ch * SS - 2.0 * Ch * Sh * CS + Sh * Sh * CC;
-        return N / (D * YY);
-    }
-    // tau rotation: cos/sin of 2 w tau, then half-angle.
     const double num = S2 - 2.0 * C * S;
     const double den = C2 - (C * C - S * S);
     const double r = hypot(num, den);
@@ -455,6 +482,119 @@ __device__ __forceinline__ double ls_power(double Ch, double Sh, double C, doubl
     return p / YY;
 }
 
+__device__ __forceinline__ double ls_power_fp64(double Ch, double Sh, double C, double S,
+                                                double C2, double S2, double YY)
+{
+    const double CC = 0.5 * (1.0 + C2) - C * C;
+    const double SS = 0.5 * (1.0 - C2) - S * S;
+    const double CS = 0.5 * S2 - C * S;
+    const double D = CC * SS - CS * CS;
+    if (D > 1e-12 * (CC * CC + SS * SS) && D > 1e-30) {
+        const double N = Ch * Ch * SS - 2.0 * Ch * Sh * CS + Sh * Sh * CC;
+        return N / (D * YY);
+    }
+    return ls_power_tau(Ch, Sh, C, S, C2, S2, YY);
+}
+
+// Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <=
+// ulp(hi)/2, about 48 significant bits.  Error-free transforms: Knuth's
+// two-sum, the fast two-sum for |a| >= |b|, and the fma two-product.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = two_sum(x.hi, y.hi);
+    const ff t = two_sum(x.lo, y.lo);
+    ff u = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(u.hi, u.lo + t.lo);
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const ff p = two_prod(x.hi, y.hi);
+    return fast_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+__device__ __forceinline__ ff ff_div(ff x, ff y)
+{
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const ff r = ff_add(x, ff_neg(ff_mul(y, ff{q1, 0.f})));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    const ff r2 = ff_add(r, ff_neg(ff_mul(y, ff{q2, 0.f})));
+    const float q3 = __fdiv_rn(r2.hi, y.hi);
+    const ff q = fast_two_sum(q1, q2);
+    return ff_add(q, ff{q3, 0.f});
+}
+
+// FP32 path: the sums arrive as FP32 values (exact inputs here); the ratio is
+// evaluated in double-float, whose rounding (~1e-14 relative) is far below
+// the FP32 sums' own error, and falls back to FP64 for a nearly singular M.
+__device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float S, float C2,
+                                              float S2, ff YY, double YYd)
+{
+    const ff CC = ff_add(two_sum(0.5f, 0.5f * C2), ff_neg(two_prod(C, C)));
+    const ff SS = ff_add(two_sum(0.5f, -0.5f * C2), ff_neg(two_prod(S, S)));
+    const ff CS = ff_add(ff{0.5f * S2, 0.f}, ff_neg(two_prod(C, S)));
+    const ff D = ff_add(ff_mul(CC, SS), ff_neg(ff_mul(CS, CS)));
+    if (!(D.hi > 1e-12f * (CC.hi * CC.hi + SS.hi * SS.hi) && D.hi > 1e-30f))
+        return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd);
+    const ff ChSh = two_prod(Ch, Sh);
+    const ff N = ff_add(ff_add(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
+                        ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, CS)));
+    const ff P = ff_div(N, ff_mul(D, YY));
+    return (double)P.hi + (double)P.lo;
+}
+
+// ---------------------------------------------------------------------------
+// Pass B: for row d, FFT the three grids over a (length N1), deconvolve the
+// needed modes and evaluate the power.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PassBArgs {
+    Geometry g;
+    const Cplx<T> *twB;
+    const int *revB;
+    const Cplx<T> *H;
+    const T *deconv;       // 1/phi_hat(|k'|)
+    const Stats *st;
+    int64_t nf, K0;
+    double *power;
+    double *sums;
+};
+
+template <typename T> struct PowerOut;
+
+template <> struct PowerOut<double> {
+    __device__ __forceinline__ static double eval(double2 g1, double2 g2, double2 g3, double dc,
+                                                  double YY, ff) {
+        return ls_power_fp64(g1.x * dc, g1.y * dc, g2.x * dc, g2.y * dc, g3.x * dc, g3.y * dc,
+                             YY);
+    }
+};
+template <> struct PowerOut<float> {
+    __device__ __forceinline__ static double eval(float2 g1, float2 g2, float2 g3, float dc,
+                                                  double YY, ff YYf) {
+        return ls_power_ff(g1.x * dc, g1.y * dc, g2.x * dc, g2.y * dc, g3.x * dc, g3.y * dc,
+                           YYf, YY);
+    }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
 {
@@ -463,48 +603,47 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     const Geometry &g = B.g;
     const int N1 = g.N1, N2 = g.N2;
     V *buf = reinterpret_cast<V *>(smem_raw);
-    V *twlo = buf + 3 * (size_t)N1;
-    V *twhi = twlo + kTwSplit;
-    const int nhi = (N1 + kTwSplit - 1) / kTwSplit;
     const int d = blockIdx.x;
 
-    for (int i = threadIdx.x; i < kTwSplit + nhi; i += blockDim.x) twlo[i] = B.twB[i];
     for (int gi = 0; gi < 3; ++gi) {
         const V *src = B.H + (size_t)gi * (size_t)g.n + (size_t)d * N1;
         for (int a = threadIdx.x; a < N1; a += blockDim.x) buf[(size_t)gi * N1 + a] = src[a];
     }
     __syncthreads();
 
-    fft_dif(buf, 3, N1, g.radB, twlo, twhi);
+    fft_dif(buf, 3, N1, g.fb, B.twB);
 
     const double YY = B.st->YY;
+    ff YYf;
+    YYf.hi = (float)YY;
+    YYf.lo = (float)(YY - (double)YYf.hi);
     const int64_t n = g.n;
-    const int64_t hi_start = n - B.K0;
-    const int64_t lo_end = B.nf - B.K0;
-    for (int c = threadIdx.x; c < N1; c += blockDim.x) {
+    const int64_t hi_start = n - B.K0;     // k >= hi_start -> k' = k - n < 0
+    const int64_t lo_end = B.nf - B.K0;    // k <  lo_end   -> k' = k >= 0
+    const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
+    const int c2 = (int)((hi_start - d + N2 - 1) / N2);
+    const int count = c1 + (N1 - c2);
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+        const int c = (e < c1) ? e : (c2 + e - c1);
         const int64_t k = d + (int64_t)N2 * c;
-        int64_t kp;
-        if (k < lo_end) kp = k;
-        else if (k >= hi_start) kp = k - n;
-        else continue;
-        const int pos = digit_rev(c, g.radB);
-        const T dc = B.deconv[kp < 0 ? -kp : kp];
+        const int64_t kp = (e < c1) ? k : k - n;
+        const int pos = __ldg(B.revB + c);
+        const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
         const V g1 = buf[pos], g2 = buf[N1 + pos], g3 = buf[2 * N1 + pos];
-        const double Ch = (double)(g1.x * dc), Sh = (double)(g1.y * dc);
-        const double C = (double)(g2.x * dc), S = (double)(g2.y * dc);
-        const double C2 = (double)(g3.x * dc), S2 = (double)(g3.y * dc);
         const int64_t out = kp + B.K0;
-        if (B.power) B.power[out] = ls_power(Ch, Sh, C, S, C2, S2, YY);
+        if (B.power) B.power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
         if (B.sums) {
             double *o = B.sums + 6 * out;
-            o[0] = Ch; o[1] = Sh; o[2] = C; o[3] = S; o[4] = C2; o[5] = S2;
+            o[0] = (double)(g1.x * dc); o[1] = (double)(g1.y * dc);
+            o[2] = (double)(g2.x * dc); o[3] = (double)(g2.y * dc);
+            o[4] = (double)(g3.x * dc); o[5] = (double)(g3.y * dc);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // Deconvolution table: 1/phi_hat(k), phi_hat(k) = w int_0^1 psi(z) cos(pi k w z / n) dz
-// by a Gauss-Legendre rule on [0, 1] (nodes z, weights already times psi(z)).
+// by the plan's quadrature rule (nodes z, weights already times psi(z)).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_deconv(T *out, int64_t count, double w_over_n, double w, const double *z,
@@ -525,17 +664,17 @@ __global__ void k_deconv(T *out, int64_t count, double w_over_n, double w, const
 template <typename T>
 size_t point_record_bytes()
 {
-    return sizeof(int) + sizeof(T) + 2 * sizeof(Cplx<T>);
+    return sizeof(uint32_t) + sizeof(T) + 2 * sizeof(Cplx<T>);
 }
 
 size_t passA_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * ((size_t)g.BA * g.N2 + kTwSplit + (g.N2 + kTwSplit - 1) / kTwSplit);
+    return cx * ((size_t)g.BA * g.N2 + (size_t)g.BA * 64 + (size_t)g.BA * ((g.N2 + 63) / 64));
 }
 
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * (3 * (size_t)g.N1 + kTwSplit + (g.N1 + kTwSplit - 1) / kTwSplit);
+    return cx * 3 * (size_t)g.N1;
 }
 
 template <typename T>
@@ -551,7 +690,7 @@ static PointSet<T> carve(void *base, int64_t max_nd)
     off = align(off + sizeof(Cplx<T>) * (size_t)max_nd);
     p.roff = reinterpret_cast<T *>(b + off);
     off = align(off + sizeof(T) * (size_t)max_nd);
-    p.cell = reinterpret_cast<int *>(b + off);
+    p.ab = reinterpret_cast<uint32_t *>(b + off);
     return p;
 }
 
@@ -582,6 +721,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     A.p2 = s2;
     A.binstart = ws.binstart;
     A.twA = static_cast<const Cplx<T> *>(ws.twA);
+    A.revA = ws.revA;
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
@@ -593,6 +733,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     PassBArgs<T> B;
     B.g = g;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
+    B.revB = ws.revB;
     B.H = static_cast<const Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv);
     B.st = ws.stats;

@@ -43,13 +43,23 @@ def test_status_strings():
     assert nl.ls_status_str(99) == "unknown status"
 
 
+ODD = (1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125)
+
+
+def _is_allowed(n):
+    m = n
+    while m % 2 == 0:
+        m //= 2
+    return m in ODD
+
+
 @pytest.mark.parametrize("nf,eps,prec,w,n", [
-    (12_000, 1e-12, 0, 13, 24_000),
-    (12_000, 1e-9, 0, 10, 24_000),
-    (12_000, 1e-6, 1, 7, 24_000),
-    (12_000_000, 1e-6, 1, 7, 24_000_000),
-    (12_000_000, 1e-9, 0, 10, 24_000_000),
-    (120_000, 1e-6, 1, 7, 240_000),
+    (12_000, 1e-12, 0, 13, 24_576),
+    (12_000, 1e-9, 0, 10, 24_576),
+    (12_000, 1e-6, 1, 7, 24_576),
+    (12_000_000, 1e-6, 1, 7, 25_165_824),
+    (12_000_000, 1e-9, 0, 10, 25_165_824),
+    (120_000, 1e-6, 1, 7, 245_760),
 ])
 def test_choose_params(nf, eps, prec, w, n):
     import paper_2409_08090_gb300 as nl
@@ -58,8 +68,9 @@ def test_choose_params(nf, eps, prec, w, n):
     assert p["n"] == n
     assert p["n1"] * p["n2"] == p["n"]
     assert abs(p["beta"] - 2.30 * w) < 1e-12
-    # split limits of the two passes
-    assert p["n1"] <= (4608 if prec == 1 else 2400)
+    # split limits of the two passes; N1 a power of two
+    assert 32 <= p["n1"] <= (4096 if prec == 1 else 2048)
+    assert p["n1"] & (p["n1"] - 1) == 0
     assert p["n2"] <= (25600 if prec == 1 else 12800)
 
 
@@ -73,14 +84,15 @@ def test_choose_params_rejects():
         nl.ls_choose_params(100, 0.5, 0)
 
 
-def test_grid_sizes_are_smooth_and_cover_oversampling():
+def test_grid_sizes_are_minimal_admissible():
     import paper_2409_08090_gb300 as nl
     for nf in (1, 2, 7, 100, 999, 4097, 65_537, 1_234_567):
         p = nl.ls_choose_params(nf, 1e-9, 0)
         n = p["n"]
-        assert n >= 2 * nf and n >= 2 * p["width"]
-        m = n
-        for q in (2, 3, 5):
-            while m % q == 0:
-                m //= q
-        assert m == 1
+        nmin = max(2 * nf, 2 * p["width"], 64)
+        assert n >= nmin and _is_allowed(n)
+        # no admissible size in [nmin, n): n = c 2^k splits as N1 = 2^k1 >= 32
+        # (a power of two) times N2 >= 2, so k >= 5 and c 2^(k-5) >= 2
+        smaller = [c * 2 ** k for c in ODD for k in range(5, 40)
+                   if nmin <= c * 2 ** k < n and c * 2 ** (k - 5) >= 2]
+        assert not smaller, (nf, n, smaller[:3])
