@@ -633,8 +633,10 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
         const int64_t out = kp + B.K0;
         if (B.power) B.power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
         if (B.sums) {
+            // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
+            const double us = 1.0 / B.st->scale;
             double *o = B.sums + 6 * out;
-            o[0] = (double)(g1.x * dc); o[1] = (double)(g1.y * dc);
+            o[0] = (double)(g1.x * dc) * us; o[1] = (double)(g1.y * dc) * us;
             o[2] = (double)(g2.x * dc); o[3] = (double)(g2.y * dc);
             o[4] = (double)(g3.x * dc); o[5] = (double)(g3.y * dc);
         }
