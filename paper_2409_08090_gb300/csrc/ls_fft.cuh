@@ -7,8 +7,8 @@
 // sequence of radix-R stages, R in {3, 5} first and then {16, 8, 4, 2}, each
 // butterfly an R-point DFT in registers.  Every butterfly reads and writes the
 // same R slots, so one buffer suffices and a stage needs only a barrier at its
-// end.  The output is left in digit-reversed order; a per-length table maps a
-// frequency index to its slot.  Twiddles exp(2 pi i j k / Ls) come from
+// end.  The output is left in digit-reversed order; a per-length table gives
+// the frequency index each slot holds.  Twiddles exp(2 pi i j k / Ls) come from
 // per-stage tables (row j holds k = 1 .. R-1), exactly rounded from FP64.
 #pragma once
 
@@ -141,6 +141,9 @@ template <> struct Dft<16> {
     }
 };
 
+__device__ __host__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+__device__ __host__ __forceinline__ int padded_len(int L) { return L + (L >> 4) + 1; }
+
 // floor(a / b) for 0 <= a < 2^22 by a float reciprocal and one correction.
 __device__ __forceinline__ int small_div(int a, int b, float inv_b)
 {
@@ -175,10 +178,11 @@ __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const
             q = small_div(bi, m, st.inv_m);
             j = bi - q * m;
         }
-        V *p = buf + col * colstride + q * st.Ls + j;
+        V *p = buf + col * colstride;
+        const int base = q * st.Ls + j;
         V v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = p[r * m];
+        for (int r = 0; r < R; ++r) v[r] = p[pad16(base + r * m)];
         Dft<R>::run(v);
         if (st.tw >= 0 && j != 0) {
             const V *t = tw + st.tw + j * (R - 1);
@@ -186,12 +190,13 @@ __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const
             for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ldg_c(t + k - 1));
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) p[r * m] = v[r];
+        for (int r = 0; r < R; ++r) p[pad16(base + r * m)] = v[r];
     }
 }
 
-// In-place DIF FFT of `ncol` transforms of length fp.L in shared memory.
-// Ends with a barrier; output in digit-reversed order (see rev table).
+// In-place DIF FFT of `ncol` transforms of length fp.L in shared memory
+// (padded layout, columns colstride apart).  Ends with a barrier; output in
+// digit-reversed order: slot pos holds frequency index inv_rev[pos].
 template <typename V>
 __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp,
                         const V *__restrict__ tw)

@@ -252,7 +252,8 @@ void plan_free(ls_plan_s *p)
 }
 
 // Stage descriptors, twiddle rows (exp(2 pi i j k / Ls), row j, k = 1..R-1,
-// exactly rounded from FP64) and the digit-reversal slots of a length-L FFT.
+// exactly rounded from FP64) and, per output slot, the frequency index it
+// holds after a length-L DIF FFT (the inverse digit reversal).
 template <typename T>
 bool build_fft(int L, FftPlan *fp, std::vector<T> &tw, std::vector<int> &rev)
 {
@@ -296,7 +297,7 @@ bool build_fft(int L, FftPlan *fp, std::vector<T> &tw, std::vector<int> &rev)
             pos += (kk % R) * m;
             kk /= R;
         }
-        rev[k] = pos;
+        rev[pos] = k;   // slot pos holds frequency index k
     }
     if (tw.empty()) { tw.push_back(T(1)); tw.push_back(T(0)); }
     return true;
@@ -398,20 +399,6 @@ ls_status ensure_staging(ls_plan_s *p, double **buf, size_t count)
     return s;
 }
 
-// fc = f0 + K0 df as a double-double (two-product and two-sum).
-void centre_frequency(double f0, double df, int64_t K0, double *hi, double *lo)
-{
-    const double k = (double)K0;
-    const double ph = k * df;
-    const double pl = fma(k, df, -ph);
-    const double s = f0 + ph;
-    const double bb = s - f0;
-    const double e = (f0 - (s - bb)) + (ph - bb);
-    const double l = e + pl;
-    *hi = s + l;
-    *lo = l - (*hi - s);
-}
-
 // Accumulate the oldest pending event set (waits for it).
 cudaError_t drain_one_timing(ls_plan_s *p)
 {
@@ -482,10 +469,10 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
     ep.y = dev_in[1];
     ep.dy = dev_in[2];
     ep.nd = nd;
+    ep.f0 = f0;
     ep.df = df;
     ep.nf = nf;
     ep.K0 = nf / 2;
-    centre_frequency(f0, df, ep.K0, &ep.fc_hi, &ep.fc_lo);
     ep.power = dpow;
     ep.sums = dsums;
     int nred = (int)((nd + 255) / 256);

@@ -87,8 +87,8 @@ struct Workspace {
     int *status;          // device status word
     void *twA;            // stage twiddle rows for length N2
     void *twB;            // stage twiddle rows for length N1
-    int *revA;            // digit-reversal slots for length N2
-    int *revB;            // digit-reversal slots for length N1
+    int *revA;            // frequency index held by each output slot, length N2
+    int *revB;            // frequency index held by each output slot, length N1
     void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
 };
@@ -96,8 +96,7 @@ struct Workspace {
 struct ExecParams {
     const double *t, *y, *dy;
     int64_t nd;
-    double df;
-    double fc_hi, fc_lo;  // centre frequency f0 + K0 df as a double-double
+    double f0, df;        // frequency grid f_k = f0 + k df
     int64_t nf, K0;
     double *power;        // may be null
     double *sums;         // may be null

@@ -18,6 +18,7 @@
 // (length N2) and applies exp(2 pi i a d / n); pass B transforms each row d over
 // a (length N1) giving mode k = d + N2 c, k' = k or k - n.
 #include <math.h>
+#include <string.h>
 
 #include "ls_fft.cuh"
 #include "ls_internal.cuh"
@@ -68,17 +69,35 @@ __device__ bool last_block(unsigned int *counter)
     return is_last;
 }
 
-// 1/x in FP64 from an FP32 reciprocal and two Newton steps (the FP64 divide is
-// a long instruction sequence on this part).  Falls back to the divide when x
-// is outside the FP32 normal range.
+// Finite-value and positivity tests on the bit pattern (integer pipe).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) !=
+           0x7ff0000000000000ull;
+}
+
+// 1/x in FP64 from an FP32 reciprocal and one Newton step (relative error
+// below 4e-15; the FP64 divide is a long sequence on a part whose FP64 rate is
+// 1/64 of FP32).  The exponent test on the bits keeps x within FP32 range;
+// otherwise the divide is used.
 __device__ __forceinline__ double rcp_fp64(double x)
 {
-    if (!(x > 1e-37 && x < 1e37)) return 1.0 / x;
-    double r = (double)__frcp_rn((float)x);
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const int ex = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+    if (ex < 1023 - 120 || ex > 1023 + 120) return 1.0 / x;
+    const double r = (double)__frcp_rn((float)x);
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Sum of `width` interleaved partial sums over `nparts` blocks, by the whole
+// (last) block in a fixed order; results valid in thread 0.
+__device__ void reduce_partials(const double *partials, int nparts, int width, double *out,
+                                double *sh)
+{
+    for (int c = 0; c < width; ++c) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += __ldcg(partials + width * i + c);
+        out[c] = block_sum(v, sh);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -93,18 +112,19 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
 {
     __shared__ double sh[32];
     double sw = 0.0, swy = 0.0, swy2 = 0.0;
-    int bad = 0;
+    bool ok = true;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double d = dy ? dy[j] : 1.0;
         const double yj = y[j];
+        ok &= finite_bits(d) && finite_bits(yj) && finite_bits(t[j]) && __double_as_longlong(d) > 0;
         const double w = rcp_fp64(d * d);
-        bad |= !(d > 0.0) || !isfinite(d) || !isfinite(yj) || !isfinite(t[j]) || !isfinite(w);
+        const double wy = w * yj;
         sw += w;
-        swy += w * yj;
-        swy2 += w * yj * yj;
+        swy += wy;
+        swy2 = fma(wy, yj, swy2);
     }
-    if (bad) atomicOr(status, kStatBadInput);
+    if (!ok) atomicOr(status, kStatBadInput);
     double a = block_sum(sw, sh);
     double b = block_sum(swy, sh);
     double c = block_sum(swy2, sh);
@@ -114,13 +134,10 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
         partials[3 * blockIdx.x + 2] = c;
     }
     if (last_block(counter)) {
+        double r[3];
+        reduce_partials(partials, gridDim.x, 3, r, sh);
         if (threadIdx.x == 0) {
-            double W = 0.0, WY = 0.0, WY2 = 0.0;
-            for (unsigned int i = 0; i < gridDim.x; ++i) {
-                W += __ldcg(partials + 3 * i);
-                WY += __ldcg(partials + 3 * i + 1);
-                WY2 += __ldcg(partials + 3 * i + 2);
-            }
+            const double W = r[0], WY = r[1], WY2 = r[2];
             st->W = W;
             st->WY = WY;
             st->WY2 = WY2;
@@ -134,106 +151,162 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
     }
 }
 
-// Split a fine-grid position u in [0, n] (cells) into the first covered cell
-// c0 = ceil(u - w/2), wrapped into [0, n) and packed as a | (b << 16) with
-// c0 = a + N1 b, and roff = c0 - u + w/2 in [0, 1].
-__device__ __forceinline__ void split_cell(double u, const Geometry &g, uint32_t &ab,
-                                           double &roff)
+// ---------------------------------------------------------------------------
+// Exact phase reduction in integer arithmetic.  A double f = +-m 2^e (m < 2^53)
+// times a double t is the 106-bit integer product of the mantissas times a
+// power of two, so frac(f t) is a bit field of that product: it is taken as a
+// 128-bit fixed-point fraction (value F / 2^128), exact up to truncation below
+// 2^-128, on the integer pipe.  frac((f0 + K0 df) t) = frac(frac(f0 t) +
+// K0 frac(df t)) then follows by 128-bit modular arithmetic.
+// ---------------------------------------------------------------------------
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 frac_fixed(uint64_t fm, int fe, int fneg, double t)
 {
-    const double lo = ceil(u - 0.5 * g.w);
-    roff = lo - u + 0.5 * g.w;
-    int c = (int)lo;
-    if (c < 0) c += (int)g.n;
-    if (c >= (int)g.n) c -= (int)g.n;
-    const int b = c / g.N1;
-    ab = (uint32_t)(c - b * g.N1) | ((uint32_t)b << 16);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const uint64_t tm = (b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
+    const int sh = fe + (ex ? ex : 1) - 1075 + 128;   // F = P 2^sh mod 2^128
+    const u128 P = (u128)fm * tm;
+    u128 F;
+    if (sh >= 128) F = 0;
+    else if (sh >= 0) F = P << sh;
+    else if (sh > -128) F = P >> (-sh);
+    else F = 0;
+    return (fneg ^ (int)(b >> 63)) ? (u128)0 - F : F;
 }
 
-// frac(a * t) for a double-double a = a_hi + a_lo, accurate to ~1e-16 cycles
-// whatever the size of a t (error-free product of a_hi t by fma).
-__device__ __forceinline__ double frac_dd(double a_hi, double a_lo, double t)
+// Cell split of the coordinate frac * n: c0 = ceil(u - w/2) packed as
+// a | (b << 16) with c0 = a + N1 b, and roff = c0 - u + w/2 in [0, 1], from
+// the 128-bit fraction (u = F n / 2^128 to within n 2^-128 cells).
+template <typename T>
+__device__ __forceinline__ void split_fixed(u128 F, const Geometry &g, uint32_t &ab, T &roff)
 {
-    const double p = a_hi * t;
-    const double e = fma(a_hi, t, -p);
-    double r = (p - floor(p)) + fma(a_lo, t, e);
-    return r - floor(r);
+    const u128 U = (u128)(uint64_t)(F >> 64) * (uint64_t)g.n +
+                   (((u128)(uint64_t)F * (uint64_t)g.n) >> 64);
+    const int ui = (int)(uint64_t)(U >> 64);       // floor(u)
+    const uint64_t uf = (uint64_t)U;               // frac(u) 2^64
+    int c0;
+    u128 R;                                        // roff 2^64
+    if (g.w & 1) {
+        const bool up = uf > 0x8000000000000000ull;
+        c0 = ui - (g.w - 1) / 2 + (up ? 1 : 0);
+        R = ((u128)(up ? 3u : 1u) << 63) - uf;
+    } else {
+        const bool up = uf != 0;
+        c0 = ui - g.w / 2 + (up ? 1 : 0);
+        R = ((u128)(up ? 1u : 0u) << 64) - uf;
+    }
+    if (c0 < 0) c0 += (int)g.n;
+    if (c0 >= (int)g.n) c0 -= (int)g.n;
+    const int bb = c0 / g.N1;
+    ab = (uint32_t)(c0 - bb * g.N1) | ((uint32_t)bb << 16);
+    if (sizeof(T) == 4) roff = (T)((float)(uint64_t)(R >> 40) * 0x1p-24f);
+    else roff = (T)((double)(uint64_t)(R >> 11) * 0x1p-53);
 }
 
-// exp(2 pi i c) for a cycle count c reduced in FP64.
+// exp(2 pi i phase) for a fixed-point phase.
 template <typename T> struct Cis;
 
 template <> struct Cis<double> {
-    __device__ __forceinline__ static double2 of(double c) {
+    __device__ __forceinline__ static double2 of(u128 F) {
+        const double c = (double)(long long)(uint64_t)(F >> 64) * 0x1p-64;   // in [-1/2, 1/2)
         double s, co;
         sincospi(2.0 * c, &s, &co);
         return make_double2(co, s);
     }
 };
 
-// FP32 path: c is split as cf + dc (cf the nearest float of c - rint(c));
-// sincospif(2 cf) is corrected to first order in 2 pi dc (|dc| < 3e-8, the
-// neglected term is < 1e-14); everything after the FP64 reduction is FP32.
+// FP32 path: the phase c (in cycles, [-1/2, 1/2)) is split as cf + dc with cf
+// its nearest float; sincospif(2 cf) is corrected to first order in 2 pi dc
+// (|dc| < 3e-8, neglected term < 1e-14).
 template <> struct Cis<float> {
-    __device__ __forceinline__ static float2 of(double c) {
-        const double cr = c - rint(c);
-        const float cf = (float)cr;
-        const float dc = 6.2831853071795865f * (float)(cr - (double)cf);
-        float sf, co;
-        sincospif(2.0f * cf, &sf, &co);
-        return make_float2(fmaf(-dc, sf, co), fmaf(dc, co, sf));
+    __device__ __forceinline__ static float2 of(u128 F) {
+        const long long s = (long long)(uint64_t)(F >> 64);
+        const float sf = (float)s;
+        const long long back = (sf >= 9.2233720368547758e18f) ? 0x7fffffffffffffffll
+                                                               : (long long)sf;
+        const float cf = sf * 0x1p-64f;
+        const float dc = 6.2831853071795865f * ((float)(s - back) * 0x1p-64f);
+        float sn, co;
+        sincospif(2.0f * cf, &sn, &co);
+        return make_float2(fmaf(-dc, sn, co), fmaf(dc, co, sn));
     }
 };
 
+// Warp-aggregated atomicAdd of 1 to counter[key] (threads with equal keys
+// share one atomic); returns the old value plus the thread's rank among them.
+__device__ __forceinline__ int agg_increment(int *counter, int key, bool active)
+{
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1 - (int)lane) & mask;
+    int old = 0;
+    if (active) {
+        const int leader = __ffs(peers) - 1;
+        if ((int)lane == leader) old = atomicAdd(counter + key, __popc(peers));
+        old = __shfl_sync(peers, old, leader);
+        old += __popc(peers & ((1u << lane) - 1u));
+    }
+    return old;
+}
+
+// Frequencies of the transform, decomposed for frac_fixed (host-filled).
+struct PhaseArgs {
+    uint64_t df_m, f0_m;
+    int df_e, f0_e, f0_neg;
+    int64_t K0;
+};
+
 // ---------------------------------------------------------------------------
-// K1b: per-point records + bin histogram + YY reduction.  Phase reduction,
-// weights and the mean-subtracted data are FP64; strengths are stored in T.
+// K1b: per-point records + bin histogram + YY reduction.  Coordinates and
+// pre-phases come from the exact integer reduction; weights and the
+// mean-subtracted data are FP64; strengths are stored in T.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
-                         const double *__restrict__ dy, int64_t nd, double df, double fc_hi,
-                         double fc_lo, Geometry g, PointSet<T> px, PointSet<T> p2, int *hist,
-                         double *partials, unsigned int *counter, Stats *st, int *status)
+                         const double *__restrict__ dy, int64_t nd, PhaseArgs ph, Geometry g,
+                         PointSet<T> px, PointSet<T> p2, int *hist, double *partials,
+                         unsigned int *counter, Stats *st, int *status)
 {
     using V = Cplx<T>;
     __shared__ double sh[32];
     const double invW = st->invW;
     const double ybar = st->ybar;
     const double scale = st->scale;
-    const double n_d = (double)g.n;
     double syy = 0.0, sy2 = 0.0;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double tj = t[j], yj = y[j];
-        const double d = dy ? dy[j] : 1.0;
-        const double wh = rcp_fp64(d * d) * invW;
-        const double yc = yj - ybar;
-        const double a = wh * yc * scale;
-        syy += wh * yc * yc;
-        sy2 += wh * yj * yj;
-        // NUFFT coordinates in cycles: frac(df t) and frac(2 df t), exact product.
-        const double ph = frac_dd(df, 0.0, tj);
-        double ph2 = ph + ph;
-        ph2 -= floor(ph2);
-        uint32_t ab1, ab2;
-        double r1, r2;
-        split_cell(ph * n_d, g, ab1, r1);
-        split_cell(ph2 * n_d, g, ab2, r2);
-        // Pre-phase p = exp(2 pi i fc t) and p^2.
-        const double pc = frac_dd(fc_hi, fc_lo, tj);
-        double pc2 = pc + pc;
-        pc2 -= floor(pc2);
-        const V p = Cis<T>::of(pc);
-        const V q = Cis<T>::of(pc2);
-        const T at = (T)a, wt = (T)wh;
-        px.ab[j] = ab1;
-        px.roff[j] = (T)r1;
-        px.s[0][j] = mk2(at * p.x, at * p.y);
-        px.s[1][j] = mk2(wt * p.x, wt * p.y);
-        p2.ab[j] = ab2;
-        p2.roff[j] = (T)r2;
-        p2.s[0][j] = mk2(wt * q.x, wt * q.y);
-        atomicAdd(&hist[(ab1 & 0xFFFFu) >> g.logBA], 1);
-        atomicAdd(&hist[g.nbins + ((ab2 & 0xFFFFu) >> g.logBA)], 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < nd; j0 += stride) {
+        const int64_t j = j0 + threadIdx.x;
+        const bool act = j < nd;
+        uint32_t ab1 = 0, ab2 = 0;
+        if (act) {
+            const double tj = t[j], yj = y[j];
+            const double d = dy ? dy[j] : 1.0;
+            const double wh = rcp_fp64(d * d) * invW;
+            const double yc = yj - ybar;
+            const double wyc = wh * yc;
+            syy = fma(wyc, yc, syy);
+            sy2 = fma(wh * yj, yj, sy2);
+            const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);          // frac(df t)
+            const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj)
+                          + (u128)(uint64_t)ph.K0 * Fx;                   // frac(fc t)
+            T r1, r2;
+            split_fixed<T>(Fx, g, ab1, r1);
+            split_fixed<T>(Fx << 1, g, ab2, r2);
+            const V p = Cis<T>::of(Fc);
+            const V q = Cis<T>::of(Fc << 1);
+            const T at = (T)(wyc * scale), wt = (T)wh;
+            px.ab[j] = ab1;
+            px.roff[j] = r1;
+            px.s[0][j] = mk2(at * p.x, at * p.y);
+            px.s[1][j] = mk2(wt * p.x, wt * p.y);
+            p2.ab[j] = ab2;
+            p2.roff[j] = r2;
+            p2.s[0][j] = mk2(wt * q.x, wt * q.y);
+        }
+        agg_increment(hist, (int)((ab1 & 0xFFFFu) >> g.logBA), act);
+        agg_increment(hist, g.nbins + (int)((ab2 & 0xFFFFu) >> g.logBA), act);
     }
     double a = block_sum(syy, sh);
     double b = block_sum(sy2, sh);
@@ -242,12 +315,10 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
         partials[2 * blockIdx.x + 1] = b;
     }
     if (last_block(counter)) {
+        double r[2];
+        reduce_partials(partials, gridDim.x, 2, r, sh);
         if (threadIdx.x == 0) {
-            double YY = 0.0, Y2 = 0.0;
-            for (unsigned int i = 0; i < gridDim.x; ++i) {
-                YY += __ldcg(partials + 2 * i);
-                Y2 += __ldcg(partials + 2 * i + 1);
-            }
+            const double YY = r[0], Y2 = r[1];
             st->YY = YY * st->scale * st->scale;
             st->Y2 = Y2;
             // A constant series: variance zero up to the rounding of the mean.
@@ -298,19 +369,23 @@ template <typename T>
 __global__ void k_scatter(int64_t nd, Geometry g, PointSet<T> rx, PointSet<T> r2,
                           PointSet<T> sx, PointSet<T> s2, int *cursor)
 {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c1 = rx.ab[j];
-        const int d1 = atomicAdd(&cursor[(c1 & 0xFFFFu) >> g.logBA], 1);
-        sx.ab[d1] = c1;
-        sx.roff[d1] = rx.roff[j];
-        sx.s[0][d1] = rx.s[0][j];
-        sx.s[1][d1] = rx.s[1][j];
-        const uint32_t c2 = r2.ab[j];
-        const int d2 = atomicAdd(&cursor[g.nbins + ((c2 & 0xFFFFu) >> g.logBA)], 1);
-        s2.ab[d2] = c2;
-        s2.roff[d2] = r2.roff[j];
-        s2.s[0][d2] = r2.s[0][j];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < nd; j0 += stride) {
+        const int64_t j = j0 + threadIdx.x;
+        const bool act = j < nd;
+        const uint32_t c1 = act ? rx.ab[j] : 0u;
+        const uint32_t c2 = act ? r2.ab[j] : 0u;
+        const int d1 = agg_increment(cursor, (int)((c1 & 0xFFFFu) >> g.logBA), act);
+        const int d2 = agg_increment(cursor, g.nbins + (int)((c2 & 0xFFFFu) >> g.logBA), act);
+        if (act) {
+            sx.ab[d1] = c1;
+            sx.roff[d1] = rx.roff[j];
+            sx.s[0][d1] = rx.s[0][j];
+            sx.s[1][d1] = rx.s[1][j];
+            s2.ab[d2] = c2;
+            s2.roff[d2] = r2.roff[j];
+            s2.s[0][d2] = r2.s[0][j];
+        }
     }
 }
 
@@ -334,7 +409,7 @@ struct PassAArgs {
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
     const Cplx<T> *twA;    // stage twiddles, length N2
-    const int *revA;       // digit-reversal slots, length N2
+    const int *revA;       // frequency index of each output slot, length N2
     const Cplx<T> *tw4;    // four-step table (lo 4096, hi)
     Cplx<T> *H;
 };
@@ -353,16 +428,17 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = A.g;
     const int N1 = g.N1, N2 = g.N2, BA = g.BA;
+    const int Lp = padded_len(N2);
     const int nhi = (N2 + 63) >> 6;
-    V *buf = reinterpret_cast<V *>(smem_raw);
-    V *alo = buf + (size_t)BA * N2;        // W_n^{a dl}, dl < 64, per column
-    V *ahi = alo + BA * 64;                // W_n^{64 a dh}, per column
+    V *buf = reinterpret_cast<V *>(smem_raw);   // BA columns, padded layout
+    V *alo = buf + (size_t)BA * Lp;             // W_n^{a dl}, dl < 64, per column
+    V *ahi = alo + BA * 64;                     // W_n^{64 a dh}, per column
 
     const int grid = blockIdx.y;
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
 
-    for (int i = threadIdx.x; i < BA * N2; i += blockDim.x) buf[i] = mk2(T(0), T(0));
+    for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
     for (int i = threadIdx.x; i < BA * 64; i += blockDim.x) {
         const int col = i >> 6;
         alo[i] = tw4_root(A.tw4, (int64_t)(a0 + col) * (i & 63));
@@ -418,7 +494,7 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
             if (b >= N2) b -= N2;
             const T z = (roff - halfw + T(i)) * zscale;
             const T v = es_kernel(z, beta);
-            V *dst = buf + (size_t)(cs + u) * N2 + b;
+            V *dst = buf + (size_t)(cs + u) * Lp + pad16(b);
             atomicAdd(&dst->x, s.x * v);
             atomicAdd(&dst->y, s.y * v);
         }
@@ -426,16 +502,18 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     __syncthreads();
 
     // ---- column FFTs over b ----
-    fft_dif(buf, BA, N2, g.fa, A.twA);
+    fft_dif(buf, BA, Lp, g.fa, A.twA);
 
-    // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a] ----
-    V *H = A.H + (size_t)grid * (size_t)g.n;
-    for (int e = threadIdx.x; e < BA * N2; e += blockDim.x) {
-        const int col = e & (BA - 1);
-        const int d = e >> g.logBA;
-        const V v = buf[(size_t)col * N2 + __ldg(A.revA + d)];
-        const V tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
-        H[(size_t)d * N1 + a0 + col] = cmul(v, tw);
+    // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
+    V *H = A.H + (size_t)grid * (size_t)g.n + a0;
+    for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
+        const int d = __ldg(A.revA + pos);
+        const int sp = pad16(pos);
+        V *dst = H + (size_t)d * N1;
+        for (int col = 0; col < BA; ++col) {
+            const V tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
+            dst[col] = cmul(buf[(size_t)col * Lp + sp], tw);
+        }
     }
 }
 
@@ -602,16 +680,42 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = B.g;
     const int N1 = g.N1, N2 = g.N2;
-    V *buf = reinterpret_cast<V *>(smem_raw);
+    const int Lp = padded_len(N1);
+    V *buf = reinterpret_cast<V *>(smem_raw);   // 3 rows, padded layout
     const int d = blockIdx.x;
 
-    for (int gi = 0; gi < 3; ++gi) {
-        const V *src = B.H + (size_t)gi * (size_t)g.n + (size_t)d * N1;
-        for (int a = threadIdx.x; a < N1; a += blockDim.x) buf[(size_t)gi * N1 + a] = src[a];
+    // rows of H: N1 is a power of two >= 32, so pairs (2i, 2i+1) stay adjacent
+    // after padding; four 16-byte loads in flight per thread.
+    {
+        const int half = N1 >> 1;
+        for (int gi = 0; gi < 3; ++gi) {
+            const V *src = B.H + (size_t)gi * (size_t)g.n + (size_t)d * N1;
+            V *dst = buf + (size_t)gi * Lp;
+            for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
+                V v[8];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < half) {
+                        v[2 * u] = src[2 * i];
+                        v[2 * u + 1] = src[2 * i + 1];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < half) {
+                        const int sp = pad16(2 * i);
+                        dst[sp] = v[2 * u];
+                        dst[sp + 1] = v[2 * u + 1];
+                    }
+                }
+            }
+        }
     }
     __syncthreads();
 
-    fft_dif(buf, 3, N1, g.fb, B.twB);
+    fft_dif(buf, 3, Lp, g.fb, B.twB);
 
     const double YY = B.st->YY;
     ff YYf;
@@ -622,14 +726,14 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     const int64_t lo_end = B.nf - B.K0;    // k <  lo_end   -> k' = k >= 0
     const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
     const int c2 = (int)((hi_start - d + N2 - 1) / N2);
-    const int count = c1 + (N1 - c2);
-    for (int e = threadIdx.x; e < count; e += blockDim.x) {
-        const int c = (e < c1) ? e : (c2 + e - c1);
+    for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
+        const int c = __ldg(B.revB + pos);
+        if (c >= c1 && c < c2) continue;            // mode not requested
         const int64_t k = d + (int64_t)N2 * c;
-        const int64_t kp = (e < c1) ? k : k - n;
-        const int pos = __ldg(B.revB + c);
+        const int64_t kp = (c < c1) ? k : k - n;
+        const int sp = pad16(pos);
         const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
-        const V g1 = buf[pos], g2 = buf[N1 + pos], g3 = buf[2 * N1 + pos];
+        const V g1 = buf[sp], g2 = buf[Lp + sp], g3 = buf[2 * Lp + sp];
         const int64_t out = kp + B.K0;
         if (B.power) B.power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
         if (B.sums) {
@@ -671,12 +775,13 @@ size_t point_record_bytes()
 
 size_t passA_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * ((size_t)g.BA * g.N2 + (size_t)g.BA * 64 + (size_t)g.BA * ((g.N2 + 63) / 64));
+    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * 64 +
+                 (size_t)g.BA * ((g.N2 + 63) / 64));
 }
 
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * 3 * (size_t)g.N1;
+    return cx * 3 * (size_t)padded_len(g.N1);
 }
 
 template <typename T>
@@ -696,6 +801,17 @@ static PointSet<T> carve(void *base, int64_t max_nd)
     return p;
 }
 
+// x = +-m 2^e with m < 2^53, the exact decomposition of a finite double.
+static void decompose_host(double x, uint64_t &m, int &e, int &neg)
+{
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    neg = (int)(b >> 63);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    m = (b & 0xFFFFFFFFFFFFFull) | (ex ? (1ull << 52) : 0ull);
+    e = (ex ? ex : 1) - 1075;
+}
+
 template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_nd,
                             const ExecParams &p, int nred, cudaStream_t st, cudaEvent_t *ev)
@@ -709,8 +825,15 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     if (err != cudaSuccess) return err;
     k_stats<<<nred, 256, 0, st>>>(p.t, p.y, p.dy, p.nd, ws.partials, ws.counter, ws.stats,
                                   ws.status);
-    k_points<T><<<nred, 256, 0, st>>>(p.t, p.y, p.dy, p.nd, p.df, p.fc_hi, p.fc_lo, g, rx, r2,
-                                      ws.hist, ws.partials, ws.counter + 1, ws.stats, ws.status);
+    PhaseArgs ph;
+    {
+        int neg;
+        decompose_host(p.df, ph.df_m, ph.df_e, neg);
+        decompose_host(p.f0, ph.f0_m, ph.f0_e, ph.f0_neg);
+        ph.K0 = p.K0;
+    }
+    k_points<T><<<nred, 256, 0, st>>>(p.t, p.y, p.dy, p.nd, ph, g, rx, r2, ws.hist, ws.partials,
+                                      ws.counter + 1, ws.stats, ws.status);
     if (ev) cudaEventRecord(ev[1], st);
     k_scan<<<1, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart, ws.cursor);
     const int nsc = (int)((p.nd + 255) / 256 < 4096 ? (p.nd + 255) / 256 : 4096);
