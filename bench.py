@@ -220,22 +220,24 @@ def allreduce_max(x: float, pg, device) -> float:
 
 def oracle_sample(s, seconds: float, seed: int = 4242):
     """Time the FP64 oracle on seeded random frequencies of the workload; the
-    count is scaled from a short pilot so the sample takes about `seconds`."""
+    count is scaled from a short pilot so the sample takes about `seconds`.
+    Returns (k, P_oracle, elapsed_s, threads)."""
     import numpy as np
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
-    pilot = 16
+    pilot = 64
     k = rng.choice(s.nf, pilot, replace=False).astype(np.int64)
+    oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k[:16])      # thread start-up
     t0 = time.perf_counter()
     oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
     dt = time.perf_counter() - t0
     nk = int(max(pilot, min(s.nf, pilot * seconds / max(dt, 1e-6))))
-    k = rng.choice(s.nf, nk, replace=False).astype(np.int64)
+    k = np.sort(rng.choice(s.nf, nk, replace=False)).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    P = oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
     dt = time.perf_counter() - t0
-    return nk, dt, oracle.threads()
+    return k, P, dt, oracle.threads()
 
 
 # ------------------------------------------------------------------ reference arm
@@ -356,6 +358,8 @@ def run_ours(args):
     spread_fft_ms = avg["pass_a_spread_fft"] + avg["pass_b_fft_deconv_power"]
     spread_fft_bytes = alg["pass_a_spread_fft"] + alg["pass_b_fft_deconv_power"]
 
+    P_gpu = out.cpu().numpy()
+
     # -- end to end through the C-ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -405,11 +409,17 @@ def run_ours(args):
         return 0
 
     cpu = None
+    accuracy = None
     if not args.no_cpu_baseline and world == 1:
-        nk, dt, cores = oracle_sample(s, args.cpu_seconds)
+        k, P_o, dt, cores = oracle_sample(s, args.cpu_seconds)
+        nk = len(k)
         cpu = {"value": (nk / s.nf) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nk} seeded random frequencies of the {s.nf}-frequency grid, all "
                          f"{s.nd} points, FP64 direct sums ({dt:.1f} s)"}
+        P_g = P_gpu[k]
+        accuracy = {"rel_l2": float(np.linalg.norm(P_g - P_o) / np.linalg.norm(P_o)),
+                    "max_abs": float(np.max(np.abs(P_g - P_o))),
+                    "frequencies": nk, "against": "FP64 oracle (direct sums)"}
 
     ms_sorted = sorted(step_ms)
     line = {
@@ -429,7 +439,7 @@ def run_ours(args):
                        "achieved_gbs": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9,
                        "frac_of_peak": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9 / peak},
         "stage_ms": avg, "stage_gbs": kern_gbs,
-        "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
+        "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
         "gpu_launches": 6 * args.steps,
         "clocks": clk, "wall_s": wall,
     }

@@ -7,9 +7,11 @@
 // sequence of radix-R stages, R in {3, 5} first and then {16, 8, 4, 2}, each
 // butterfly an R-point DFT in registers.  Every butterfly reads and writes the
 // same R slots, so one buffer suffices and a stage needs only a barrier at its
-// end.  The output is left in digit-reversed order; a per-length table gives
-// the frequency index each slot holds.  Twiddles exp(2 pi i j k / Ls) come from
-// per-stage tables (row j holds k = 1 .. R-1), exactly rounded from FP64.
+// end.  The output is left in digit-reversed order; slot_to_freq() gives the
+// frequency index each slot holds.  Twiddles exp(2 pi i j k / Ls) =
+// W_L^(j k L/Ls) come from a two-level root table of W_L = exp(2 pi i / L) held
+// in shared memory (W_L^p = lo[p % 64] * hi[p / 64], both exactly rounded from
+// FP64), so a stage's twiddles never leave the SM.
 #pragma once
 
 #include "ls_internal.cuh"
@@ -154,12 +156,45 @@ __device__ __forceinline__ int small_div(int a, int b, float inv_b)
     return q;
 }
 
-template <typename V> __device__ __forceinline__ V ldg_c(const V *p) { return __ldg(p); }
+// exp(2 pi i p / L) from the two-level root table (lo: 64 entries, hi: L/64).
+template <typename V>
+__device__ __forceinline__ V root_tw(const V *roots, int p)
+{
+    return cmul(roots[p & 63], roots[64 + (p >> 6)]);
+}
+
+// Load the two-level root table of length L into shared memory (no barrier).
+template <typename V>
+__device__ __forceinline__ void load_roots(V *dst, const V *__restrict__ src, int L)
+{
+    const int cnt = 64 + ((L + 63) >> 6);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+// Frequency index held by output slot pos of fft_dif: pos = sum_s d_s m_s
+// with m_s = L / (R_0 ... R_s); the index is sum_s d_s R_0 ... R_{s-1}.
+__device__ __forceinline__ int slot_to_freq(int pos, const FftPlan &fp)
+{
+    int c = 0, mult = 1;
+    for (int s = 0; s < fp.nstages; ++s) {
+        const FftStage &st = fp.st[s];
+        int dgt;
+        if (st.shift >= 0) {
+            dgt = pos >> st.shift;
+        } else {
+            dgt = small_div(pos, st.m, st.inv_m);
+        }
+        pos -= dgt * st.m;
+        c += dgt * mult;
+        mult *= st.R;
+    }
+    return c;
+}
 
 // One DIF stage of radix R over `ncol` transforms (stride colstride).
 template <int R, typename V>
 __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const FftStage &st,
-                                          const V *__restrict__ tw)
+                                          const V *roots, int L)
 {
     const int nb = st.nb;
     const int total = ncol * nb;
@@ -184,10 +219,10 @@ __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = p[pad16(base + r * m)];
         Dft<R>::run(v);
-        if (st.tw >= 0 && j != 0) {
-            const V *t = tw + st.tw + j * (R - 1);
+        if (j != 0) {
+            const int step = j * (L / st.Ls);      // W_Ls^(j k) = W_L^(k step)
 #pragma unroll
-            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ldg_c(t + k - 1));
+            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], root_tw(roots, k * step));
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) p[pad16(base + r * m)] = v[r];
@@ -198,18 +233,17 @@ __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const
 // (padded layout, columns colstride apart).  Ends with a barrier; output in
 // digit-reversed order: slot pos holds frequency index inv_rev[pos].
 template <typename V>
-__device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp,
-                        const V *__restrict__ tw)
+__device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots)
 {
     for (int s = 0; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
-        case 16: dif_stage<16>(buf, ncol, colstride, st, tw); break;
-        case 8: dif_stage<8>(buf, ncol, colstride, st, tw); break;
-        case 4: dif_stage<4>(buf, ncol, colstride, st, tw); break;
-        case 5: dif_stage<5>(buf, ncol, colstride, st, tw); break;
-        case 3: dif_stage<3>(buf, ncol, colstride, st, tw); break;
-        default: dif_stage<2>(buf, ncol, colstride, st, tw); break;
+        case 16: dif_stage<16>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 8: dif_stage<8>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 4: dif_stage<4>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 5: dif_stage<5>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 3: dif_stage<3>(buf, ncol, colstride, st, roots, fp.L); break;
+        default: dif_stage<2>(buf, ncol, colstride, st, roots, fp.L); break;
         }
         __syncthreads();
     }

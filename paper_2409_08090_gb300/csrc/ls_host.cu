@@ -251,17 +251,14 @@ void plan_free(ls_plan_s *p)
     p->allocations.clear();
 }
 
-// Stage descriptors, twiddle rows (exp(2 pi i j k / Ls), row j, k = 1..R-1,
-// exactly rounded from FP64) and, per output slot, the frequency index it
-// holds after a length-L DIF FFT (the inverse digit reversal).
-template <typename T>
-bool build_fft(int L, FftPlan *fp, std::vector<T> &tw, std::vector<int> &rev)
+// Stage descriptors of a length-L DIF FFT (radix schedule, sub-lengths and
+// the constants for exact small divisions).
+bool build_fft(int L, FftPlan *fp)
 {
     std::vector<int> rad;
     if (!radix_schedule(L, rad)) return false;
     fp->L = L;
     fp->nstages = (int)rad.size();
-    tw.clear();
     int Ls = L;
     for (int s = 0; s < fp->nstages; ++s) {
         FftStage &st = fp->st[s];
@@ -273,33 +270,8 @@ bool build_fft(int L, FftPlan *fp, std::vector<T> &tw, std::vector<int> &rev)
         st.shift = ilog2_exact(st.m);
         st.inv_m = 1.0f / (float)st.m;
         st.inv_nb = 1.0f / (float)st.nb;
-        if (st.m > 1) {
-            st.tw = (int)(tw.size() / 2);
-            for (int j = 0; j < st.m; ++j) {
-                for (int k = 1; k < R; ++k) {
-                    double re, im;
-                    root_of_unity((int64_t)j * k, Ls, &re, &im);
-                    tw.push_back((T)re);
-                    tw.push_back((T)im);
-                }
-            }
-        } else {
-            st.tw = -1;
-        }
         Ls = st.m;
     }
-    rev.assign(L, 0);
-    for (int k = 0; k < L; ++k) {
-        int pos = 0, m = L, kk = k;
-        for (int s = 0; s < fp->nstages; ++s) {
-            const int R = rad[s];
-            m /= R;
-            pos += (kk % R) * m;
-            kk /= R;
-        }
-        rev[pos] = k;   // slot pos holds frequency index k
-    }
-    if (tw.empty()) { tw.push_back(T(1)); tw.push_back(T(0)); }
     return true;
 }
 
@@ -316,18 +288,13 @@ ls_status upload_tables(ls_plan_s *p)
 {
     Geometry &g = p->g;
     std::vector<T> tA, tB, t4;
-    std::vector<int> rA, rB;
-    if (!build_fft<T>(g.N2, &g.fa, tA, rA) || !build_fft<T>(g.N1, &g.fb, tB, rB))
-        return LS_ERR_UNSUPPORTED;
+    if (!build_fft(g.N2, &g.fa) || !build_fft(g.N1, &g.fb)) return LS_ERR_UNSUPPORTED;
+    fill_root_table(tA, g.N2, 6);
+    fill_root_table(tB, g.N1, 6);
     fill_root_table(t4, g.n, kTw4Bits);
     ls_status s;
-    void *v;
     if ((s = upload<T>(p, &p->ws.twA, tA.data(), tA.size() * sizeof(T))) != LS_OK) return s;
     if ((s = upload<T>(p, &p->ws.twB, tB.data(), tB.size() * sizeof(T))) != LS_OK) return s;
-    if ((s = upload<T>(p, &v, rA.data(), rA.size() * sizeof(int))) != LS_OK) return s;
-    p->ws.revA = static_cast<int *>(v);
-    if ((s = upload<T>(p, &v, rB.data(), rB.size() * sizeof(int))) != LS_OK) return s;
-    p->ws.revB = static_cast<int *>(v);
     if ((s = upload<T>(p, &p->ws.tw4, t4.data(), t4.size() * sizeof(T))) != LS_OK) return s;
 
     // deconvolution table 1/phi_hat(k'), k' = 0 .. nf/2

@@ -30,7 +30,6 @@ struct FftStage {
     int shift;      // log2(m) if m is a power of two, else -1
     float inv_m;    // 1/m and 1/nb for small exact divisions
     float inv_nb;
-    int tw;         // offset of this stage's twiddle rows (row j: k = 1..R-1), -1 if none
 };
 
 struct FftPlan {
@@ -85,10 +84,8 @@ struct Workspace {
     unsigned int *counter;// last-block tickets (2)
     Stats *stats;
     int *status;          // device status word
-    void *twA;            // stage twiddle rows for length N2
-    void *twB;            // stage twiddle rows for length N1
-    int *revA;            // frequency index held by each output slot, length N2
-    int *revB;            // frequency index held by each output slot, length N1
+    void *twA;            // two-level root table for length N2: lo (64) then hi (ceil(N2/64))
+    void *twB;            // two-level root table for length N1
     void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
 };

@@ -408,8 +408,7 @@ struct PassAArgs {
     Geometry g;
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
-    const Cplx<T> *twA;    // stage twiddles, length N2
-    const int *revA;       // frequency index of each output slot, length N2
+    const Cplx<T> *twA;    // two-level root table, length N2
     const Cplx<T> *tw4;    // four-step table (lo 4096, hi)
     Cplx<T> *H;
 };
@@ -433,12 +432,14 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     V *buf = reinterpret_cast<V *>(smem_raw);   // BA columns, padded layout
     V *alo = buf + (size_t)BA * Lp;             // W_n^{a dl}, dl < 64, per column
     V *ahi = alo + BA * 64;                     // W_n^{64 a dh}, per column
+    V *roots = ahi + BA * nhi;                  // two-level root table of length N2
 
     const int grid = blockIdx.y;
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
 
     for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
+    load_roots(roots, A.twA, N2);
     for (int i = threadIdx.x; i < BA * 64; i += blockDim.x) {
         const int col = i >> 6;
         alo[i] = tw4_root(A.tw4, (int64_t)(a0 + col) * (i & 63));
@@ -502,12 +503,12 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     __syncthreads();
 
     // ---- column FFTs over b ----
-    fft_dif(buf, BA, Lp, g.fa, A.twA);
+    fft_dif(buf, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     V *H = A.H + (size_t)grid * (size_t)g.n + a0;
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
-        const int d = __ldg(A.revA + pos);
+        const int d = slot_to_freq(pos, g.fa);
         const int sp = pad16(pos);
         V *dst = H + (size_t)d * N1;
         for (int col = 0; col < BA; ++col) {
@@ -609,15 +610,19 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y)
     const ff p = two_prod(x.hi, y.hi);
     return fast_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
 }
+// Sum of two double-float values of equal sign (no cancellation possible).
+__device__ __forceinline__ ff ff_add_same_sign(ff x, ff y)
+{
+    const ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+// x / y with a float reciprocal and one correction: ~2^-46 relative.
 __device__ __forceinline__ ff ff_div(ff x, ff y)
 {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float ry = __frcp_rn(y.hi);
+    const float q1 = x.hi * ry;
     const ff r = ff_add(x, ff_neg(ff_mul(y, ff{q1, 0.f})));
-    const float q2 = __fdiv_rn(r.hi, y.hi);
-    const ff r2 = ff_add(r, ff_neg(ff_mul(y, ff{q2, 0.f})));
-    const float q3 = __fdiv_rn(r2.hi, y.hi);
-    const ff q = fast_two_sum(q1, q2);
-    return ff_add(q, ff{q3, 0.f});
+    return fast_two_sum(q1, r.hi * ry);
 }
 
 // FP32 path: the sums arrive as FP32 values (exact inputs here); the ratio is
@@ -630,10 +635,12 @@ __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float
     const ff SS = ff_add(two_sum(0.5f, -0.5f * C2), ff_neg(two_prod(S, S)));
     const ff CS = ff_add(ff{0.5f * S2, 0.f}, ff_neg(two_prod(C, S)));
     const ff D = ff_add(ff_mul(CC, SS), ff_neg(ff_mul(CS, CS)));
-    if (!(D.hi > 1e-12f * (CC.hi * CC.hi + SS.hi * SS.hi) && D.hi > 1e-30f))
+    if (!(D.hi > 1e-12f * (CC.hi * CC.hi + SS.hi * SS.hi) && D.hi > 1e-30f && CC.hi > 0.f &&
+          SS.hi > 0.f))
         return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd);
     const ff ChSh = two_prod(Ch, Sh);
-    const ff N = ff_add(ff_add(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
+    // CC, SS > 0 here, so the first two terms add without cancellation.
+    const ff N = ff_add(ff_add_same_sign(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
                         ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, CS)));
     const ff P = ff_div(N, ff_mul(D, YY));
     return (double)P.hi + (double)P.lo;
@@ -646,8 +653,7 @@ __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float
 template <typename T>
 struct PassBArgs {
     Geometry g;
-    const Cplx<T> *twB;
-    const int *revB;
+    const Cplx<T> *twB;    // two-level root table, length N1
     const Cplx<T> *H;
     const T *deconv;       // 1/phi_hat(|k'|)
     const Stats *st;
@@ -682,7 +688,9 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     const int N1 = g.N1, N2 = g.N2;
     const int Lp = padded_len(N1);
     V *buf = reinterpret_cast<V *>(smem_raw);   // 3 rows, padded layout
+    V *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
     const int d = blockIdx.x;
+    load_roots(roots, B.twB, N1);
 
     // rows of H: N1 is a power of two >= 32, so pairs (2i, 2i+1) stay adjacent
     // after padding; four 16-byte loads in flight per thread.
@@ -715,7 +723,7 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     }
     __syncthreads();
 
-    fft_dif(buf, 3, Lp, g.fb, B.twB);
+    fft_dif(buf, 3, Lp, g.fb, roots);
 
     const double YY = B.st->YY;
     ff YYf;
@@ -727,7 +735,7 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
     const int c2 = (int)((hi_start - d + N2 - 1) / N2);
     for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
-        const int c = __ldg(B.revB + pos);
+        const int c = slot_to_freq(pos, g.fb);
         if (c >= c1 && c < c2) continue;            // mode not requested
         const int64_t k = d + (int64_t)N2 * c;
         const int64_t kp = (c < c1) ? k : k - n;
@@ -775,13 +783,13 @@ size_t point_record_bytes()
 
 size_t passA_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * 64 +
-                 (size_t)g.BA * ((g.N2 + 63) / 64));
+    const size_t nhi = (size_t)(g.N2 + 63) / 64;
+    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * (64 + nhi) + 64 + nhi);
 }
 
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * 3 * (size_t)padded_len(g.N1);
+    return cx * (3 * (size_t)padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64);
 }
 
 template <typename T>
@@ -846,7 +854,6 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     A.p2 = s2;
     A.binstart = ws.binstart;
     A.twA = static_cast<const Cplx<T> *>(ws.twA);
-    A.revA = ws.revA;
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
@@ -858,7 +865,6 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     PassBArgs<T> B;
     B.g = g;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
-    B.revB = ws.revB;
     B.H = static_cast<const Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv);
     B.st = ws.stats;
