@@ -191,20 +191,16 @@ __device__ __forceinline__ int slot_to_freq(int pos, const FftPlan &fp)
     return c;
 }
 
-// One DIF stage of radix R over `ncol` transforms (stride colstride).
-template <int R, typename V>
-__device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const FftStage &st,
+// One DIF stage of radix R over NC transforms (stride colstride) processed
+// together: a thread takes butterfly (q, j) of every transform, so the NC
+// groups of loads are in flight at once and each twiddle is formed once.
+template <int R, int NC, typename V>
+__device__ __forceinline__ void dif_stage(V *buf, int colstride, const FftStage &st,
                                           const V *roots, int L)
 {
-    const int nb = st.nb;
-    const int total = ncol * nb;
     const int m = st.m;
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int col = 0, bi = e;
-        if (ncol > 1) {
-            col = small_div(e, nb, st.inv_nb);
-            bi = e - col * nb;
-        }
+    const int tmul = L / st.Ls;
+    for (int bi = threadIdx.x; bi < st.nb; bi += blockDim.x) {
         int q, j;
         if (st.shift >= 0) {
             q = bi >> st.shift;
@@ -213,37 +209,61 @@ __device__ __forceinline__ void dif_stage(V *buf, int ncol, int colstride, const
             q = small_div(bi, m, st.inv_m);
             j = bi - q * m;
         }
-        V *p = buf + col * colstride;
         const int base = q * st.Ls + j;
-        V v[R];
+        V v[NC][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = p[pad16(base + r * m)];
-        Dft<R>::run(v);
-        if (j != 0) {
-            const int step = j * (L / st.Ls);      // W_Ls^(j k) = W_L^(k step)
+        for (int c = 0; c < NC; ++c) {
 #pragma unroll
-            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], root_tw(roots, k * step));
+            for (int r = 0; r < R; ++r) v[c][r] = buf[c * colstride + pad16(base + r * m)];
         }
 #pragma unroll
-        for (int r = 0; r < R; ++r) p[pad16(base + r * m)] = v[r];
+        for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
+        if (j != 0) {
+            const int step = j * tmul;             // W_Ls^(j k) = W_L^(k step)
+#pragma unroll
+            for (int k = 1; k < R; ++k) {
+                const V w = root_tw(roots, k * step);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[c * colstride + pad16(base + r * m)] = v[c][r];
+        }
     }
 }
 
+// One stage over `ncol` transforms, G at a time (G = 1 for the remainder).
+template <int R, int G, typename V>
+__device__ __forceinline__ void dif_stage_cols(V *buf, int ncol, int colstride, const FftStage &st,
+                                               const V *roots, int L)
+{
+    int c0 = 0;
+    if (G > 1) {
+        for (; c0 + G <= ncol; c0 += G) dif_stage<R, G>(buf + c0 * colstride, colstride, st, roots, L);
+    }
+    for (; c0 < ncol; ++c0) dif_stage<R, 1>(buf + c0 * colstride, colstride, st, roots, L);
+}
+
 // In-place DIF FFT of `ncol` transforms of length fp.L in shared memory
-// (padded layout, columns colstride apart).  Ends with a barrier; output in
-// digit-reversed order: slot pos holds frequency index inv_rev[pos].
-template <typename V>
+// (padded layout, columns colstride apart), up to NC of them per thread at a
+// time (at most 2 for radix 16, to stay within 128 registers in FP32).
+// Ends with a barrier; output in digit-reversed order (see slot_to_freq).
+template <int NC, typename V>
 __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots)
 {
+    constexpr int NC16 = NC < 2 ? NC : 2;
     for (int s = 0; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
-        case 16: dif_stage<16>(buf, ncol, colstride, st, roots, fp.L); break;
-        case 8: dif_stage<8>(buf, ncol, colstride, st, roots, fp.L); break;
-        case 4: dif_stage<4>(buf, ncol, colstride, st, roots, fp.L); break;
-        case 5: dif_stage<5>(buf, ncol, colstride, st, roots, fp.L); break;
-        case 3: dif_stage<3>(buf, ncol, colstride, st, roots, fp.L); break;
-        default: dif_stage<2>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 16: dif_stage_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 8: dif_stage_cols<8, NC>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 4: dif_stage_cols<4, NC>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 5: dif_stage_cols<5, NC>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 3: dif_stage_cols<3, NC>(buf, ncol, colstride, st, roots, fp.L); break;
+        default: dif_stage_cols<2, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         }
         __syncthreads();
     }

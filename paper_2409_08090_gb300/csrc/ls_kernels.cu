@@ -421,7 +421,7 @@ __device__ __forceinline__ T es_kernel(T z, T beta)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
+__global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 {
     using V = Cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -503,7 +503,8 @@ __global__ void __launch_bounds__(kThreadsA) k_passA(PassAArgs<T> A)
     __syncthreads();
 
     // ---- column FFTs over b ----
-    fft_dif(buf, BA, Lp, g.fa, roots);
+    if (sizeof(T) == 4 && (BA & 1) == 0) fft_dif<2>(buf, BA, Lp, g.fa, roots);
+    else fft_dif<1>(buf, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     V *H = A.H + (size_t)grid * (size_t)g.n + a0;
@@ -680,7 +681,7 @@ template <> struct PowerOut<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
+__global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
 {
     using V = Cplx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -723,7 +724,8 @@ __global__ void __launch_bounds__(kThreadsB) k_passB(PassBArgs<T> B)
     }
     __syncthreads();
 
-    fft_dif(buf, 3, Lp, g.fb, roots);
+    if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
+    else fft_dif<1>(buf, 3, Lp, g.fb, roots);
 
     const double YY = B.st->YY;
     ff YYf;
