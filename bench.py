@@ -62,9 +62,9 @@ def parse_args():
 def workload(name: str, rank: int):
     from paper_2409_08090_gb300 import workloads as W
     if name == "single_medium":
-        s = W.single_large(seed=W.BASE_SEED + 1 + 1000 * rank, nd=300_000, nf=4_000_000)
-        desc = ("single_medium (profiling size): Nd=3e5 over [0,3650) d with seasonal gaps; "
-                "Nf=4e6, f0=1/3650, df=1/18250")
+        s = W.single_large(seed=W.BASE_SEED + 1 + 1000 * rank, nd=250_000, nf=3_000_000)
+        desc = ("single_medium (profiling size): Nd=2.5e5 over [0,3650) d with seasonal gaps; "
+                "Nf=3e6, f0=1/3650, df=1/18250")
         return s, desc
     if name == "single_small":
         s = W.single_small(seed=W.BASE_SEED + 1000 * rank)

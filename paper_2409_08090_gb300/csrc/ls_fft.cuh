@@ -191,6 +191,21 @@ __device__ __forceinline__ int slot_to_freq(int pos, const FftPlan &fp)
     return c;
 }
 
+// Frequency index of slot pos with the per-block table D[i] =
+// slot_to_freq(i * Rlast): the last stage's digit is pos mod Rlast and
+// contributes (pos mod Rlast) * L / Rlast.
+__device__ __forceinline__ int slot_freq_tab(int pos, const int *D, const FftPlan &fp)
+{
+    return D[pos >> fp.logRlast] + (pos & (fp.Rlast - 1)) * (fp.L >> fp.logRlast);
+}
+
+// Fill D (L / Rlast entries) in shared memory (no barrier).
+__device__ __forceinline__ void fill_slot_table(int *D, const FftPlan &fp)
+{
+    const int cnt = fp.L >> fp.logRlast;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) D[i] = slot_to_freq(i << fp.logRlast, fp);
+}
+
 // One DIF stage of radix R over NC transforms (stride colstride) processed
 // together: a thread takes butterfly (q, j) of every transform, so the NC
 // groups of loads are in flight at once and each twiddle is formed once.
@@ -210,11 +225,15 @@ __device__ __forceinline__ void dif_stage(V *buf, int colstride, const FftStage 
             j = bi - q * m;
         }
         const int base = q * st.Ls + j;
+        const int pb = pad16(base);
+        int off[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) off[r] = st.lin ? pb + st.off[r] : pad16(base + r * m);
         V v[NC][R];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[c][r] = buf[c * colstride + pad16(base + r * m)];
+            for (int r = 0; r < R; ++r) v[c][r] = buf[c * colstride + off[r]];
         }
 #pragma unroll
         for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
@@ -230,7 +249,7 @@ __device__ __forceinline__ void dif_stage(V *buf, int colstride, const FftStage 
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[c * colstride + pad16(base + r * m)] = v[c][r];
+            for (int r = 0; r < R; ++r) buf[c * colstride + off[r]] = v[c][r];
         }
     }
 }

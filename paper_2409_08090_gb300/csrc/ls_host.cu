@@ -270,9 +270,22 @@ bool build_fft(int L, FftPlan *fp)
         st.shift = ilog2_exact(st.m);
         st.inv_m = 1.0f / (float)st.m;
         st.inv_nb = 1.0f / (float)st.nb;
+        // padded-slot offsets: linear in the butterfly base when the same
+        // off[r] works for every (q, j) of the stage (checked exhaustively)
+        auto pad = [](int i) { return i + (i >> 4); };
+        st.lin = R <= 16 ? 1 : 0;
+        for (int r = 0; r < R && r < 16; ++r) st.off[r] = pad(r * st.m);
+        for (int q = 0; q < L / Ls && st.lin; ++q)
+            for (int j = 0; j < st.m && st.lin; ++j) {
+                const int base = q * Ls + j;
+                for (int r = 0; r < R; ++r)
+                    if (pad(base + r * st.m) - pad(base) != st.off[r]) { st.lin = 0; break; }
+            }
         Ls = st.m;
     }
-    return true;
+    fp->Rlast = rad.back();
+    fp->logRlast = ilog2_exact(fp->Rlast);
+    return fp->logRlast >= 0;
 }
 
 template <typename T>

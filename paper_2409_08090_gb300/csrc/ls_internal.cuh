@@ -9,7 +9,7 @@
 
 namespace nls {
 
-constexpr int kMaxStages = 16;    // stages of one sub-FFT
+constexpr int kMaxStages = 8;     // stages of one sub-FFT
 constexpr int kTw4Bits = 12;      // four-step twiddle table split: W^p = lo[p % 4096] * hi[p / 4096]
 constexpr int kThreadsA = 256;
 constexpr int kThreadsB = 256;
@@ -30,11 +30,15 @@ struct FftStage {
     int shift;      // log2(m) if m is a power of two, else -1
     float inv_m;    // 1/m and 1/nb for small exact divisions
     float inv_nb;
+    int lin;        // 1: slot of element base + r*m is pad16(base) + off[r] for every butterfly
+    int off[16];
 };
 
 struct FftPlan {
     int L;
     int nstages;
+    int Rlast;      // radix of the last stage (a power of two)
+    int logRlast;
     FftStage st[kMaxStages];
 };
 

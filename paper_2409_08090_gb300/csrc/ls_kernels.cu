@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     V *alo = buf + (size_t)BA * Lp;             // W_n^{a dl}, dl < 64, per column
     V *ahi = alo + BA * 64;                     // W_n^{64 a dh}, per column
     V *roots = ahi + BA * nhi;                  // two-level root table of length N2
+    int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
     const int grid = blockIdx.y;
     const int blk = blockIdx.x;
@@ -440,6 +441,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 
     for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
     load_roots(roots, A.twA, N2);
+    fill_slot_table(dtab, g.fa);
     for (int i = threadIdx.x; i < BA * 64; i += blockDim.x) {
         const int col = i >> 6;
         alo[i] = tw4_root(A.tw4, (int64_t)(a0 + col) * (i & 63));
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     V *H = A.H + (size_t)grid * (size_t)g.n + a0;
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
-        const int d = slot_to_freq(pos, g.fa);
+        const int d = slot_freq_tab(pos, dtab, g.fa);
         const int sp = pad16(pos);
         V *dst = H + (size_t)d * N1;
         for (int col = 0; col < BA; ++col) {
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 
 // Explicit tau rotation (FP64), used for a nearly singular M (all phases equal
 // mod pi): a vanishing CC_tau or SS_tau term is dropped.
-__device__ double ls_power_tau(double Ch, double Sh, double C, double S, double C2, double S2,
+__device__ __noinline__ double ls_power_tau(double Ch, double Sh, double C, double S, double C2, double S2,
                                double YY)
 {
     const double num = S2 - 2.0 * C * S;
@@ -690,8 +692,10 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     const int Lp = padded_len(N1);
     V *buf = reinterpret_cast<V *>(smem_raw);   // 3 rows, padded layout
     V *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
+    int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
     load_roots(roots, B.twB, N1);
+    fill_slot_table(dtab, g.fb);
 
     // rows of H: N1 is a power of two >= 32, so pairs (2i, 2i+1) stay adjacent
     // after padding; four 16-byte loads in flight per thread.
@@ -737,7 +741,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
     const int c2 = (int)((hi_start - d + N2 - 1) / N2);
     for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
-        const int c = slot_to_freq(pos, g.fb);
+        const int c = slot_freq_tab(pos, dtab, g.fb);
         if (c >= c1 && c < c2) continue;            // mode not requested
         const int64_t k = d + (int64_t)N2 * c;
         const int64_t kp = (c < c1) ? k : k - n;
@@ -786,12 +790,14 @@ size_t point_record_bytes()
 size_t passA_smem_bytes(const Geometry &g, size_t cx)
 {
     const size_t nhi = (size_t)(g.N2 + 63) / 64;
-    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * (64 + nhi) + 64 + nhi);
+    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * (64 + nhi) + 64 + nhi) +
+           sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
 }
 
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
 {
-    return cx * (3 * (size_t)padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64);
+    return cx * (3 * (size_t)padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64) +
+           sizeof(int) * (size_t)(g.N1 / g.fb.Rlast);
 }
 
 template <typename T>
