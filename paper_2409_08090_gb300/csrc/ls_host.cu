@@ -65,17 +65,21 @@ int ilog2_exact(int64_t x)
     return ((int64_t)1 << k) == x ? k : -1;
 }
 
-// Radix schedule of a sub-FFT of length L = c 2^k (c = 3^a 5^b): the odd
-// radices first, then 16s, then one stage of 8, 4 or 2.
+// Radix schedule of a sub-FFT of length L = c 2^k (c = 3^a 5^b, k >= 1): the
+// odd radices first, then one stage of 8, 4 or 2 for k mod 4, then 16s, so
+// the last stage is a power of two (16 whenever k >= 4).
 bool radix_schedule(int L, std::vector<int> &rad)
 {
     rad.clear();
     int x = L;
     while (x % 3 == 0) { rad.push_back(3); x /= 3; }
     while (x % 5 == 0) { rad.push_back(5); x /= 5; }
-    while (x % 16 == 0) { rad.push_back(16); x /= 16; }
-    if (x == 8 || x == 4 || x == 2) { rad.push_back(x); x = 1; }
-    return x == 1 && (int)rad.size() <= kMaxStages;
+    int k = 0;
+    while ((x >> k) > 1) ++k;
+    if ((1 << k) != x || k == 0) return false;
+    if (k % 4) rad.push_back(1 << (k % 4));
+    for (int i = 0; i < k / 4; ++i) rad.push_back(16);
+    return (int)rad.size() <= kMaxStages;
 }
 
 // ES kernel width and shape for tolerance eps (upsampling factor 2): the
@@ -96,7 +100,7 @@ void es_params(double eps, int *w, double *beta)
 // Fine grid: the smallest n = c 2^k >= max(2 nf, 2 w, 64), c in the odd
 // 5-smooth set {1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125}, that splits as
 // n = N1 * N2 with N1 = 2^k1 a power of two in [kMinN1, n1max] and
-// N2 = n / N1 <= n2max (the odd factor lives in N2); among the splits the
+// N2 = n / N1 <= n2max even (the odd factor lives in N2); among the splits the
 // most balanced one is taken.
 ls_status choose_grid(int64_t nf, int w, int prec, int64_t *n_out, int *n1_out, int *n2_out)
 {
@@ -119,7 +123,7 @@ ls_status choose_grid(int64_t nf, int w, int prec, int64_t *n_out, int *n1_out, 
                 const int64_t N1 = (int64_t)1 << k1;
                 if (n % N1) break;
                 const int64_t N2 = n / N1;
-                if (N2 > n2max || N2 < 2) continue;
+                if (N2 > n2max || N2 < 2 || (N2 & 1)) continue;
                 const double b = fabs(log((double)N1) - log((double)N2));
                 if (b < bal) { bal = b; pick = (int)N1; }
             }

@@ -71,7 +71,7 @@ def test_choose_params(nf, eps, prec, w, n):
     # split limits of the two passes; N1 a power of two
     assert 32 <= p["n1"] <= (4096 if prec == 1 else 2048)
     assert p["n1"] & (p["n1"] - 1) == 0
-    assert p["n2"] <= (25600 if prec == 1 else 12800)
+    assert p["n2"] <= (25600 if prec == 1 else 12800) and p["n2"] % 2 == 0
 
 
 def test_choose_params_rejects():
@@ -92,7 +92,6 @@ def test_grid_sizes_are_minimal_admissible():
         nmin = max(2 * nf, 2 * p["width"], 64)
         assert n >= nmin and _is_allowed(n)
         # no admissible size in [nmin, n): n = c 2^k splits as N1 = 2^k1 >= 32
-        # (a power of two) times N2 >= 2, so k >= 5 and c 2^(k-5) >= 2
-        smaller = [c * 2 ** k for c in ODD for k in range(5, 40)
-                   if nmin <= c * 2 ** k < n and c * 2 ** (k - 5) >= 2]
+        # (a power of two) times an even N2, so k >= 6
+        smaller = [c * 2 ** k for c in ODD for k in range(6, 40) if nmin <= c * 2 ** k < n]
         assert not smaller, (nf, n, smaller[:3])
