@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--upsampling", type=float, default=0.0,
+                    help="fine-grid upsampling: 0 (plan chooses), 2.0 or 1.5")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -303,7 +305,7 @@ def run_ours(args):
 
     s, desc = workload(args.workload, rank)
     eps = eps_for(args.precision)
-    plan = nl.Plan(s.nd, s.nf, eps, args.precision, device=local)
+    plan = nl.Plan(s.nd, s.nf, eps, args.precision, device=local, upsampling=args.upsampling)
     info = plan.info
     t = torch.tensor(s.t, dtype=torch.float64, device=device)
     y = torch.tensor(s.y, dtype=torch.float64, device=device)
@@ -432,7 +434,8 @@ def run_ours(args):
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": desc, "nd": s.nd, "nf": s.nf, "eps": eps,
                    "precision": args.precision, "n": info.n, "n1": info.n1, "n2": info.n2,
-                   "width": info.width, "l2": "flushed between steps (256 MB write, untimed)",
+                   "width": info.width, "sigma": info.sigma,
+                   "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"independent series per GPU x{world}"},
         "roofline": roofline,
         "spread_fft": {"ms": spread_fft_ms, "algorithmic_bytes": spread_fft_bytes,

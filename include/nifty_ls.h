@@ -66,16 +66,17 @@ typedef struct {
     int32_t prec;          /* ls_prec                                         */
     double beta;           /* ES kernel shape parameter                       */
     double eps;            /* tolerance the plan was made for                 */
-    double sigma;          /* upsampling factor n / nf                        */
+    double sigma;          /* upsampling factor chosen (n >= sigma nf)        */
     int64_t workspace_bytes;
 } ls_plan_info;
 
 /*
  * ls_plan: choose the NUFFT parameters for tolerance eps and nf frequencies
- * (Sec. 1: "width and fine grid size ... chosen to match the user tolerance"),
+ * (Sec. 1: width and fine-grid size are matched to the user tolerance),
  * allocate the workspace on `device` and build the twiddle and deconvolution
- * tables.  Kernel: exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1, upsampling 2,
- * w = ceil(log10(1/eps)) + 1 cells, beta = 2.30 w.
+ * tables.  Kernel: exp(beta (sqrt(1 - z^2) - 1)), |z| <= 1; at upsampling 2
+ * w = ceil(log10(1/eps)) + 1 cells and beta = 2.30 w (see ls_plan_opts for
+ * upsampling 1.5, which ls_plan may pick when it is cheaper).
  *   out      receives the plan handle (NULL on failure).
  *   max_nd   largest number of observations a later execute may pass (>= 2).
  *   nf       number of frequencies (>= 1); executes may use any nf' <= nf.
@@ -89,6 +90,20 @@ typedef struct {
  */
 ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec,
                   int device, void *stream);
+
+/* Options of ls_plan_ex (zero-initialise for the defaults). */
+typedef struct {
+    /* Fine-grid upsampling factor sigma = n / nf: 0 lets the plan choose
+     * (the cheaper of 2 and 1.5 by a cost model of grid cells plus kernel
+     * evaluations), or exactly 2.0 or 1.5.  Sigma 1.5 needs eps >= 1e-10.
+     * The kernel width grows as sigma falls: w = ceil(ln(1/eps) /
+     * (pi sqrt(1 - 1/sigma))), beta = 0.976 pi (1 - 1/(2 sigma)) w. */
+    double upsampling;
+} ls_plan_opts;
+
+/* ls_plan with options (opts may be NULL: the defaults). */
+ls_status ls_plan_ex(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec,
+                     int device, void *stream, const ls_plan_opts *opts);
 
 /* Replace the stream later calls launch on (NULL: legacy default stream). */
 ls_status ls_set_stream(ls_plan_t plan, void *stream);
@@ -154,13 +169,15 @@ const char *ls_status_str(ls_status s);
 
 /*
  * Host-only queries (no GPU needed), used to check the plan's arithmetic.
- * ls_choose_params: the (w, beta, n, n1, n2) ls_plan would choose.
+ * ls_choose_params: the (w, beta, n, n1, n2, sigma) ls_plan_ex would choose
+ * for max_nd observations and the requested upsampling (0: automatic).
  * ls_kernel_ft: phi_hat(k) = int phi(x) e^{i k x} dx of the ES kernel for
  * grid size n, in grid units: (w/2) int_{-1}^{1} psi(z) cos(pi k w z / n) dz,
  * by the same Gauss-Legendre rule the plan uses.
  */
-ls_status ls_choose_params(int64_t nf, double eps, int prec, int32_t *width, double *beta,
-                           int64_t *n, int32_t *n1, int32_t *n2);
+ls_status ls_choose_params(int64_t nf, double eps, int prec, int64_t max_nd, double upsampling,
+                           int32_t *width, double *beta, int64_t *n, int32_t *n1, int32_t *n2,
+                           double *sigma);
 double ls_kernel_ft(double k, int64_t n, int32_t width, double beta);
 
 #ifdef __cplusplus

@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
            "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
            "ls_destroy", "ls_set_stream", "ls_plan_describe", "ls_status_str",
-           "ls_choose_params", "ls_kernel_ft", "PlanInfo", "ls_timing_enable",
+           "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES"]
 
 LS_FP64, LS_FP32 = 0, 1
@@ -61,9 +61,12 @@ _SIGS = {
     "ls_plan_describe": (ctypes.c_int, [_c_void_p, ctypes.POINTER(PlanInfo)]),
     "ls_destroy": (ctypes.c_int, [_c_void_p]),
     "ls_status_str": (ctypes.c_char_p, [ctypes.c_int]),
-    "ls_choose_params": (ctypes.c_int, [_i64, _dbl, ctypes.c_int, ctypes.POINTER(_i32),
-                                        ctypes.POINTER(_dbl), ctypes.POINTER(_i64),
-                                        ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "ls_choose_params": (ctypes.c_int, [_i64, _dbl, ctypes.c_int, _i64, _dbl,
+                                        ctypes.POINTER(_i32), ctypes.POINTER(_dbl),
+                                        ctypes.POINTER(_i64), ctypes.POINTER(_i32),
+                                        ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
+    "ls_plan_ex": (ctypes.c_int, [ctypes.POINTER(_c_void_p), _i64, _i64, _dbl, ctypes.c_int,
+                                  ctypes.c_int, _c_void_p, ctypes.c_void_p]),
     "ls_kernel_ft": (_dbl, [_dbl, _i64, _i32, _dbl]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "ls_timing_report": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
@@ -104,11 +107,23 @@ def ls_status_str(status: int) -> str:
     return load_library().ls_status_str(int(status)).decode()
 
 
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("upsampling", _dbl)]
+
+
 def ls_plan(max_nd: int, nf: int, eps: float, prec: int = LS_FP64, device: int = 0,
-            stream: int = 0) -> int:
+            stream: int = 0, upsampling: float = 0.0) -> int:
+    """Plan handle; ``upsampling`` 0 (automatic), 2.0 or 1.5 (via ls_plan_ex)."""
     h = _c_void_p()
-    _check(load_library().ls_plan(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
-                                  int(device), _c_void_p(stream or None)), "ls_plan")
+    lib = load_library()
+    if upsampling:
+        opts = PlanOpts(float(upsampling))
+        st = lib.ls_plan_ex(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
+                            int(device), _c_void_p(stream or None), ctypes.byref(opts))
+    else:
+        st = lib.ls_plan(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
+                         int(device), _c_void_p(stream or None))
+    _check(st, "ls_plan")
     return h.value
 
 
@@ -147,12 +162,16 @@ def ls_plan_describe(plan: int) -> PlanInfo:
     return info
 
 
-def ls_choose_params(nf: int, eps: float, prec: int = LS_FP64) -> dict:
-    w, b, n, n1, n2 = _i32(), _dbl(), _i64(), _i32(), _i32()
-    _check(load_library().ls_choose_params(int(nf), float(eps), int(prec), ctypes.byref(w),
-                                           ctypes.byref(b), ctypes.byref(n), ctypes.byref(n1),
-                                           ctypes.byref(n2)), "ls_choose_params")
-    return {"width": w.value, "beta": b.value, "n": n.value, "n1": n1.value, "n2": n2.value}
+def ls_choose_params(nf: int, eps: float, prec: int = LS_FP64, max_nd: int | None = None,
+                     upsampling: float = 0.0) -> dict:
+    w, b, n, n1, n2, sg = _i32(), _dbl(), _i64(), _i32(), _i32(), _dbl()
+    nd = max(1, int(nf) // 12) if max_nd is None else int(max_nd)
+    _check(load_library().ls_choose_params(int(nf), float(eps), int(prec), nd, float(upsampling),
+                                           ctypes.byref(w), ctypes.byref(b), ctypes.byref(n),
+                                           ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(sg)),
+           "ls_choose_params")
+    return {"width": w.value, "beta": b.value, "n": n.value, "n1": n1.value, "n2": n2.value,
+            "sigma": sg.value}
 
 
 def ls_timing_enable(plan: int, enable: bool = True) -> None:
@@ -187,10 +206,10 @@ class Plan:
     """Owns one ``ls_plan`` (workspace + tables for ``nf`` frequencies at ``eps``)."""
 
     def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
-                 device: int = 0):
+                 device: int = 0, upsampling: float = 0.0):
         self.prec = _prec_code(precision)
         self.device = int(device)
-        self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0)
+        self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling)
         self.info = ls_plan_describe(self.handle)
 
     def close(self):

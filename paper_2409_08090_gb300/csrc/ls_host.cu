@@ -19,6 +19,7 @@ struct ls_plan_s {
     int64_t max_nd;
     int64_t nf;
     double eps;
+    double sigma;         // upsampling factor the plan chose
     Geometry g;
     Workspace ws;
     int nred;
@@ -82,32 +83,46 @@ bool radix_schedule(int L, std::vector<int> &rad)
     return (int)rad.size() <= kMaxStages;
 }
 
-// ES kernel width and shape for tolerance eps (upsampling factor 2): the
-// error of the ES kernel falls roughly tenfold per extra cell of width.
-void es_params(double eps, int *w, double *beta)
+// ES kernel width and shape for tolerance eps and upsampling factor sigma.
+// sigma = 2: w = ceil(log10(1/eps)) + 1, beta = 2.30 w (the error falls about
+// tenfold per extra cell).  Other sigma: the kernel's aliasing error decays as
+// exp(-pi w sqrt(1 - 1/sigma)), so w = ceil(ln(1/eps) / (pi sqrt(1 - 1/sigma)))
+// and beta = 0.976 pi (1 - 1/(2 sigma)) w (the same constant that gives 2.30 w
+// at sigma = 2).  Returns false when the width would exceed 16 cells.
+bool es_params(double eps, double sigma, int *w, double *beta)
 {
-    int ww = (int)ceil(log10(1.0 / eps) - 1e-9) + 1;
-    if (ww < 2) ww = 2;
-    if (ww > 16) ww = 16;
-    double bo = 2.30;
-    if (ww == 2) bo = 2.20;
-    else if (ww == 3) bo = 2.26;
-    else if (ww == 4) bo = 2.38;
+    int ww;
+    double bo;
+    if (sigma == 2.0) {
+        ww = (int)ceil(log10(1.0 / eps) - 1e-9) + 1;
+        if (ww < 2) ww = 2;
+        bo = 2.30;
+        if (ww == 2) bo = 2.20;
+        else if (ww == 3) bo = 2.26;
+        else if (ww == 4) bo = 2.38;
+    } else {
+        ww = (int)ceil(log(1.0 / eps) / (M_PI * sqrt(1.0 - 1.0 / sigma)) - 1e-9);
+        if (ww < 2) ww = 2;
+        bo = 0.976 * M_PI * (1.0 - 0.5 / sigma);
+    }
+    if (ww > 16) return false;
     *w = ww;
     *beta = bo * ww;
+    return true;
 }
 
-// Fine grid: the smallest n = c 2^k >= max(2 nf, 2 w, 64), c in the odd
+// Fine grid: the smallest n = c 2^k >= max(sigma nf, 2 w, 64), c in the odd
 // 5-smooth set {1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125}, that splits as
 // n = N1 * N2 with N1 = 2^k1 a power of two in [kMinN1, n1max] and
 // N2 = n / N1 <= n2max even (the odd factor lives in N2); among the splits the
 // most balanced one is taken.
-ls_status choose_grid(int64_t nf, int w, int prec, int64_t *n_out, int *n1_out, int *n2_out)
+ls_status choose_grid(int64_t nf, double sigma, int w, int prec, int64_t *n_out, int *n1_out,
+                      int *n2_out)
 {
     static const int odd[] = {1, 3, 5, 9, 15, 25, 27, 45, 75, 81, 125};
     const int n1max = prec == LS_FP32 ? kN1MaxF32 : kN1MaxF64;
     const int n2max = prec == LS_FP32 ? kN2MaxF32 : kN2MaxF64;
-    int64_t nmin = 2 * nf;
+    int64_t nmin = (int64_t)ceil(sigma * (double)nf - 1e-9);
     if (nmin < 2 * w) nmin = 2 * w;
     if (nmin < 64) nmin = 64;
     int64_t best_n = -1;
@@ -507,25 +522,42 @@ const char *ls_status_str(ls_status s)
     return "unknown status";
 }
 
-ls_status ls_choose_params(int64_t nf, double eps, int prec, int32_t *width, double *beta,
-                           int64_t *n, int32_t *n1, int32_t *n2)
+ls_status ls_choose_params(int64_t nf, double eps, int prec, int64_t max_nd, double upsampling,
+                           int32_t *width, double *beta, int64_t *n, int32_t *n1, int32_t *n2,
+                           double *sigma_out)
 {
     if (nf < 1 || !(eps >= 1e-14 && eps <= 1e-1)) return LS_ERR_ARG;
     if (prec != LS_FP32 && prec != LS_FP64) return LS_ERR_ARG;
     if (prec == LS_FP32 && eps < 1e-7) return LS_ERR_ARG;
-    int w;
-    double b;
-    es_params(eps, &w, &b);
-    int64_t nn;
-    int a1, a2;
-    ls_status s = choose_grid(nf, w, prec, &nn, &a1, &a2);
-    if (s != LS_OK) return s;
-    if (width) *width = w;
-    if (beta) *beta = b;
-    if (n) *n = nn;
-    if (n1) *n1 = a1;
-    if (n2) *n2 = a2;
-    return LS_OK;
+    if (max_nd < 1) max_nd = 1;
+    if (!(upsampling == 0.0 || upsampling == 2.0 || upsampling == 1.5)) return LS_ERR_ARG;
+    // Candidates: sigma = 2 always; sigma = 1.5 for eps >= 1e-10.  Auto picks
+    // the smaller modelled cost: fine-grid cells (FFT and HBM traffic) plus
+    // half a cell per kernel evaluation of the spread.
+    double best_cost = 1e300;
+    ls_status st = LS_ERR_UNSUPPORTED;
+    for (double sg : {2.0, 1.5}) {
+        if (upsampling != 0.0 && sg != upsampling) continue;
+        if (sg != 2.0 && eps < 1e-10) continue;
+        int w;
+        double b;
+        if (!es_params(eps, sg, &w, &b)) continue;
+        int64_t nn;
+        int a1, a2;
+        if (choose_grid(nf, sg, w, prec, &nn, &a1, &a2) != LS_OK) continue;
+        const double cost = (double)nn + 0.5 * (double)max_nd * w;
+        if (cost < best_cost) {
+            best_cost = cost;
+            st = LS_OK;
+            if (width) *width = w;
+            if (beta) *beta = b;
+            if (n) *n = nn;
+            if (n1) *n1 = a1;
+            if (n2) *n2 = a2;
+            if (sigma_out) *sigma_out = sg;
+        }
+    }
+    return st;
 }
 
 double ls_kernel_ft(double k, int64_t n, int32_t width, double beta)
@@ -540,14 +572,21 @@ double ls_kernel_ft(double k, int64_t n, int32_t width, double beta)
 ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec, int device,
                   void *stream)
 {
+    return ls_plan_ex(out, max_nd, nf, eps, prec, device, stream, nullptr);
+}
+
+ls_status ls_plan_ex(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec, int device,
+                     void *stream, const ls_plan_opts *opts)
+{
     if (!out) return LS_ERR_ARG;
     *out = nullptr;
     if (max_nd < 2 || max_nd > ((int64_t)1 << 30)) return LS_ERR_ARG;
     int w;
-    double beta;
+    double beta, sigma = 2.0;
     int64_t n;
     int n1, n2;
-    ls_status s = ls_choose_params(nf, eps, prec, &w, &beta, &n, &n1, &n2);
+    const double ups = opts ? opts->upsampling : 0.0;
+    ls_status s = ls_choose_params(nf, eps, prec, max_nd, ups, &w, &beta, &n, &n1, &n2, &sigma);
     if (s != LS_OK) return s;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -565,6 +604,7 @@ ls_status ls_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int pr
     p->max_nd = max_nd;
     p->nf = nf;
     p->eps = eps;
+    p->sigma = sigma;
     p->bytes = 0;
     p->stage_in = p->stage_out = p->stage_sums = nullptr;
     p->timing = false;
@@ -655,7 +695,7 @@ ls_status ls_plan_describe(ls_plan_t p, ls_plan_info *info)
     info->prec = p->prec;
     info->beta = p->g.beta;
     info->eps = p->eps;
-    info->sigma = (double)p->g.n / (double)p->nf;
+    info->sigma = p->sigma;
     info->workspace_bytes = p->bytes;
     return LS_OK;
 }

@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -53,25 +55,42 @@ def _is_allowed(n):
     return m in ODD
 
 
-@pytest.mark.parametrize("nf,eps,prec,w,n", [
-    (12_000, 1e-12, 0, 13, 24_576),
-    (12_000, 1e-9, 0, 10, 24_576),
-    (12_000, 1e-6, 1, 7, 24_576),
-    (12_000_000, 1e-6, 1, 7, 25_165_824),
-    (12_000_000, 1e-9, 0, 10, 25_165_824),
-    (120_000, 1e-6, 1, 7, 245_760),
+@pytest.mark.parametrize("nf,eps,prec,ups,w,n", [
+    (12_000, 1e-12, 0, 0.0, 13, 24_576),          # sigma 1.5 is not offered below 1e-10
+    (12_000, 1e-9, 0, 2.0, 10, 24_576),
+    (12_000, 1e-6, 1, 2.0, 7, 24_576),
+    (12_000_000, 1e-6, 1, 2.0, 7, 25_165_824),
+    (12_000_000, 1e-6, 1, 1.5, 8, 18_874_368),
+    (12_000_000, 1e-9, 0, 2.0, 10, 25_165_824),
+    (120_000, 1e-6, 1, 2.0, 7, 245_760),
 ])
-def test_choose_params(nf, eps, prec, w, n):
+def test_choose_params(nf, eps, prec, ups, w, n):
     import paper_2409_08090_gb300 as nl
-    p = nl.ls_choose_params(nf, eps, prec)
+    p = nl.ls_choose_params(nf, eps, prec, upsampling=ups)
     assert p["width"] == w
     assert p["n"] == n
     assert p["n1"] * p["n2"] == p["n"]
-    assert abs(p["beta"] - 2.30 * w) < 1e-12
+    sigma = p["sigma"]
+    if sigma == 2.0:
+        assert abs(p["beta"] - 2.30 * w) < 1e-12
+    else:
+        assert sigma == 1.5
+        assert abs(p["beta"] - 0.976 * np.pi * (1 - 0.5 / sigma) * w) < 1e-12
+        assert w == int(np.ceil(np.log(1 / eps) / (np.pi * np.sqrt(1 - 1 / sigma))))
     # split limits of the two passes; N1 a power of two
     assert 32 <= p["n1"] <= (4096 if prec == 1 else 2048)
     assert p["n1"] & (p["n1"] - 1) == 0
     assert p["n2"] <= (25600 if prec == 1 else 12800) and p["n2"] % 2 == 0
+    assert p["n"] >= sigma * nf
+
+
+def test_automatic_upsampling_prefers_the_smaller_grid_when_fft_dominates():
+    import paper_2409_08090_gb300 as nl
+    big = nl.ls_choose_params(12_000_000, 1e-6, 1, max_nd=1_000_000)
+    assert big["sigma"] == 1.5
+    # a spread-dominated plan (many points, few frequencies) keeps sigma 2
+    few = nl.ls_choose_params(1_000, 1e-6, 1, max_nd=10_000_000)
+    assert few["sigma"] == 2.0
 
 
 def test_choose_params_rejects():
@@ -87,7 +106,7 @@ def test_choose_params_rejects():
 def test_grid_sizes_are_minimal_admissible():
     import paper_2409_08090_gb300 as nl
     for nf in (1, 2, 7, 100, 999, 4097, 65_537, 1_234_567):
-        p = nl.ls_choose_params(nf, 1e-9, 0)
+        p = nl.ls_choose_params(nf, 1e-9, 0, upsampling=2.0)
         n = p["n"]
         nmin = max(2 * nf, 2 * p["width"], 64)
         assert n >= nmin and _is_allowed(n)

@@ -23,10 +23,11 @@ def nl():
     return m
 
 
-def gpu_run(nl, s, eps, precision, nf=None, plan_nf=None, want_sums=False, max_nd=None):
+def gpu_run(nl, s, eps, precision, nf=None, plan_nf=None, want_sums=False, max_nd=None,
+            upsampling=0.0):
     import torch
     nf = s.nf if nf is None else nf
-    plan = nl.Plan(max_nd or s.nd, plan_nf or nf, eps, precision)
+    plan = nl.Plan(max_nd or s.nd, plan_nf or nf, eps, precision, upsampling=upsampling)
     dev = torch.device("cuda:0")
     t = torch.tensor(s.t, dtype=torch.float64, device=dev)
     y = torch.tensor(s.y, dtype=torch.float64, device=dev)
@@ -105,6 +106,19 @@ def test_random_cases(nl, oracle_mod, seed, nd, nf, sort, unit_dy, df_t, prec, e
         if nd >= 500:
             assert rel_l2(P, P_o) <= 1e-5
         assert np.max(np.abs(P - P_o)) <= 1e-4
+
+
+@pytest.mark.parametrize("seed,nd,nf,sort,unit_dy,df_t", CASES[3:])
+@pytest.mark.parametrize("prec,eps,ups,tol", [("fp64", 1e-9, 1.5, 1e-6), ("fp32", 1e-6, 1.5, 1e-4),
+                                              ("fp64", 1e-9, 2.0, 1e-6)])
+def test_random_cases_upsampling(nl, oracle_mod, seed, nd, nf, sort, unit_dy, df_t, prec, eps,
+                                 ups, tol):
+    # both fine-grid sizes the plan can choose (sigma = 1.5 and 2)
+    s = W.random_case(seed, nd, nf, sort=sort, unit_dy=unit_dy, df_t=df_t)
+    P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(nf))
+    P = gpu_run(nl, s, eps, prec, upsampling=ups)
+    assert np.max(np.abs(P - P_o)) <= tol
+    assert rel_l2(P, P_o) <= (1e-7 if prec == "fp64" else 1e-5)
 
 
 def test_time_offset_costs_no_accuracy(nl, oracle_mod):

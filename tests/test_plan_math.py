@@ -46,11 +46,12 @@ def test_kernel_ft_is_sum_of_grid_samples(nl):
         assert abs(lhs - rhs) < 1e-11 * abs(rhs)
 
 
-@pytest.mark.parametrize("eps,tol_max", [(1e-12, 1e-9), (1e-9, 1e-6), (1e-6, 1e-4)])
-def test_chosen_parameters_meet_tolerance(nl, oracle_mod, eps, tol_max):
+@pytest.mark.parametrize("eps,ups", [(1e-12, 2.0), (1e-9, 2.0), (1e-6, 2.0), (1e-9, 1.5),
+                                     (1e-6, 1.5)])
+def test_chosen_parameters_meet_tolerance(nl, oracle_mod, eps, ups):
     from tests.nufft_model import model_sums
     s = W.single_small()
-    p = nl.ls_choose_params(s.nf, eps, 0)
+    p = nl.ls_choose_params(s.nf, eps, 0, upsampling=ups)
     sums, YY = model_sums(s.t, s.y, s.dy, s.f0, s.df, s.nf, p["width"], p["beta"], p["n"],
                           nl.ls_kernel_ft)
     k = np.arange(s.nf)
