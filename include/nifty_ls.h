@@ -180,6 +180,36 @@ ls_status ls_choose_params(int64_t nf, double eps, int prec, int64_t max_nd, dou
                            double *sigma);
 double ls_kernel_ft(double k, int64_t n, int32_t width, double beta);
 
+/*
+ * ls_execute_noalloc: the periodogram of one small series without allocating
+ * any memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- code running while a CUDA
+ * stream is being captured (cudaMalloc cannot be captured), programs whose
+ * device memory belongs to another allocator or a fixed arena, and loops that
+ * cannot afford an allocation's synchronisation -- and so cannot create an
+ * ls_plan.  It runs the ls_execute pipeline on a fixed scratch area of
+ * LS_NOALLOC_SCRATCH_BYTES that the library reserves in every GPU's memory
+ * when it is loaded and keeps until the process exits.
+ *   t, y, dy, power: device pointers (dy may be NULL); nd, f0, df, nf, eps and
+ *   prec as for ls_plan/ls_execute (standard normalisation).
+ *   Limits: nd <= LS_NOALLOC_MAX_ND, nf <= LS_NOALLOC_MAX_NF, and the request's
+ *   workspace must fit the scratch area; otherwise LS_ERR_UNSUPPORTED and
+ *   nothing is launched.  Host pointers: LS_ERR_ARG.
+ * The call is synchronous on `stream` (NULL: legacy default stream) and returns
+ * the device-side status (LS_ERR_ARG for non-finite values or dy <= 0,
+ * LS_ERR_DEGENERATE for a constant series).  The first call on a device looks
+ * up the scratch area's device address (once per device); make it before any
+ * stream capture.  Every call reuses the same scratch area and clears what must
+ * start at zero: calls whose work overlaps on the GPU (other streams or host
+ * threads) race on it and must be serialised by the caller.
+ */
+#define LS_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define LS_NOALLOC_MAX_ND 16384
+#define LS_NOALLOC_MAX_NF 16384
+ls_status ls_execute_noalloc(const double *t, const double *y, const double *dy, int64_t nd,
+                             double f0, double df, int64_t nf, double eps, int prec,
+                             double *power, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

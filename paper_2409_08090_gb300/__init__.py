@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
            "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
-           "ls_destroy", "ls_set_stream", "ls_plan_describe", "ls_status_str",
+           "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES"]
 
@@ -68,6 +68,8 @@ _SIGS = {
     "ls_plan_ex": (ctypes.c_int, [ctypes.POINTER(_c_void_p), _i64, _i64, _dbl, ctypes.c_int,
                                   ctypes.c_int, _c_void_p, ctypes.c_void_p]),
     "ls_kernel_ft": (_dbl, [_dbl, _i64, _i32, _dbl]),
+    "ls_execute_noalloc": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _i64, _dbl, _dbl,
+                                          _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "ls_timing_report": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
 }
@@ -145,6 +147,17 @@ def ls_execute_sums(plan: int, t: int, y: int, dy: int | None, nd: int, f0: floa
                                           _c_void_p(dy or None), int(nd), float(f0), float(df),
                                           int(nf), float(eps), int(norm),
                                           _c_void_p(power or None), _c_void_p(sums))
+
+
+def ls_execute_noalloc(t: int, y: int, dy: int | None, nd: int, f0: float, df: float, nf: int,
+                       eps: float, prec: int, power: int, stream: int = 0) -> int:
+    """Periodogram of a small series on the library's fixed scratch area (no
+    allocation, for callers that cannot allocate device memory); device
+    pointers only; synchronous; returns the status code."""
+    return load_library().ls_execute_noalloc(_c_void_p(t), _c_void_p(y), _c_void_p(dy or None),
+                                             int(nd), float(f0), float(df), int(nf), float(eps),
+                                             int(prec), _c_void_p(power),
+                                             _c_void_p(stream or None))
 
 
 def ls_sync(plan: int) -> int:

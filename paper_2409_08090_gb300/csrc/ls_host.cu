@@ -506,6 +506,11 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
 
 }  // namespace
 
+namespace nls {
+// Stage descriptors of a length-L FFT for callers outside this file.
+bool fft_plan_for_length(int L, FftPlan *fp) { return build_fft(L, fp); }
+}  // namespace nls
+
 extern "C" {
 
 const char *ls_status_str(ls_status s)

@@ -118,6 +118,9 @@ cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
 template <typename T>
 size_t point_record_bytes();
 
+// Stage descriptors of a length-L sub-FFT (false if L has no schedule).
+bool fft_plan_for_length(int L, FftPlan *fp);
+
 size_t passA_smem_bytes(const Geometry &g, size_t cx_bytes);
 size_t passB_smem_bytes(const Geometry &g, size_t cx_bytes);
 
