@@ -99,6 +99,11 @@ typedef struct {
      * The kernel width grows as sigma falls: w = ceil(ln(1/eps) /
      * (pi sqrt(1 - 1/sigma))), beta = 0.976 pi (1 - 1/(2 sigma)) w. */
     double upsampling;
+    /* Device memory ls_execute_batch may use for its workspace (fine grids and
+     * point records of the series launched together); 0: half of the free
+     * memory at the first batch call, at most 8 GiB.  Larger batches are cut
+     * into launches that fit. */
+    uint64_t batch_workspace_bytes;
 } ls_plan_opts;
 
 /* ls_plan with options (opts may be NULL: the defaults). */
@@ -135,6 +140,32 @@ ls_status ls_execute(ls_plan_t plan, const double *t, const double *y, const dou
 ls_status ls_execute_sums(ls_plan_t plan, const double *t, const double *y, const double *dy,
                           int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
                           double *power, double *sums);
+
+/*
+ * ls_execute_batch: periodograms of nseries independent series (a ragged
+ * batch: each series has its own times, values, uncertainties and frequency
+ * grid), the many-series workload the paper's batched mode serves (Sec. 2,
+ * "Performance").  Series whose frequency counts map to the same fine grid
+ * run together: one launch per pipeline stage, the series on the grid's second
+ * dimension, within the plan's batch workspace (ls_plan_opts); larger groups
+ * are cut into several launches.  The plan supplies precision, tolerance,
+ * upsampling, device and stream; its nf and max_nd do not limit the batch.
+ *   offsets      host int64[nseries + 1]: series s owns points
+ *                offsets[s] .. offsets[s+1]-1 of t, y and dy (>= 2 points).
+ *   t, y, dy     device arrays of offsets[nseries] FP64 values (dy may be NULL).
+ *   f0, df       host double[nseries]: grid of series s is f0[s] + k df[s].
+ *   nf           host int64[nseries] (>= 1).
+ *   out_offsets  host int64[nseries]: P_k of series s goes to
+ *                power[out_offsets[s] + k], k < nf[s].
+ *   eps          >= the plan's eps.  norm: LS_NORM_STANDARD.
+ *   power        device array.
+ * Asynchronous like ls_execute with device buffers; a non-finite value,
+ * dy <= 0 or a constant series in any series is reported by ls_sync.
+ */
+ls_status ls_execute_batch(ls_plan_t plan, int64_t nseries, const int64_t *offsets,
+                           const double *t, const double *y, const double *dy, const double *f0,
+                           const double *df, const int64_t *nf, const int64_t *out_offsets,
+                           double eps, int norm, double *power);
 
 /* Wait for the plan's stream; return and clear the device-side status of every
  * execute since the previous ls_sync (LS_ERR_ARG for invalid values,

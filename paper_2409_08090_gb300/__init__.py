@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
            "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
-           "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_plan_describe", "ls_status_str",
+           "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES"]
 
@@ -68,6 +68,9 @@ _SIGS = {
     "ls_plan_ex": (ctypes.c_int, [ctypes.POINTER(_c_void_p), _i64, _i64, _dbl, ctypes.c_int,
                                   ctypes.c_int, _c_void_p, ctypes.c_void_p]),
     "ls_kernel_ft": (_dbl, [_dbl, _i64, _i32, _dbl]),
+    "ls_execute_batch": (ctypes.c_int, [_c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p,
+                                        _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p,
+                                        _dbl, ctypes.c_int, _c_void_p]),
     "ls_execute_noalloc": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _i64, _dbl, _dbl,
                                           _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
@@ -110,16 +113,17 @@ def ls_status_str(status: int) -> str:
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("upsampling", _dbl)]
+    _fields_ = [("upsampling", _dbl), ("batch_workspace_bytes", ctypes.c_uint64)]
 
 
 def ls_plan(max_nd: int, nf: int, eps: float, prec: int = LS_FP64, device: int = 0,
-            stream: int = 0, upsampling: float = 0.0) -> int:
-    """Plan handle; ``upsampling`` 0 (automatic), 2.0 or 1.5 (via ls_plan_ex)."""
+            stream: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0) -> int:
+    """Plan handle; ``upsampling`` 0 (automatic), 2.0 or 1.5, and the batch
+    workspace budget in bytes (0: automatic), both through ls_plan_ex."""
     h = _c_void_p()
     lib = load_library()
-    if upsampling:
-        opts = PlanOpts(float(upsampling))
+    if upsampling or batch_workspace_bytes:
+        opts = PlanOpts(float(upsampling), int(batch_workspace_bytes))
         st = lib.ls_plan_ex(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
                             int(device), _c_void_p(stream or None), ctypes.byref(opts))
     else:
@@ -158,6 +162,17 @@ def ls_execute_noalloc(t: int, y: int, dy: int | None, nd: int, f0: float, df: f
                                              int(nd), float(f0), float(df), int(nf), float(eps),
                                              int(prec), _c_void_p(power),
                                              _c_void_p(stream or None))
+
+
+def ls_execute_batch(plan: int, nseries: int, offsets: int, t: int, y: int, dy: int | None,
+                     f0: int, df: int, nf: int, out_offsets: int, eps: float, norm: int,
+                     power: int) -> int:
+    """Raw C-ABI call; offsets, f0, df, nf, out_offsets are host addresses."""
+    return load_library().ls_execute_batch(_c_void_p(plan), int(nseries), _c_void_p(offsets),
+                                           _c_void_p(t), _c_void_p(y), _c_void_p(dy or None),
+                                           _c_void_p(f0), _c_void_p(df), _c_void_p(nf),
+                                           _c_void_p(out_offsets), float(eps), int(norm),
+                                           _c_void_p(power))
 
 
 def ls_sync(plan: int) -> int:
@@ -219,10 +234,11 @@ class Plan:
     """Owns one ``ls_plan`` (workspace + tables for ``nf`` frequencies at ``eps``)."""
 
     def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
-                 device: int = 0, upsampling: float = 0.0):
+                 device: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0):
         self.prec = _prec_code(precision)
         self.device = int(device)
-        self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling)
+        self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling,
+                              batch_workspace_bytes)
         self.info = ls_plan_describe(self.handle)
 
     def close(self):
@@ -265,6 +281,36 @@ class Plan:
         if sync:
             _check(ls_sync(self.handle), "ls_execute (device status)")
         return out
+
+    def execute_batch(self, t, y, dy, offsets, f0, df, nf, eps=None, out=None,
+                      sync: bool = True):
+        """Periodograms of a ragged batch.  ``t, y, dy``: concatenated float64 CUDA
+        tensors (``dy`` may be None); ``offsets``: nseries+1 point offsets;
+        ``f0, df, nf``: per-series grids (sequences).  Returns ``(power, out_offsets)``
+        with series s's power at ``power[out_offsets[s]:out_offsets[s] + nf[s]]``."""
+        import numpy as np
+        import torch
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        ns = offsets.shape[0] - 1
+        f0 = np.ascontiguousarray(np.broadcast_to(np.asarray(f0, dtype=np.float64), (ns,)))
+        df = np.ascontiguousarray(np.broadcast_to(np.asarray(df, dtype=np.float64), (ns,)))
+        nf = np.ascontiguousarray(np.broadcast_to(np.asarray(nf, dtype=np.int64), (ns,)))
+        out_off = np.zeros(ns, dtype=np.int64)
+        if ns > 1:
+            out_off[1:] = np.cumsum(nf)[:-1]
+        total = int(nf.sum())
+        if out is None:
+            out = torch.empty(total, dtype=torch.float64, device=t.device)
+        eps = float(self.info.eps if eps is None else eps)
+        ls_set_stream(self.handle, self._stream())
+        st = ls_execute_batch(self.handle, ns, offsets.ctypes.data, t.data_ptr(), y.data_ptr(),
+                              dy.data_ptr() if dy is not None else None, f0.ctypes.data,
+                              df.ctypes.data, nf.ctypes.data, out_off.ctypes.data, eps,
+                              LS_NORM_STANDARD, out.data_ptr())
+        _check(st, "ls_execute_batch")
+        if sync:
+            _check(ls_sync(self.handle), "ls_execute_batch (device status)")
+        return out, out_off
 
     def execute_host(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
                      out=None):

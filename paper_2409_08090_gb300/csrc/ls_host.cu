@@ -5,12 +5,42 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
 #include "ls_internal.cuh"
 
 using namespace nls;
+
+// Parameters chosen for a plan (see ls_choose_params).
+struct PlanParams {
+    int32_t w, n1, n2;
+    double beta, sigma, upsampling;
+    int64_t n;
+};
+
+struct ls_plan_s;
+
+// One grid class of a ragged batch: series whose frequency count maps to the
+// same fine grid share these tables (sub-plan without workspace).
+struct BatchClass {
+    PlanParams pp;
+    ls_plan_s *sub;
+};
+
+// Workspace of ls_execute_batch, grown on demand.
+struct BatchWorkspace {
+    Workspace ws;
+    int64_t cap_points = 0;   // point records
+    int cap_S = 0;            // series per launch
+    int64_t cap_cells = 0;    // elements of H (3 n S)
+    int cap_nred = 0;         // reduction blocks per series
+    int64_t ws_bins = 0;      // entries of each of hist, binstart, cursor
+    SeriesDesc *desc = nullptr;
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+};
 
 struct ls_plan_s {
     int device;
@@ -20,6 +50,8 @@ struct ls_plan_s {
     int64_t nf;
     double eps;
     double sigma;         // upsampling factor the plan chose
+    double upsampling;    // requested upsampling (0: automatic)
+    int nsm;
     Geometry g;
     Workspace ws;
     int nred;
@@ -36,6 +68,10 @@ struct ls_plan_s {
     int t_head, t_pending;
     double t_acc[LS_NUM_STAGES];
     int64_t t_count;
+    // ls_execute_batch
+    std::vector<BatchClass> classes;
+    BatchWorkspace bws;
+    int64_t batch_budget = 0;   // bytes for the batch workspace (0: chosen on first use)
 };
 
 namespace {
@@ -347,13 +383,14 @@ ls_status upload_tables(ls_plan_s *p)
 }
 
 template <typename T>
-ls_status plan_workspace(ls_plan_s *p)
+ls_status plan_workspace(ls_plan_s *p, bool tables_only)
 {
+    if (tables_only) return upload_tables<T>(p);
     const Geometry &g = p->g;
     const size_t cx = sizeof(typename Cx<T>::type);
     ls_status s;
     if ((s = plan_alloc(p, &p->ws.H, 3 * (size_t)g.n * cx)) != LS_OK) return s;
-    const size_t rec = (point_record_bytes<T>() + 64) * (size_t)p->max_nd + 4096;
+    const size_t rec = point_record_bytes<T>() * (size_t)p->max_nd + 4 * 256;   // carve() alignment
     for (int i = 0; i < 2; ++i) {
         if ((s = plan_alloc(p, &p->ws.pts_raw[i], rec)) != LS_OK) return s;
         if ((s = plan_alloc(p, &p->ws.pts_sorted[i], rec)) != LS_OK) return s;
@@ -396,6 +433,24 @@ ls_status ensure_staging(ls_plan_s *p, double **buf, size_t count)
     ls_status s = plan_alloc(p, &v, count * sizeof(double));
     if (s == LS_OK) *buf = static_cast<double *>(v);
     return s;
+}
+
+// Descriptor of one series: inputs at pt_off, records at rec_off, outputs at
+// out_off, frequencies f0 + k df (k < nf), centre mode nf / 2.
+SeriesDesc make_series(int64_t pt_off, int64_t rec_off, int64_t nd, int64_t out_off, int64_t nf,
+                       double f0, double df)
+{
+    SeriesDesc d;
+    d.pt_off = pt_off;
+    d.rec_off = rec_off;
+    d.nd = nd;
+    d.out_off = out_off;
+    d.nf = nf;
+    int neg;
+    decompose_double(df, d.ph.df_m, d.ph.df_e, neg);
+    decompose_double(f0, d.ph.f0_m, d.ph.f0_e, d.ph.f0_neg);
+    d.ph.K0 = nf / 2;
+    return d;
 }
 
 // Accumulate the oldest pending event set (waits for it).
@@ -463,17 +518,10 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
         dsums = p->stage_sums;
     }
 
-    ExecParams ep;
-    ep.t = dev_in[0];
-    ep.y = dev_in[1];
-    ep.dy = dev_in[2];
-    ep.nd = nd;
-    ep.f0 = f0;
-    ep.df = df;
-    ep.nf = nf;
-    ep.K0 = nf / 2;
-    ep.power = dpow;
-    ep.sums = dsums;
+    Batch bt;
+    bt.S = 1;
+    bt.many = nullptr;
+    bt.one = make_series(0, 0, nd, 0, nf, f0, df);
     int nred = (int)((nd + 255) / 256);
     if (nred > p->nred) nred = p->nred;
     cudaEvent_t *ev = nullptr;
@@ -486,8 +534,11 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
         p->t_head = (p->t_head + 1) % kTimingRing;
         p->t_pending += 1;
     }
-    e = (p->prec == LS_FP32) ? launch_pipeline<float>(p->g, p->ws, p->max_nd, ep, nred, st, ev)
-                             : launch_pipeline<double>(p->g, p->ws, p->max_nd, ep, nred, st, ev);
+    e = (p->prec == LS_FP32)
+            ? launch_pipeline<float>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
+                                     dev_in[2], dpow, dsums, nred, st, ev)
+            : launch_pipeline<double>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
+                                      dev_in[2], dpow, dsums, nred, st, ev);
     if (e != cudaSuccess) return cuda_status(e);
     if (host_power || host_sums) {
         if (host_power) {
@@ -502,6 +553,206 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
         return ls_sync(p);
     }
     return LS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ls_execute_batch support
+// ---------------------------------------------------------------------------
+void batch_free(ls_plan_s *p);
+
+// Make the batch workspace hold S series, `points` records, `cells` elements
+// of H, `bins` histogram entries per array and nred reduction blocks per
+// series (the buffers grow by a quarter beyond the request).
+template <typename T>
+ls_status batch_reserve(ls_plan_s *p, int S, int64_t points, int64_t cells, int64_t bins, int nred)
+{
+    BatchWorkspace &b = p->bws;
+    if (S <= b.cap_S && points <= b.cap_points && cells <= b.cap_cells && nred <= b.cap_nred &&
+        bins <= b.ws_bins)
+        return LS_OK;
+    cudaStreamSynchronize(p->stream);
+    for (void *a : b.allocs) cudaFree(a);
+    b.allocs.clear();
+    b.bytes = 0;
+    auto grow = [](int64_t need, int64_t have) { return need > have ? need + need / 4 : have; };
+    b.cap_S = (int)grow(S, b.cap_S);
+    b.cap_points = grow(points, b.cap_points);
+    b.cap_cells = grow(cells, b.cap_cells);
+    b.cap_nred = (int)grow(nred, b.cap_nred);
+    b.ws_bins = grow(bins, b.ws_bins);
+    auto alloc = [&](void **ptr, size_t bytes) -> ls_status {
+        cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+        if (e != cudaSuccess) {
+            *ptr = nullptr;
+            return cuda_status(e);
+        }
+        b.allocs.push_back(*ptr);
+        b.bytes += (int64_t)bytes;
+        return LS_OK;
+    };
+    const size_t cx = sizeof(typename Cx<T>::type);
+    Workspace &ws = b.ws;
+    ls_status s;
+    void *v;
+    if ((s = alloc(&ws.H, cx * (size_t)b.cap_cells)) != LS_OK) return s;
+    const size_t rec = point_record_bytes<T>() * (size_t)b.cap_points + 4 * 256;
+    for (int i = 0; i < 2; ++i) {
+        if ((s = alloc(&ws.pts_raw[i], rec)) != LS_OK) return s;
+        if ((s = alloc(&ws.pts_sorted[i], rec)) != LS_OK) return s;
+    }
+    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
+    ws.hist = static_cast<int *>(v);
+    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
+    ws.binstart = static_cast<int *>(v);
+    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
+    ws.cursor = static_cast<int *>(v);
+    if ((s = alloc(&v, sizeof(double) * 3 * (size_t)b.cap_nred * b.cap_S)) != LS_OK) return s;
+    ws.partials = static_cast<double *>(v);
+    if ((s = alloc(&v, sizeof(unsigned int) * 2 * (size_t)b.cap_S)) != LS_OK) return s;
+    ws.counter = static_cast<unsigned int *>(v);
+    if (cudaMemset(ws.counter, 0, sizeof(unsigned int) * 2 * (size_t)b.cap_S) != cudaSuccess)
+        return LS_ERR_CUDA;
+    if ((s = alloc(&v, sizeof(Stats) * (size_t)b.cap_S)) != LS_OK) return s;
+    ws.stats = static_cast<Stats *>(v);
+    if ((s = alloc(&v, sizeof(SeriesDesc) * (size_t)b.cap_S)) != LS_OK) return s;
+    b.desc = static_cast<SeriesDesc *>(v);
+    ws.status = p->ws.status;   // errors of batch launches reach ls_sync too
+    return LS_OK;
+}
+
+// Plan (geometry, tables and, unless tables_only, the single-series workspace)
+// for the parameters pp.
+ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec,
+                      int device, void *stream, const PlanParams &pp, bool tables_only)
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? LS_ERR_ARG : LS_ERR_CUDA;
+    }
+    DeviceGuard guard(device);
+    if (!guard.ok) return LS_ERR_CUDA;
+
+    ls_plan_s *p = new (std::nothrow) ls_plan_s();
+    if (!p) return LS_ERR_NOMEM;
+    p->device = device;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->prec = prec;
+    p->max_nd = max_nd;
+    p->nf = nf;
+    p->eps = eps;
+    p->sigma = pp.sigma;
+    p->upsampling = pp.upsampling;
+    p->bytes = 0;
+    p->stage_in = p->stage_out = p->stage_sums = nullptr;
+    p->timing = false;
+    p->t_head = p->t_pending = 0;
+    for (double &a : p->t_acc) a = 0.0;
+    p->t_count = 0;
+    Geometry &g = p->g;
+    g.n = pp.n;
+    g.N1 = pp.n1;
+    g.N2 = pp.n2;
+    g.w = pp.w;
+    g.beta = pp.beta;
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    int BA = 1;
+    for (int cand : {8, 4, 2}) {
+        if (pp.n1 % cand == 0 && (size_t)cand * pp.n2 * cx <= kSmemPairBudget &&
+            pp.n1 / cand >= 2) {
+            BA = cand;
+            break;
+        }
+    }
+    g.BA = BA;
+    g.logBA = ilog2_exact(BA);
+    g.nbins = pp.n1 / BA;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    if (nsm <= 0) nsm = 152;
+    p->nsm = nsm;
+    p->nred = 8 * nsm;
+    ls_status s = (prec == LS_FP32) ? plan_workspace<float>(p, tables_only)
+                                    : plan_workspace<double>(p, tables_only);
+    if (s != LS_OK) {
+        plan_free(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return LS_OK;
+}
+
+void batch_free(ls_plan_s *p)
+{
+    for (BatchClass &c : p->classes) {
+        plan_free(c.sub);
+        delete c.sub;
+    }
+    p->classes.clear();
+    for (void *a : p->bws.allocs) cudaFree(a);
+    p->bws = BatchWorkspace();
+}
+
+// Tables-only sub-plan for the grid class of pp covering nf frequencies.
+ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s **sub)
+{
+    for (BatchClass &c : p->classes) {
+        if (c.pp.n == pp.n && c.pp.n1 == pp.n1 && c.pp.w == pp.w && c.pp.beta == pp.beta) {
+            if (c.sub->nf >= nf) {
+                *sub = c.sub;
+                return LS_OK;
+            }
+            // the deconvolution table must reach nf/2: rebuild with the larger nf
+            cudaStreamSynchronize(p->stream);
+            plan_free(c.sub);
+            delete c.sub;
+            ls_plan_t np;
+            ls_status s = create_plan(&np, 2, nf, p->eps, p->prec, p->device, p->stream, pp, true);
+            if (s != LS_OK) return s;
+            c.sub = np;
+            *sub = np;
+            return LS_OK;
+        }
+    }
+    ls_plan_t np;
+    ls_status s = create_plan(&np, 2, nf, p->eps, p->prec, p->device, p->stream, pp, true);
+    if (s != LS_OK) return s;
+    p->classes.push_back(BatchClass{pp, np});
+    *sub = np;
+    return LS_OK;
+}
+
+template <typename T>
+ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
+                       int64_t points, int64_t max_nd, const double *t, const double *y,
+                       const double *dy, double *power)
+{
+    const Geometry &g = sub->g;
+    const int S = (int)descs.size();
+    int nred = (int)((max_nd + 255) / 256);
+    const int cap_red = (8 * p->nsm + S - 1) / S;
+    if (nred > cap_red) nred = cap_red;
+    if (nred < 1) nred = 1;
+    ls_status s = batch_reserve<T>(p, S, points, 3 * g.n * (int64_t)S,
+                                   2 * ((int64_t)g.nbins + 1) * S, nred);
+    if (s != LS_OK) return s;
+    BatchWorkspace &b = p->bws;
+    cudaError_t e = cudaMemcpyAsync(b.desc, descs.data(), sizeof(SeriesDesc) * descs.size(),
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    Workspace ws = b.ws;
+    ws.twA = sub->ws.twA;
+    ws.twB = sub->ws.twB;
+    ws.tw4 = sub->ws.tw4;
+    ws.deconv = sub->ws.deconv;
+    Batch bt;
+    bt.S = S;
+    bt.many = b.desc;
+    bt.one = descs[0];
+    e = launch_pipeline<T>(g, ws, b.cap_points, bt, max_nd, t, y, dy, power, nullptr, nred,
+                           p->stream, nullptr);
+    return cuda_status(e);
 }
 
 }  // namespace
@@ -586,64 +837,101 @@ ls_status ls_plan_ex(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int
     if (!out) return LS_ERR_ARG;
     *out = nullptr;
     if (max_nd < 2 || max_nd > ((int64_t)1 << 30)) return LS_ERR_ARG;
-    int w;
-    double beta, sigma = 2.0;
-    int64_t n;
-    int n1, n2;
-    const double ups = opts ? opts->upsampling : 0.0;
-    ls_status s = ls_choose_params(nf, eps, prec, max_nd, ups, &w, &beta, &n, &n1, &n2, &sigma);
+    PlanParams pp;
+    pp.upsampling = opts ? opts->upsampling : 0.0;
+    ls_status s = ls_choose_params(nf, eps, prec, max_nd, pp.upsampling, &pp.w, &pp.beta, &pp.n,
+                                   &pp.n1, &pp.n2, &pp.sigma);
     if (s != LS_OK) return s;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
-        cudaGetLastError();
-        return device < 0 ? LS_ERR_ARG : LS_ERR_CUDA;
-    }
-    DeviceGuard guard(device);
-    if (!guard.ok) return LS_ERR_CUDA;
+    s = create_plan(out, max_nd, nf, eps, prec, device, stream, pp, false);
+    if (s == LS_OK && opts && opts->batch_workspace_bytes > 0)
+        (*out)->batch_budget = (int64_t)opts->batch_workspace_bytes;
+    return s;
+}
 
-    ls_plan_s *p = new (std::nothrow) ls_plan_s();
-    if (!p) return LS_ERR_NOMEM;
-    p->device = device;
-    p->stream = static_cast<cudaStream_t>(stream);
-    p->prec = prec;
-    p->max_nd = max_nd;
-    p->nf = nf;
-    p->eps = eps;
-    p->sigma = sigma;
-    p->bytes = 0;
-    p->stage_in = p->stage_out = p->stage_sums = nullptr;
-    p->timing = false;
-    p->t_head = p->t_pending = 0;
-    for (double &a : p->t_acc) a = 0.0;
-    p->t_count = 0;
-    Geometry &g = p->g;
-    g.n = n;
-    g.N1 = n1;
-    g.N2 = n2;
-    g.w = w;
-    g.beta = beta;
-    const size_t cx = prec == LS_FP32 ? 8 : 16;
-    int BA = 1;
-    for (int cand : {8, 4, 2}) {
-        if (n1 % cand == 0 && (size_t)cand * n2 * cx <= kSmemPairBudget && n1 / cand >= 2) {
-            BA = cand;
-            break;
+ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets, const double *t,
+                           const double *y, const double *dy, const double *f0, const double *df,
+                           const int64_t *nf, const int64_t *out_offsets, double eps, int norm,
+                           double *power)
+{
+    if (!p || nseries < 0 || !offsets || !f0 || !df || !nf || !out_offsets) return LS_ERR_ARG;
+    if (nseries == 0) return LS_OK;
+    if (!t || !y || !power) return LS_ERR_ARG;
+    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (!is_device_pointer(t) || !is_device_pointer(y) || !is_device_pointer(power) ||
+        (dy && !is_device_pointer(dy)))
+        return LS_ERR_ARG;
+    // Validate every series and find its grid class.
+    struct Item {
+        int64_t s;
+        PlanParams pp;
+    };
+    std::vector<Item> items;
+    items.reserve((size_t)nseries);
+    for (int64_t s = 0; s < nseries; ++s) {
+        const int64_t nd = offsets[s + 1] - offsets[s];
+        if (offsets[s] < 0 || nd < 2 || nf[s] < 1 || out_offsets[s] < 0) return LS_ERR_ARG;
+        if (!(df[s] > 0.0) || !isfinite(df[s]) || !isfinite(f0[s])) return LS_ERR_ARG;
+        Item it;
+        it.s = s;
+        it.pp.upsampling = p->upsampling;
+        ls_status st = ls_choose_params(nf[s], eps, p->prec, nd, p->upsampling, &it.pp.w,
+                                        &it.pp.beta, &it.pp.n, &it.pp.n1, &it.pp.n2, &it.pp.sigma);
+        if (st != LS_OK) return st;
+        items.push_back(it);
+    }
+    // Group by class (stable: series keep their order inside a class).
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.pp.n != b.pp.n) return a.pp.n > b.pp.n;
+        if (a.pp.n1 != b.pp.n1) return a.pp.n1 < b.pp.n1;
+        return a.pp.w < b.pp.w;
+    });
+    if (p->batch_budget <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        p->batch_budget = (int64_t)std::min<size_t>(fr / 2, (size_t)8 << 30);
+    }
+    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
+    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    constexpr int kMaxBatchS = 16384;
+    size_t i = 0;
+    while (i < items.size()) {
+        // one class
+        size_t j = i;
+        int64_t nf_max = 0;
+        while (j < items.size() && items[j].pp.n == items[i].pp.n && items[j].pp.n1 == items[i].pp.n1 &&
+               items[j].pp.w == items[i].pp.w && items[j].pp.beta == items[i].pp.beta) {
+            nf_max = std::max(nf_max, nf[items[j].s]);
+            ++j;
         }
+        ls_plan_s *sub = nullptr;
+        ls_status st = batch_class(p, items[i].pp, nf_max, &sub);
+        if (st != LS_OK) return st;
+        // launches within the budget
+        size_t k = i;
+        while (k < j) {
+            std::vector<SeriesDesc> descs;
+            int64_t points = 0, max_nd = 0;
+            while (k < j && (int)descs.size() < kMaxBatchS) {
+                const int64_t s = items[k].s;
+                const int64_t nd = offsets[s + 1] - offsets[s];
+                const int64_t bytes = (int64_t)(3 * (size_t)items[k].pp.n * cx * (descs.size() + 1) +
+                                                4 * recb * (size_t)(points + nd));
+                if (!descs.empty() && bytes > p->batch_budget) break;
+                descs.push_back(make_series(offsets[s], points, nd, out_offsets[s], nf[s], f0[s], df[s]));
+                points += nd;
+                max_nd = std::max(max_nd, nd);
+                ++k;
+            }
+            st = (p->prec == LS_FP32)
+                     ? batch_launch<float>(p, sub, descs, points, max_nd, t, y, dy, power)
+                     : batch_launch<double>(p, sub, descs, points, max_nd, t, y, dy, power);
+            if (st != LS_OK) return st;
+        }
+        i = j;
     }
-    g.BA = BA;
-    g.logBA = ilog2_exact(BA);
-    g.nbins = n1 / BA;
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    if (nsm <= 0) nsm = 152;
-    p->nred = 8 * nsm;
-    s = (prec == LS_FP32) ? plan_workspace<float>(p) : plan_workspace<double>(p);
-    if (s != LS_OK) {
-        plan_free(p);
-        delete p;
-        return s;
-    }
-    *out = p;
     return LS_OK;
 }
 
@@ -756,6 +1044,7 @@ ls_status ls_destroy(ls_plan_t p)
         DeviceGuard guard(p->device);
         cudaStreamSynchronize(p->stream);
         destroy_timing(p);
+        batch_free(p);
         plan_free(p);
     }
     delete p;

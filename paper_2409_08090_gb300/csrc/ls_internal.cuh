@@ -94,21 +94,45 @@ struct Workspace {
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
 };
 
-struct ExecParams {
-    const double *t, *y, *dy;
-    int64_t nd;
-    double f0, df;        // frequency grid f_k = f0 + k df
-    int64_t nf, K0;
-    double *power;        // may be null
-    double *sums;         // may be null
+// Frequencies of one series, decomposed for the exact phase reduction:
+// df = df_m 2^df_e, f0 = (-1)^f0_neg f0_m 2^f0_e, centre mode K0.
+struct PhaseArgs {
+    uint64_t df_m, f0_m;
+    int df_e, f0_e, f0_neg;
+    int64_t K0;
 };
 
+// One series of a launch: its points [pt_off, pt_off + nd) of t, y, dy, its
+// point records [rec_off, rec_off + nd) of the workspace, its nf outputs at
+// power[out_off ...] (sums at 6 out_off).
+struct SeriesDesc {
+    int64_t pt_off, rec_off, nd;
+    int64_t out_off, nf;
+    PhaseArgs ph;
+};
+
+// S series launched together (grid dimension y): `many` points to S device
+// descriptors, or is null and the single series is `one`.  Per-series
+// workspace: stats[s], counter[2s .. 2s+1], partials[s * 3 * nred ...],
+// hist/cursor[s * 2 * nbins ...], binstart[s * 2 * (nbins + 1) ...],
+// H[s * 3 * n ...].
+struct Batch {
+    int S;
+    SeriesDesc one;
+    const SeriesDesc *many;
+};
+
+// x = +-m 2^e with m < 2^53, the exact decomposition of a finite double.
+void decompose_double(double x, uint64_t &m, int &e, int &neg);
+
 // `ev`, if not null, holds LS_NUM_STAGES + 1 events recorded at the stage
-// boundaries.
+// boundaries.  `capacity` = points the record arrays hold; `max_nd` = largest
+// series of the batch; nred = reduction blocks per series.
 template <typename T>
-cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_nd,
-                            const ExecParams &p, int nred_blocks, cudaStream_t st,
-                            cudaEvent_t *ev);
+cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
+                            const Batch &b, int64_t max_nd, const double *t, const double *y,
+                            const double *dy, double *power, double *sums, int nred,
+                            cudaStream_t st, cudaEvent_t *ev);
 
 template <typename T>
 cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,

@@ -27,6 +27,21 @@ namespace nls {
 
 template <typename T> using Cplx = typename Cx<T>::type;
 
+__device__ __forceinline__ SeriesDesc series_of(const Batch &b, int s)
+{
+    return b.many ? b.many[s] : b.one;
+}
+
+template <typename T>
+__device__ __forceinline__ PointSet<T> shifted(PointSet<T> p, int64_t off)
+{
+    p.ab += off;
+    p.roff += off;
+    p.s[0] += off;
+    p.s[1] += off;
+    return p;
+}
+
 // ---------------------------------------------------------------------------
 // Block reduction helpers
 // ---------------------------------------------------------------------------
@@ -107,9 +122,18 @@ __device__ void reduce_partials(const double *partials, int nparts, int width, d
 // comes from the second pass.
 // ---------------------------------------------------------------------------
 __global__ void k_stats(const double *__restrict__ t, const double *__restrict__ y,
-                        const double *__restrict__ dy, int64_t nd, double *partials,
+                        const double *__restrict__ dy, Batch bt, double *partials,
                         unsigned int *counter, Stats *st, int *status)
 {
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    t += sd.pt_off;
+    y += sd.pt_off;
+    if (dy) dy += sd.pt_off;
+    const int64_t nd = sd.nd;
+    partials += (size_t)ser * 3 * gridDim.x;
+    counter += 2 * ser;
+    st += ser;
     __shared__ double sh[32];
     double sw = 0.0, swy = 0.0, swy2 = 0.0;
     bool ok = true;
@@ -251,12 +275,6 @@ __device__ __forceinline__ int agg_increment(int *counter, int key, bool active)
     return old;
 }
 
-// Frequencies of the transform, decomposed for frac_fixed (host-filled).
-struct PhaseArgs {
-    uint64_t df_m, f0_m;
-    int df_e, f0_e, f0_neg;
-    int64_t K0;
-};
 
 // ---------------------------------------------------------------------------
 // K1b: per-point records + bin histogram + YY reduction.  Coordinates and
@@ -265,11 +283,24 @@ struct PhaseArgs {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
-                         const double *__restrict__ dy, int64_t nd, PhaseArgs ph, Geometry g,
-                         PointSet<T> px, PointSet<T> p2, int *hist, double *partials,
-                         unsigned int *counter, Stats *st, int *status)
+                         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
+                         PointSet<T> p2, int *hist, double *partials, unsigned int *counter,
+                         Stats *st, int *status)
 {
     using V = Cplx<T>;
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    t += sd.pt_off;
+    y += sd.pt_off;
+    if (dy) dy += sd.pt_off;
+    const int64_t nd = sd.nd;
+    const PhaseArgs ph = sd.ph;
+    px = shifted(px, sd.rec_off);
+    p2 = shifted(p2, sd.rec_off);
+    hist += (size_t)ser * 2 * g.nbins;
+    partials += (size_t)ser * 3 * gridDim.x;
+    counter += 2 * ser + 1;
+    st += ser;
     __shared__ double sh[32];
     const double invW = st->invW;
     const double ybar = st->ybar;
@@ -333,6 +364,9 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
 // ---------------------------------------------------------------------------
 __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, int *cursor)
 {
+    hist += (size_t)blockIdx.x * 2 * nbins;
+    binstart += (size_t)blockIdx.x * 2 * (nbins + 1);
+    cursor += (size_t)blockIdx.x * 2 * nbins;
     __shared__ int chunk_tot[1024];
     for (int geo = 0; geo < 2; ++geo) {
         const int *h = hist + geo * nbins;
@@ -366,9 +400,17 @@ __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, i
 // K2b: scatter the point records into bin order (order inside a bin is free).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_scatter(int64_t nd, Geometry g, PointSet<T> rx, PointSet<T> r2,
+__global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
                           PointSet<T> sx, PointSet<T> s2, int *cursor)
 {
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    const int64_t nd = sd.nd;
+    rx = shifted(rx, sd.rec_off);
+    r2 = shifted(r2, sd.rec_off);
+    sx = shifted(sx, sd.rec_off);
+    s2 = shifted(s2, sd.rec_off);
+    cursor += (size_t)ser * 2 * g.nbins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < nd; j0 += stride) {
         const int64_t j = j0 + threadIdx.x;
@@ -406,6 +448,7 @@ __device__ __forceinline__ V tw4_root(const V *__restrict__ tw4, int64_t p)
 template <typename T>
 struct PassAArgs {
     Geometry g;
+    Batch bt;
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
     const Cplx<T> *twA;    // two-level root table, length N2
@@ -435,9 +478,11 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     V *roots = ahi + BA * nhi;                  // two-level root table of length N2
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
-    const int grid = blockIdx.y;
+    const int ser = blockIdx.y / 3;         // series of this block
+    const int grid = blockIdx.y - 3 * ser;  // its transform: 0 -> s1, 1 -> s2, 2 -> s3
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
+    const int64_t pt_off = series_of(A.bt, ser).rec_off;
 
     for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
     load_roots(roots, A.twA, N2);
@@ -454,9 +499,9 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     __syncthreads();
 
     // ---- spread ----
-    const PointSet<T> &P = (grid < 2) ? A.px : A.p2;
-    const V *str = (grid == 1) ? A.px.s[1] : P.s[0];
-    const int *bs = A.binstart + ((grid < 2) ? 0 : (g.nbins + 1));
+    const PointSet<T> P = shifted((grid < 2) ? A.px : A.p2, pt_off);
+    const V *str = (grid == 1) ? P.s[1] : P.s[0];
+    const int *bs = A.binstart + (size_t)ser * 2 * (g.nbins + 1) + ((grid < 2) ? 0 : (g.nbins + 1));
     const int nbb = (g.w - 1 + BA - 1) >> g.logBA;   // bins before this one that reach it
     int r0s, r0e, r1s = 0, r1e = 0;
     if (nbb + 1 >= g.nbins) {
@@ -509,7 +554,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     else fft_dif<1>(buf, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
-    V *H = A.H + (size_t)grid * (size_t)g.n + a0;
+    V *H = A.H + (size_t)(3 * ser + grid) * (size_t)g.n + a0;
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
         const int d = slot_freq_tab(pos, dtab, g.fa);
         const int sp = pad16(pos);
@@ -656,11 +701,11 @@ __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float
 template <typename T>
 struct PassBArgs {
     Geometry g;
+    Batch bt;
     const Cplx<T> *twB;    // two-level root table, length N1
     const Cplx<T> *H;
     const T *deconv;       // 1/phi_hat(|k'|)
     const Stats *st;
-    int64_t nf, K0;
     double *power;
     double *sums;
 };
@@ -694,6 +739,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     V *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
     int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(B.bt, ser);
+    const int64_t nf = sd.nf, K0 = sd.ph.K0;
+    const Stats *stat = B.st + ser;
+    double *power = B.power ? B.power + sd.out_off : nullptr;
+    double *sums = B.sums ? B.sums + 6 * sd.out_off : nullptr;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
 
@@ -702,7 +753,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     {
         const int half = N1 >> 1;
         for (int gi = 0; gi < 3; ++gi) {
-            const V *src = B.H + (size_t)gi * (size_t)g.n + (size_t)d * N1;
+            const V *src = B.H + (size_t)(3 * ser + gi) * (size_t)g.n + (size_t)d * N1;
             V *dst = buf + (size_t)gi * Lp;
             for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
                 V v[8];
@@ -731,13 +782,13 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
     else fft_dif<1>(buf, 3, Lp, g.fb, roots);
 
-    const double YY = B.st->YY;
+    const double YY = stat->YY;
     ff YYf;
     YYf.hi = (float)YY;
     YYf.lo = (float)(YY - (double)YYf.hi);
     const int64_t n = g.n;
-    const int64_t hi_start = n - B.K0;     // k >= hi_start -> k' = k - n < 0
-    const int64_t lo_end = B.nf - B.K0;    // k <  lo_end   -> k' = k >= 0
+    const int64_t hi_start = n - K0;       // k >= hi_start -> k' = k - n < 0
+    const int64_t lo_end = nf - K0;        // k <  lo_end   -> k' = k >= 0
     const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
     const int c2 = (int)((hi_start - d + N2 - 1) / N2);
     for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
@@ -748,12 +799,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         const int sp = pad16(pos);
         const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
         const V g1 = buf[sp], g2 = buf[Lp + sp], g3 = buf[2 * Lp + sp];
-        const int64_t out = kp + B.K0;
-        if (B.power) B.power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
-        if (B.sums) {
+        const int64_t out = kp + K0;
+        if (power) power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
+        if (sums) {
             // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
-            const double us = 1.0 / B.st->scale;
-            double *o = B.sums + 6 * out;
+            const double us = 1.0 / stat->scale;
+            double *o = sums + 6 * out;
             o[0] = (double)(g1.x * dc) * us; o[1] = (double)(g1.y * dc) * us;
             o[2] = (double)(g2.x * dc); o[3] = (double)(g2.y * dc);
             o[4] = (double)(g3.x * dc); o[5] = (double)(g3.y * dc);
@@ -817,8 +868,7 @@ static PointSet<T> carve(void *base, int64_t max_nd)
     return p;
 }
 
-// x = +-m 2^e with m < 2^53, the exact decomposition of a finite double.
-static void decompose_host(double x, uint64_t &m, int &e, int &neg)
+void decompose_double(double x, uint64_t &m, int &e, int &neg)
 {
     uint64_t b;
     memcpy(&b, &x, sizeof b);
@@ -829,35 +879,33 @@ static void decompose_host(double x, uint64_t &m, int &e, int &neg)
 }
 
 template <typename T>
-cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_nd,
-                            const ExecParams &p, int nred, cudaStream_t st, cudaEvent_t *ev)
+cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
+                            const Batch &bt, int64_t max_nd, const double *t, const double *y,
+                            const double *dy, double *power, double *sums, int nred,
+                            cudaStream_t st, cudaEvent_t *ev)
 {
     cudaError_t err;
-    PointSet<T> rx = carve<T>(ws.pts_raw[0], max_nd), r2 = carve<T>(ws.pts_raw[1], max_nd);
-    PointSet<T> sx = carve<T>(ws.pts_sorted[0], max_nd), s2 = carve<T>(ws.pts_sorted[1], max_nd);
+    const int S = bt.S;
+    PointSet<T> rx = carve<T>(ws.pts_raw[0], capacity), r2 = carve<T>(ws.pts_raw[1], capacity);
+    PointSet<T> sx = carve<T>(ws.pts_sorted[0], capacity), s2 = carve<T>(ws.pts_sorted[1], capacity);
 
     if (ev) cudaEventRecord(ev[0], st);
-    err = cudaMemsetAsync(ws.hist, 0, sizeof(int) * 2 * (size_t)g.nbins, st);
+    err = cudaMemsetAsync(ws.hist, 0, sizeof(int) * 2 * (size_t)g.nbins * S, st);
     if (err != cudaSuccess) return err;
-    k_stats<<<nred, 256, 0, st>>>(p.t, p.y, p.dy, p.nd, ws.partials, ws.counter, ws.stats,
-                                  ws.status);
-    PhaseArgs ph;
-    {
-        int neg;
-        decompose_host(p.df, ph.df_m, ph.df_e, neg);
-        decompose_host(p.f0, ph.f0_m, ph.f0_e, ph.f0_neg);
-        ph.K0 = p.K0;
-    }
-    k_points<T><<<nred, 256, 0, st>>>(p.t, p.y, p.dy, p.nd, ph, g, rx, r2, ws.hist, ws.partials,
-                                      ws.counter + 1, ws.stats, ws.status);
+    k_stats<<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, ws.partials, ws.counter, ws.stats,
+                                           ws.status);
+    k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, g, rx, r2, ws.hist, ws.partials,
+                                               ws.counter, ws.stats, ws.status);
     if (ev) cudaEventRecord(ev[1], st);
-    k_scan<<<1, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart, ws.cursor);
-    const int nsc = (int)((p.nd + 255) / 256 < 4096 ? (p.nd + 255) / 256 : 4096);
-    k_scatter<T><<<nsc, 256, 0, st>>>(p.nd, g, rx, r2, sx, s2, ws.cursor);
+    k_scan<<<S, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart, ws.cursor);
+    int nsc = (int)((max_nd + 255) / 256);
+    if (nsc > 4096) nsc = 4096;
+    k_scatter<T><<<dim3(nsc, S), 256, 0, st>>>(bt, g, rx, r2, sx, s2, ws.cursor);
 
     if (ev) cudaEventRecord(ev[2], st);
     PassAArgs<T> A;
     A.g = g;
+    A.bt = bt;
     A.px = sx;
     A.p2 = s2;
     A.binstart = ws.binstart;
@@ -867,23 +915,22 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t max_
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
     err = cudaFuncSetAttribute(k_passA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
     if (err != cudaSuccess) return err;
-    k_passA<T><<<dim3(g.nbins, 3), kThreadsA, smA, st>>>(A);
+    k_passA<T><<<dim3(g.nbins, 3 * S), kThreadsA, smA, st>>>(A);
 
     if (ev) cudaEventRecord(ev[3], st);
     PassBArgs<T> B;
     B.g = g;
+    B.bt = bt;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
     B.H = static_cast<const Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv);
     B.st = ws.stats;
-    B.nf = p.nf;
-    B.K0 = p.K0;
-    B.power = p.power;
-    B.sums = p.sums;
+    B.power = power;
+    B.sums = sums;
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     err = cudaFuncSetAttribute(k_passB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
     if (err != cudaSuccess) return err;
-    k_passB<T><<<g.N2, kThreadsB, smB, st>>>(B);
+    k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
@@ -901,9 +948,13 @@ cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
 }
 
 template cudaError_t launch_pipeline<float>(const Geometry &, const Workspace &, int64_t,
-                                            const ExecParams &, int, cudaStream_t, cudaEvent_t *);
+                                            const Batch &, int64_t, const double *,
+                                            const double *, const double *, double *, double *,
+                                            int, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_pipeline<double>(const Geometry &, const Workspace &, int64_t,
-                                             const ExecParams &, int, cudaStream_t, cudaEvent_t *);
+                                             const Batch &, int64_t, const double *,
+                                             const double *, const double *, double *, double *,
+                                             int, cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_deconv_table<float>(const Geometry &, void *, int64_t, const double *,
                                                 const double *, int, cudaStream_t);
 template cudaError_t launch_deconv_table<double>(const Geometry &, void *, int64_t, const double *,

@@ -219,18 +219,19 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     e = launch_deconv_table<T>(g, ws.deconv, ndeconv, dquad, dquad + kMaxQuad, q, st);
     if (e != cudaSuccess) return LS_ERR_CUDA;
 
-    ExecParams ep;
-    ep.t = t;
-    ep.y = y;
-    ep.dy = dy;
-    ep.nd = nd;
-    ep.f0 = f0;
-    ep.df = df;
-    ep.nf = nf;
-    ep.K0 = nf / 2;
-    ep.power = power;
-    ep.sums = nullptr;
-    e = launch_pipeline<T>(g, ws, nd, ep, nred, st, nullptr);
+    Batch bt;
+    bt.S = 1;
+    bt.many = nullptr;
+    bt.one.pt_off = 0;
+    bt.one.rec_off = 0;
+    bt.one.nd = nd;
+    bt.one.out_off = 0;
+    bt.one.nf = nf;
+    int neg;
+    decompose_double(df, bt.one.ph.df_m, bt.one.ph.df_e, neg);
+    decompose_double(f0, bt.one.ph.f0_m, bt.one.ph.f0_e, bt.one.ph.f0_neg);
+    bt.one.ph.K0 = nf / 2;
+    e = launch_pipeline<T>(g, ws, nd, bt, nd, t, y, dy, power, nullptr, nred, st, nullptr);
     if (e != cudaSuccess) return LS_ERR_CUDA;
     // Synchronous: wait (the host copy of the quadrature nodes also lives on
     // this stack frame) and read the device-side status.

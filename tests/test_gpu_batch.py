@@ -1,0 +1,120 @@
+"""Ragged batches through ls_execute_batch: every series must match the oracle
+at the single-series tolerances and the single-series path (ls_execute) at
+rounding level, however the batch is grouped into launches."""
+import numpy as np
+import pytest
+
+from paper_2409_08090_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2409_08090_gb300 as m
+    m.build.build()
+    m.load_library()
+    return m
+
+
+def _series(seed, n=14):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nd = int(rng.choice([2, 3, 40, 300, 1000, 2500, 5000]))
+        nf = int(rng.choice([1, 7, 500, 3000, 9001, 20000]))
+        s = W.random_case(seed * 100 + i, nd, nf, sort=bool(i % 2), unit_dy=(i % 3 == 0),
+                          df_t=float(rng.choice([0.2, 0.9, 1.7])),
+                          baseline=float(rng.uniform(10, 500)))
+        out.append(s)
+    return out
+
+
+def _pack(series):
+    import torch
+    dev = torch.device("cuda:0")
+    offsets = np.zeros(len(series) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([s.nd for s in series])
+    t = torch.tensor(np.concatenate([s.t for s in series]), device=dev)
+    y = torch.tensor(np.concatenate([s.y for s in series]), device=dev)
+    dyv = [np.ones(s.nd) if s.dy is None else s.dy for s in series]
+    dy = torch.tensor(np.concatenate(dyv), device=dev)
+    return offsets, t, y, dy
+
+
+def _run_batch(nl, series, eps, prec, budget=0):
+    offsets, t, y, dy = _pack(series)
+    plan = nl.Plan(2, 1, eps, prec, batch_workspace_bytes=budget)
+    P, off = plan.execute_batch(t, y, dy, offsets, [s.f0 for s in series],
+                                [s.df for s in series], [s.nf for s in series])
+    P = P.cpu().numpy()
+    plan.close()
+    return [P[o:o + s.nf] for o, s in zip(off, series)]
+
+
+def _run_single(nl, s, eps, prec):
+    import torch
+    dev = torch.device("cuda:0")
+    plan = nl.Plan(s.nd, s.nf, eps, prec)
+    dy = torch.tensor(np.ones(s.nd) if s.dy is None else s.dy, device=dev)
+    P = plan.execute(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev), dy,
+                     s.f0, s.df).cpu().numpy()
+    plan.close()
+    return P
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_ragged_batch_matches_oracle_and_single(nl, oracle_mod, prec, eps):
+    series = _series(3)
+    got = _run_batch(nl, series, eps, prec)
+    for s, P in zip(series, got):
+        P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(s.nf))
+        assert np.all(np.isfinite(P))
+        if prec == "fp64":
+            assert np.max(np.abs(P - P_o)) <= 1e-9
+        else:
+            assert np.max(np.abs(P - P_o)) <= 1e-4
+            if s.nd >= 500:
+                assert np.linalg.norm(P - P_o) / np.linalg.norm(P_o) <= 1e-5
+        P_1 = _run_single(nl, s, eps, prec)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.max(np.abs(P - P_1)) <= tol
+
+
+def test_small_budget_splits_launches_without_changing_results(nl):
+    series = _series(5, n=10)
+    full = _run_batch(nl, series, 1e-9, "fp64")
+    split = _run_batch(nl, series, 1e-9, "fp64", budget=2_000_000)
+    for a, b in zip(full, split):
+        assert np.max(np.abs(a - b)) <= 1e-12
+
+
+def test_shared_times_uniform_batch(nl, oracle_mod):
+    # the uniform-batch shape: many series on one time array (replicated here)
+    t, Y, dy, f0, df, nf = W.uniform_batch(nseries=48, nd=2000, nf=24_000)
+    series = [W.Series(t, Y[i], dy, f0, df, nf) for i in range(Y.shape[0])]
+    got = _run_batch(nl, series, 1e-6, "fp32")
+    for i in (0, 17, 47):
+        s = series[i]
+        P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(nf))
+        assert np.linalg.norm(got[i] - P_o) / np.linalg.norm(P_o) <= 1e-5
+
+
+def test_bad_series_is_reported_at_sync(nl):
+    import torch
+    series = _series(7, n=4)
+    series[2].y = series[2].y.copy()
+    series[2].y[1] = np.nan
+    offsets, t, y, dy = _pack(series)
+    plan = nl.Plan(2, 1, 1e-9, "fp64")
+    with pytest.raises(nl.LSError) as ei:
+        plan.execute_batch(t, y, dy, offsets, [s.f0 for s in series], [s.df for s in series],
+                           [s.nf for s in series])
+    assert ei.value.status == nl.LS_ERR_ARG
+    # invalid metadata is rejected before any launch
+    with pytest.raises(nl.LSError):
+        plan.execute_batch(t, y, dy, offsets, [s.f0 for s in series], [-1.0] * 4,
+                           [s.nf for s in series])
+    plan.close()
