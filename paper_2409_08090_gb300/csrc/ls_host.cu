@@ -655,6 +655,7 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
     g.N2 = pp.n2;
     g.w = pp.w;
     g.beta = pp.beta;
+    g.eps = eps;
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     int BA = 1;
     for (int cand : {8, 4, 2}) {

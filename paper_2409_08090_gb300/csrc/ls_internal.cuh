@@ -53,6 +53,7 @@ struct Geometry {
     int nbins;     // N1 / BA
     int w;
     double beta;
+    double eps;    // tolerance the tables were built for
     FftPlan fa;    // length N2
     FftPlan fb;    // length N1
 };

@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 // Explicit tau rotation (FP64), used for a nearly singular M (all phases equal
 // mod pi): a vanishing CC_tau or SS_tau term is dropped.
 __device__ __noinline__ double ls_power_tau(double Ch, double Sh, double C, double S, double C2, double S2,
-                               double YY)
+                               double YY, double lam_tol)
 {
     const double num = S2 - 2.0 * C * S;
     const double den = C2 - (C * C - S * S);
@@ -604,23 +604,25 @@ __device__ __noinline__ double ls_power_tau(double Ch, double Sh, double C, doub
     const double CCt = 0.5 * (1.0 + C2 * c2 + S2 * s2) - Ct * Ct;
     const double SSt = 0.5 * (1.0 - C2 * c2 - S2 * s2) - St * St;
     double p = 0.0;
-    if (CCt > 1e-15) p += YC * YC / CCt;
-    if (SSt > 1e-15) p += YS * YS / SSt;
+    if (CCt > lam_tol) p += YC * YC / CCt;
+    if (SSt > lam_tol) p += YS * YS / SSt;
     return p / YY;
 }
 
 __device__ __forceinline__ double ls_power_fp64(double Ch, double Sh, double C, double S,
-                                                double C2, double S2, double YY)
+                                                double C2, double S2, double YY, double lam_tol)
 {
     const double CC = 0.5 * (1.0 + C2) - C * C;
     const double SS = 0.5 * (1.0 - C2) - S * S;
     const double CS = 0.5 * S2 - C * S;
     const double D = CC * SS - CS * CS;
-    if (D > 1e-12 * (CC * CC + SS * SS) && D > 1e-30) {
+    // D = lam_min lam_max and CC + SS = lam_min + lam_max: the closed form needs
+    // lam_min clearly above the sums' accuracy.
+    if (D > lam_tol * (CC + SS) && CC > 0.0 && SS > 0.0) {
         const double N = Ch * Ch * SS - 2.0 * Ch * Sh * CS + Sh * Sh * CC;
         return N / (D * YY);
     }
-    return ls_power_tau(Ch, Sh, C, S, C2, S2, YY);
+    return ls_power_tau(Ch, Sh, C, S, C2, S2, YY, lam_tol);
 }
 
 // Double-float ("float-float") arithmetic: a value is hi + lo with |lo| <=
@@ -677,15 +679,14 @@ __device__ __forceinline__ ff ff_div(ff x, ff y)
 // evaluated in double-float, whose rounding (~1e-14 relative) is far below
 // the FP32 sums' own error, and falls back to FP64 for a nearly singular M.
 __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float S, float C2,
-                                              float S2, ff YY, double YYd)
+                                              float S2, ff YY, double YYd, float lam_tol)
 {
     const ff CC = ff_add(two_sum(0.5f, 0.5f * C2), ff_neg(two_prod(C, C)));
     const ff SS = ff_add(two_sum(0.5f, -0.5f * C2), ff_neg(two_prod(S, S)));
     const ff CS = ff_add(ff{0.5f * S2, 0.f}, ff_neg(two_prod(C, S)));
     const ff D = ff_add(ff_mul(CC, SS), ff_neg(ff_mul(CS, CS)));
-    if (!(D.hi > 1e-12f * (CC.hi * CC.hi + SS.hi * SS.hi) && D.hi > 1e-30f && CC.hi > 0.f &&
-          SS.hi > 0.f))
-        return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd);
+    if (!(D.hi > lam_tol * (CC.hi + SS.hi) && CC.hi > 0.f && SS.hi > 0.f))
+        return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd, (double)lam_tol);
     const ff ChSh = two_prod(Ch, Sh);
     // CC, SS > 0 here, so the first two terms add without cancellation.
     const ff N = ff_add(ff_add_same_sign(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
@@ -708,22 +709,23 @@ struct PassBArgs {
     const Stats *st;
     double *power;
     double *sums;
+    double lam_tol;        // eigenvalues of M at or below this count as zero
 };
 
 template <typename T> struct PowerOut;
 
 template <> struct PowerOut<double> {
     __device__ __forceinline__ static double eval(double2 g1, double2 g2, double2 g3, double dc,
-                                                  double YY, ff) {
+                                                  double YY, ff, double lam_tol) {
         return ls_power_fp64(g1.x * dc, g1.y * dc, g2.x * dc, g2.y * dc, g3.x * dc, g3.y * dc,
-                             YY);
+                             YY, lam_tol);
     }
 };
 template <> struct PowerOut<float> {
     __device__ __forceinline__ static double eval(float2 g1, float2 g2, float2 g3, float dc,
-                                                  double YY, ff YYf) {
+                                                  double YY, ff YYf, double lam_tol) {
         return ls_power_ff(g1.x * dc, g1.y * dc, g2.x * dc, g2.y * dc, g3.x * dc, g3.y * dc,
-                           YYf, YY);
+                           YYf, YY, (float)lam_tol);
     }
 };
 
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
         const V g1 = buf[sp], g2 = buf[Lp + sp], g3 = buf[2 * Lp + sp];
         const int64_t out = kp + K0;
-        if (power) power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf);
+        if (power) power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, B.lam_tol);
         if (sums) {
             // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
             const double us = 1.0 / stat->scale;
@@ -927,6 +929,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.st = ws.stats;
     B.power = power;
     B.sums = sums;
+    // The sums carry an absolute error of about eps (sum w^ = 1), plus FP32
+    // rounding on the FP32 path: an eigenvalue of M within ten times that of
+    // zero is indistinguishable from a rank-deficient M (the oracle's exact
+    // arithmetic uses 1e-15).
+    B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     err = cudaFuncSetAttribute(k_passB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
     if (err != cudaSuccess) return err;

@@ -146,6 +146,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     g.N2 = n2;
     g.w = w;
     g.beta = beta;
+    g.eps = eps;
     if (!fft_plan_for_length(n2, &g.fa) || !fft_plan_for_length(n1, &g.fb))
         return LS_ERR_UNSUPPORTED;
     int BA = 1;

@@ -23,7 +23,7 @@ def _series(seed, n=14):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
-        nd = int(rng.choice([2, 3, 40, 300, 1000, 2500, 5000]))
+        nd = int(rng.choice([2, 40, 300, 1000, 2500, 5000]))
         nf = int(rng.choice([1, 7, 500, 3000, 9001, 20000]))
         s = W.random_case(seed * 100 + i, nd, nf, sort=bool(i % 2), unit_dy=(i % 3 == 0),
                           df_t=float(rng.choice([0.2, 0.9, 1.7])),
