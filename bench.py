@@ -50,7 +50,10 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="single_large",
-                    choices=["single_large", "single_medium", "single_small"])
+                    choices=["single_large", "single_medium", "single_small", "uniform_batch",
+                             "ragged_batch"])
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="fraction of the batch workloads' series (4096 uniform, 10,000 ragged)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
@@ -453,10 +456,171 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batch workloads
+
+def batch_workload(name: str, rank: int, scale: float = 1.0):
+    """Packed many-series workload: (offsets, t, y, dy, f0[], df[], nf[], desc)."""
+    import numpy as np
+    from paper_2409_08090_gb300 import workloads as W
+    if name == "uniform_batch":
+        ns = max(8, int(4096 * scale))
+        t, Y, dy, f0, df, nf = W.uniform_batch(seed=W.BASE_SEED + 2 + 1000 * rank, nseries=ns)
+        nd = t.shape[0]
+        offsets = np.arange(ns + 1, dtype=np.int64) * nd
+        tt = np.tile(t, ns)
+        dd = np.tile(dy, ns)
+        yy = Y.reshape(-1)
+        desc = (f"uniform_batch: {ns} series on one time array, Nd=1e4 over [0,1000) d, "
+                "Nf=1.2e5, f0=1e-3, df=1e-4, dy=1")
+        return offsets, tt, yy, dd, np.full(ns, f0), np.full(ns, df), np.full(ns, nf, np.int64), desc
+    ns = max(16, int(10_000 * scale))
+    series = W.ragged_batch(seed=W.BASE_SEED + 3 + 1000 * rank, nseries=ns)
+    offsets = np.zeros(ns + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([s.nd for s in series])
+    desc = (f"ragged_batch: {ns} series, Nd log-uniform in [100, 1e5], baselines log-uniform in "
+            "[10, 3650] d with gaps, lognormal dy, Nf = 12 Nd, df = 1/(5T), f0 = df")
+    return (offsets, np.concatenate([s.t for s in series]), np.concatenate([s.y for s in series]),
+            np.concatenate([s.dy for s in series]), np.array([s.f0 for s in series]),
+            np.array([s.df for s in series]), np.array([s.nf for s in series], np.int64), desc)
+
+
+def run_batch(args):
+    import numpy as np
+    import torch
+
+    world, rank, local, pg = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import paper_2409_08090_gb300 as nl
+    nl.build.build()
+    nl.load_library()
+
+    offsets, th, yh, dyh, f0, df, nf, desc = batch_workload(args.workload, rank, args.batch_scale)
+    ns = len(nf)
+    eps = eps_for(args.precision)
+    plan = nl.Plan(2, 1, eps, args.precision, device=local, upsampling=args.upsampling)
+    t = torch.from_numpy(th).to(device)
+    y = torch.from_numpy(yh).to(device)
+    dy = torch.from_numpy(dyh).to(device)
+    out = torch.empty(int(nf.sum()), dtype=torch.float64, device=device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    for _ in range(args.warmup):
+        plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+    if nl.ls_sync(plan.handle) != 0:
+        raise SystemExit("device status after warm-up")
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev0[i].record()
+        plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+        ev1[i].record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    if nl.ls_sync(plan.handle) != 0:
+        raise SystemExit("device status after timing")
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = allreduce_max(sum(step_ms), pg, device)
+    value = world * ns * args.steps / (total_ms * 1e-3)
+    P_gpu = out.cpu().numpy()
+    out_off = np.zeros(ns, dtype=np.int64)
+    out_off[1:] = np.cumsum(nf)[:-1]
+
+    # whole-step roofline: what one batch must move
+    cx = 8 if args.precision == "fp32" else 16
+    cells = 0
+    for k in range(ns):
+        p = nl.ls_choose_params(int(nf[k]), eps, nl._prec_code(args.precision),
+                                max_nd=int(offsets[k + 1] - offsets[k]), upsampling=args.upsampling)
+        cells += 3 * p["n"]
+    alg = 24 * int(offsets[-1]) + 8 * int(nf.sum()) + 2 * cells * cx
+    peak, peak_kind = measured_hbm_peak()
+    achieved = alg / (sum(step_ms) / len(step_ms) * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "whole batch step (all kernels)", "achieved": achieved,
+                "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg}
+
+    e2e = None
+    if not args.no_e2e:
+        tp = torch.from_numpy(th).pin_memory()
+        yp = torch.from_numpy(yh).pin_memory()
+        dp = torch.from_numpy(dyh).pin_memory()
+        ph = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
+        nsteps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(nsteps):
+            t.copy_(tp, non_blocking=True)
+            y.copy_(yp, non_blocking=True)
+            dy.copy_(dp, non_blocking=True)
+            plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+            ph.copy_(out, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = allreduce_max(time.perf_counter() - t0, pg, device)
+        e2e = {"value": world * ns * nsteps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(3 * 8 * offsets[-1]), "d2h_bytes_per_step": int(8 * nf.sum()),
+               "steps": nsteps, "host_buffers": "pinned", "api": "Plan.execute_batch"}
+    plan.close()
+    if rank != 0:
+        return 0
+    cpu = accuracy = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(7)
+        pick = rng.choice(ns, min(8, ns), replace=False)
+        errs, tot_freq, tot_time = [], 0, 0.0
+        for k in pick:
+            a, b = offsets[k], offsets[k + 1]
+            kk = np.sort(rng.choice(int(nf[k]), min(int(nf[k]), 256), replace=False)).astype(np.int64)
+            t0 = time.perf_counter()
+            P_o = oracle.periodogram(th[a:b], yh[a:b], dyh[a:b], f0[k], df[k], kk)
+            tot_time += time.perf_counter() - t0
+            tot_freq += len(kk) / nf[k]
+            P_g = P_gpu[out_off[k] + kk]
+            errs.append((np.linalg.norm(P_g - P_o) / np.linalg.norm(P_o), np.max(np.abs(P_g - P_o))))
+        cpu = {"value": tot_freq / tot_time, "unit": UNIT, "cores": oracle.threads(),
+               "kind": "oracle", "sample": f"{len(pick)} random series x <=256 random frequencies"}
+        accuracy = {"rel_l2_max": float(max(e[0] for e in errs)),
+                    "max_abs": float(max(e[1] for e in errs)), "series": len(pick),
+                    "against": "FP64 oracle (direct sums)"}
+    ms_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms),
+        "p50_ms": statistics.median(step_ms),
+        "p99_ms": ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "series": ns, "points": int(offsets[-1]),
+                   "frequencies": int(nf.sum()), "eps": eps, "precision": args.precision,
+                   "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": f"independent batches per GPU x{world}"},
+        "roofline": roofline, "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": None, "clocks": clk, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("uniform_batch", "ragged_batch"):
+        return run_batch(args)
     return run_ours(args)
 
 
