@@ -466,13 +466,12 @@ def batch_workload(name: str, rank: int, scale: float = 1.0):
         ns = max(8, int(4096 * scale))
         t, Y, dy, f0, df, nf = W.uniform_batch(seed=W.BASE_SEED + 2 + 1000 * rank, nseries=ns)
         nd = t.shape[0]
+        # shared time array: t and dy hold nd values, Y the series row by row
         offsets = np.arange(ns + 1, dtype=np.int64) * nd
-        tt = np.tile(t, ns)
-        dd = np.tile(dy, ns)
-        yy = Y.reshape(-1)
-        desc = (f"uniform_batch: {ns} series on one time array, Nd=1e4 over [0,1000) d, "
-                "Nf=1.2e5, f0=1e-3, df=1e-4, dy=1")
-        return offsets, tt, yy, dd, np.full(ns, f0), np.full(ns, df), np.full(ns, nf, np.int64), desc
+        desc = (f"uniform_batch: {ns} series on one time array (shared-times path), Nd=1e4 over "
+                "[0,1000) d, Nf=1.2e5, f0=1e-3, df=1e-4, dy=1")
+        return (offsets, t, Y.reshape(-1), dy, np.full(ns, f0), np.full(ns, df),
+                np.full(ns, nf, np.int64), desc)
     ns = max(16, int(10_000 * scale))
     series = W.ragged_batch(seed=W.BASE_SEED + 3 + 1000 * rank, nseries=ns)
     offsets = np.zeros(ns + 1, dtype=np.int64)
@@ -506,8 +505,18 @@ def run_batch(args):
     dy = torch.from_numpy(dyh).to(device)
     out = torch.empty(int(nf.sum()), dtype=torch.float64, device=device)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)
+    shared = args.workload == "uniform_batch"
+    nd0 = int(offsets[1] - offsets[0])
+
+    def step():
+        if shared:
+            plan.execute_shared(t, y.view(ns, nd0), dy, float(f0[0]), float(df[0]), int(nf[0]),
+                                out=out.view(ns, int(nf[0])), sync=False)
+        else:
+            plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+
     for _ in range(args.warmup):
-        plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+        step()
     if nl.ls_sync(plan.handle) != 0:
         raise SystemExit("device status after warm-up")
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -520,7 +529,7 @@ def run_batch(args):
     for i in range(args.steps):
         flush.fill_(float(i))
         ev0[i].record()
-        plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+        step()
         ev1[i].record()
     torch.cuda.synchronize()
     barrier(pg)
@@ -538,11 +547,15 @@ def run_batch(args):
     # whole-step roofline: what one batch must move
     cx = 8 if args.precision == "fp32" else 16
     cells = 0
-    for k in range(ns):
+    if shared:
+        p = nl.ls_choose_params(int(nf[0]), eps, nl._prec_code(args.precision), max_nd=nd0,
+                                upsampling=args.upsampling)
+        cells = (ns + 2) * p["n"]
+    for k in range(0 if shared else ns):
         p = nl.ls_choose_params(int(nf[k]), eps, nl._prec_code(args.precision),
                                 max_nd=int(offsets[k + 1] - offsets[k]), upsampling=args.upsampling)
         cells += 3 * p["n"]
-    alg = 24 * int(offsets[-1]) + 8 * int(nf.sum()) + 2 * cells * cx
+    alg = 8 * (th.size + yh.size + dyh.size) + 8 * int(nf.sum()) + 2 * cells * cx
     peak, peak_kind = measured_hbm_peak()
     achieved = alg / (sum(step_ms) / len(step_ms) * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "whole batch step (all kernels)", "achieved": achieved,
@@ -562,12 +575,12 @@ def run_batch(args):
             t.copy_(tp, non_blocking=True)
             y.copy_(yp, non_blocking=True)
             dy.copy_(dp, non_blocking=True)
-            plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
+            step()
             ph.copy_(out, non_blocking=True)
             torch.cuda.synchronize()
         dt = allreduce_max(time.perf_counter() - t0, pg, device)
         e2e = {"value": world * ns * nsteps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(3 * 8 * offsets[-1]), "d2h_bytes_per_step": int(8 * nf.sum()),
+               "h2d_bytes_per_step": int(8 * (th.size + yh.size + dyh.size)), "d2h_bytes_per_step": int(8 * nf.sum()),
                "steps": nsteps, "host_buffers": "pinned", "api": "Plan.execute_batch"}
     plan.close()
     if rank != 0:
@@ -581,9 +594,10 @@ def run_batch(args):
         errs, tot_freq, tot_time = [], 0, 0.0
         for k in pick:
             a, b = offsets[k], offsets[k + 1]
+            ts, ds = (th, dyh) if shared else (th[a:b], dyh[a:b])
             kk = np.sort(rng.choice(int(nf[k]), min(int(nf[k]), 256), replace=False)).astype(np.int64)
             t0 = time.perf_counter()
-            P_o = oracle.periodogram(th[a:b], yh[a:b], dyh[a:b], f0[k], df[k], kk)
+            P_o = oracle.periodogram(ts, yh[a:b], ds, f0[k], df[k], kk)
             tot_time += time.perf_counter() - t0
             tot_freq += len(kk) / nf[k]
             P_g = P_gpu[out_off[k] + kk]

@@ -167,6 +167,22 @@ ls_status ls_execute_batch(ls_plan_t plan, int64_t nseries, const int64_t *offse
                            const double *df, const int64_t *nf, const int64_t *out_offsets,
                            double eps, int norm, double *power);
 
+/*
+ * ls_execute_batch_shared: periodograms of nseries series observed at the same
+ * times with the same uncertainties (a uniform batch, the case the paper's
+ * batched mode names, Sec. 2).  The transforms of w^ at f and at 2f depend
+ * only on t and dy, so they are taken once for the whole batch; each series
+ * adds one transform (w^ (y - ybar) at f).
+ *   t, dy        device, nd values each (dy may be NULL: unit weights).
+ *   Y            device, nseries x nd values, series s at Y + s nd.
+ *   f0, df, nf   the common grid f_k = f0 + k df, k < nf.
+ *   power        device, nseries x nf values, series s at power + s nf.
+ * Other arguments and the asynchronous behaviour as for ls_execute_batch.
+ */
+ls_status ls_execute_batch_shared(ls_plan_t plan, int64_t nseries, int64_t nd, const double *t,
+                                  const double *Y, const double *dy, double f0, double df,
+                                  int64_t nf, double eps, int norm, double *power);
+
 /* Wait for the plan's stream; return and clear the device-side status of every
  * execute since the previous ls_sync (LS_ERR_ARG for invalid values,
  * LS_ERR_DEGENERATE for a constant series, else LS_OK). */

@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
            "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
-           "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_plan_describe", "ls_status_str",
+           "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_execute_batch_shared", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES"]
 
@@ -71,6 +71,9 @@ _SIGS = {
     "ls_execute_batch": (ctypes.c_int, [_c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p,
                                         _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p,
                                         _dbl, ctypes.c_int, _c_void_p]),
+    "ls_execute_batch_shared": (ctypes.c_int, [_c_void_p, _i64, _i64, _c_void_p, _c_void_p,
+                                               _c_void_p, _dbl, _dbl, _i64, _dbl, ctypes.c_int,
+                                               _c_void_p]),
     "ls_execute_noalloc": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _i64, _dbl, _dbl,
                                           _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
@@ -173,6 +176,15 @@ def ls_execute_batch(plan: int, nseries: int, offsets: int, t: int, y: int, dy: 
                                            _c_void_p(f0), _c_void_p(df), _c_void_p(nf),
                                            _c_void_p(out_offsets), float(eps), int(norm),
                                            _c_void_p(power))
+
+
+def ls_execute_batch_shared(plan: int, nseries: int, nd: int, t: int, Y: int, dy: int | None,
+                            f0: float, df: float, nf: int, eps: float, norm: int,
+                            power: int) -> int:
+    return load_library().ls_execute_batch_shared(_c_void_p(plan), int(nseries), int(nd),
+                                                  _c_void_p(t), _c_void_p(Y),
+                                                  _c_void_p(dy or None), float(f0), float(df),
+                                                  int(nf), float(eps), int(norm), _c_void_p(power))
 
 
 def ls_sync(plan: int) -> int:
@@ -311,6 +323,25 @@ class Plan:
         if sync:
             _check(ls_sync(self.handle), "ls_execute_batch (device status)")
         return out, out_off
+
+    def execute_shared(self, t, Y, dy, f0: float, df: float, nf: int, eps=None, out=None,
+                       sync: bool = True):
+        """Uniform batch: series Y[s] (a 2-D float64 CUDA tensor, one row per
+        series) all observed at times ``t`` with uncertainties ``dy`` (or None).
+        Returns power as a (nseries, nf) tensor."""
+        import torch
+        ns, nd = int(Y.shape[0]), int(Y.shape[1])
+        if out is None:
+            out = torch.empty((ns, int(nf)), dtype=torch.float64, device=Y.device)
+        eps = float(self.info.eps if eps is None else eps)
+        ls_set_stream(self.handle, self._stream())
+        st = ls_execute_batch_shared(self.handle, ns, nd, t.data_ptr(), Y.data_ptr(),
+                                     dy.data_ptr() if dy is not None else None, f0, df, nf, eps,
+                                     LS_NORM_STANDARD, out.data_ptr())
+        _check(st, "ls_execute_batch_shared")
+        if sync:
+            _check(ls_sync(self.handle), "ls_execute_batch_shared (device status)")
+        return out
 
     def execute_host(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
                      out=None):

@@ -442,6 +442,7 @@ SeriesDesc make_series(int64_t pt_off, int64_t rec_off, int64_t nd, int64_t out_
 {
     SeriesDesc d;
     d.pt_off = pt_off;
+    d.y_off = pt_off;
     d.rec_off = rec_off;
     d.nd = nd;
     d.out_off = out_off;
@@ -727,16 +728,17 @@ ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s 
 template <typename T>
 ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
                        int64_t points, int64_t max_nd, const double *t, const double *y,
-                       const double *dy, double *power)
+                       const double *dy, double *power, int shared = 0)
 {
     const Geometry &g = sub->g;
     const int S = (int)descs.size();
+    const int64_t grids = shared ? S + 2 : 3 * (int64_t)S;
     int nred = (int)((max_nd + 255) / 256);
     const int cap_red = (8 * p->nsm + S - 1) / S;
     if (nred > cap_red) nred = cap_red;
     if (nred < 1) nred = 1;
-    ls_status s = batch_reserve<T>(p, S, points, 3 * g.n * (int64_t)S,
-                                   2 * ((int64_t)g.nbins + 1) * S, nred);
+    ls_status s = batch_reserve<T>(p, S, points, g.n * grids, 2 * ((int64_t)g.nbins + 1) * S,
+                                   nred);
     if (s != LS_OK) return s;
     BatchWorkspace &b = p->bws;
     cudaError_t e = cudaMemcpyAsync(b.desc, descs.data(), sizeof(SeriesDesc) * descs.size(),
@@ -752,7 +754,7 @@ ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDes
     bt.many = b.desc;
     bt.one = descs[0];
     e = launch_pipeline<T>(g, ws, b.cap_points, bt, max_nd, t, y, dy, power, nullptr, nred,
-                           p->stream, nullptr);
+                           p->stream, nullptr, shared);
     return cuda_status(e);
 }
 
@@ -932,6 +934,60 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
             if (st != LS_OK) return st;
         }
         i = j;
+    }
+    return LS_OK;
+}
+
+ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, const double *t,
+                                  const double *Y, const double *dy, double f0, double df,
+                                  int64_t nf, double eps, int norm, double *power)
+{
+    if (!p || nseries < 0) return LS_ERR_ARG;
+    if (nseries == 0) return LS_OK;
+    if (!t || !Y || !power || nd < 2 || nf < 1) return LS_ERR_ARG;
+    if (!(df > 0.0) || !isfinite(df) || !isfinite(f0)) return LS_ERR_ARG;
+    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (!is_device_pointer(t) || !is_device_pointer(Y) || !is_device_pointer(power) ||
+        (dy && !is_device_pointer(dy)))
+        return LS_ERR_ARG;
+    PlanParams pp;
+    pp.upsampling = p->upsampling;
+    ls_status st = ls_choose_params(nf, eps, p->prec, nd, p->upsampling, &pp.w, &pp.beta, &pp.n,
+                                    &pp.n1, &pp.n2, &pp.sigma);
+    if (st != LS_OK) return st;
+    ls_plan_s *sub = nullptr;
+    if ((st = batch_class(p, pp, nf, &sub)) != LS_OK) return st;
+    if (p->batch_budget <= 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        p->batch_budget = (int64_t)std::min<size_t>(fr / 2, (size_t)8 << 30);
+    }
+    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
+    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    constexpr int kMaxBatchS = 16384;
+    int64_t s0 = 0;
+    while (s0 < nseries) {
+        // series per launch within the budget: H holds S + 2 grids
+        int64_t S = 1;
+        while (S < kMaxBatchS && s0 + S < nseries &&
+               (int64_t)((size_t)pp.n * cx * (S + 3) + 4 * recb * (size_t)nd * (S + 1)) <=
+                   p->batch_budget)
+            ++S;
+        std::vector<SeriesDesc> descs;
+        descs.reserve((size_t)S);
+        for (int64_t k = 0; k < S; ++k) {
+            SeriesDesc d = make_series(0, k * nd, nd, (s0 + k) * nf, nf, f0, df);
+            d.y_off = (s0 + k) * nd;
+            descs.push_back(d);
+        }
+        st = (p->prec == LS_FP32)
+                 ? batch_launch<float>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1)
+                 : batch_launch<double>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1);
+        if (st != LS_OK) return st;
+        s0 += S;
     }
     return LS_OK;
 }

@@ -107,11 +107,13 @@ struct PhaseArgs {
 // point records [rec_off, rec_off + nd) of the workspace, its nf outputs at
 // power[out_off ...] (sums at 6 out_off).
 struct SeriesDesc {
-    int64_t pt_off, rec_off, nd;
+    int64_t pt_off, y_off, rec_off, nd;   // t, dy at pt_off; y at y_off
     int64_t out_off, nf;
     PhaseArgs ph;
 };
 
+// `shared` = 1: all series share t and dy (uniform batch); the s2 and s3
+// transforms of series 0 serve every series and H holds S + 2 grids.
 // S series launched together (grid dimension y): `many` points to S device
 // descriptors, or is null and the single series is `one`.  Per-series
 // workspace: stats[s], counter[2s .. 2s+1], partials[s * 3 * nred ...],
@@ -133,7 +135,7 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &b, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev);
+                            cudaStream_t st, cudaEvent_t *ev, int shared = 0);
 
 template <typename T>
 cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,

@@ -128,7 +128,7 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
     t += sd.pt_off;
-    y += sd.pt_off;
+    y += sd.y_off;
     if (dy) dy += sd.pt_off;
     const int64_t nd = sd.nd;
     partials += (size_t)ser * 3 * gridDim.x;
@@ -291,7 +291,7 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
     t += sd.pt_off;
-    y += sd.pt_off;
+    y += sd.y_off;
     if (dy) dy += sd.pt_off;
     const int64_t nd = sd.nd;
     const PhaseArgs ph = sd.ph;
@@ -449,6 +449,7 @@ template <typename T>
 struct PassAArgs {
     Geometry g;
     Batch bt;
+    int shared;            // 1: series share t and dy, so s2 and s3 are transformed once
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
     const Cplx<T> *twA;    // two-level root table, length N2
@@ -478,8 +479,19 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     V *roots = ahi + BA * nhi;                  // two-level root table of length N2
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
-    const int ser = blockIdx.y / 3;         // series of this block
-    const int grid = blockIdx.y - 3 * ser;  // its transform: 0 -> s1, 1 -> s2, 2 -> s3
+    // Instance -> (series, transform 0: s1, 1: s2, 2: s3) and its slot of H.
+    // Independent series: 3 per series.  Shared t and dy: slots 0, 1 hold s2, s3
+    // of series 0, slot 2 + s the s1 of series s.
+    int ser, grid, slot;
+    if (A.shared) {
+        slot = blockIdx.y;
+        ser = slot < 2 ? 0 : slot - 2;
+        grid = slot < 2 ? slot + 1 : 0;
+    } else {
+        ser = blockIdx.y / 3;
+        grid = blockIdx.y - 3 * ser;
+        slot = blockIdx.y;
+    }
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
     const int64_t pt_off = series_of(A.bt, ser).rec_off;
@@ -554,7 +566,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     else fft_dif<1>(buf, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
-    V *H = A.H + (size_t)(3 * ser + grid) * (size_t)g.n + a0;
+    V *H = A.H + (size_t)slot * (size_t)g.n + a0;
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
         const int d = slot_freq_tab(pos, dtab, g.fa);
         const int sp = pad16(pos);
@@ -703,6 +715,7 @@ template <typename T>
 struct PassBArgs {
     Geometry g;
     Batch bt;
+    int shared;            // see PassAArgs
     const Cplx<T> *twB;    // two-level root table, length N1
     const Cplx<T> *H;
     const T *deconv;       // 1/phi_hat(|k'|)
@@ -755,7 +768,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     {
         const int half = N1 >> 1;
         for (int gi = 0; gi < 3; ++gi) {
-            const V *src = B.H + (size_t)(3 * ser + gi) * (size_t)g.n + (size_t)d * N1;
+            const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
+            const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
             V *dst = buf + (size_t)gi * Lp;
             for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
                 V v[8];
@@ -884,7 +898,7 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &bt, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev)
+                            cudaStream_t st, cudaEvent_t *ev, int shared)
 {
     cudaError_t err;
     const int S = bt.S;
@@ -908,6 +922,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     PassAArgs<T> A;
     A.g = g;
     A.bt = bt;
+    A.shared = shared;
     A.px = sx;
     A.p2 = s2;
     A.binstart = ws.binstart;
@@ -917,12 +932,13 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
     err = cudaFuncSetAttribute(k_passA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
     if (err != cudaSuccess) return err;
-    k_passA<T><<<dim3(g.nbins, 3 * S), kThreadsA, smA, st>>>(A);
+    k_passA<T><<<dim3(g.nbins, shared ? S + 2 : 3 * S), kThreadsA, smA, st>>>(A);
 
     if (ev) cudaEventRecord(ev[3], st);
     PassBArgs<T> B;
     B.g = g;
     B.bt = bt;
+    B.shared = shared;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
     B.H = static_cast<const Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv);
@@ -957,11 +973,11 @@ cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
 template cudaError_t launch_pipeline<float>(const Geometry &, const Workspace &, int64_t,
                                             const Batch &, int64_t, const double *,
                                             const double *, const double *, double *, double *,
-                                            int, cudaStream_t, cudaEvent_t *);
+                                            int, cudaStream_t, cudaEvent_t *, int);
 template cudaError_t launch_pipeline<double>(const Geometry &, const Workspace &, int64_t,
                                              const Batch &, int64_t, const double *,
                                              const double *, const double *, double *, double *,
-                                             int, cudaStream_t, cudaEvent_t *);
+                                             int, cudaStream_t, cudaEvent_t *, int);
 template cudaError_t launch_deconv_table<float>(const Geometry &, void *, int64_t, const double *,
                                                 const double *, int, cudaStream_t);
 template cudaError_t launch_deconv_table<double>(const Geometry &, void *, int64_t, const double *,

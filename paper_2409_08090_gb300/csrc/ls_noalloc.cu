@@ -224,6 +224,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     bt.S = 1;
     bt.many = nullptr;
     bt.one.pt_off = 0;
+    bt.one.y_off = 0;
     bt.one.rec_off = 0;
     bt.one.nd = nd;
     bt.one.out_off = 0;

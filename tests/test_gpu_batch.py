@@ -138,3 +138,25 @@ def test_two_point_series_in_a_batch(nl, oracle_mod):
             assert np.max(np.abs(P[ok] - 1.0)) <= (1e-8 if prec == "fp64" else 1e-3)
             # near-singular frequencies: error ~ (sums' accuracy) / eigenvalue
             assert np.all(np.isfinite(P)) and P.min() >= -1e-6 and P.max() <= 1.1
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_shared_times_batch_matches_replicated_batch(nl, oracle_mod, prec, eps):
+    import torch
+    t, Y, dy, f0, df, nf = W.uniform_batch(seed=11, nseries=40, nd=1500, nf=9000)
+    dev = torch.device("cuda:0")
+    plan = nl.Plan(2, 1, eps, prec, batch_workspace_bytes=3_000_000)   # several launches
+    Pshared = plan.execute_shared(torch.tensor(t, device=dev), torch.tensor(Y, device=dev),
+                                  torch.tensor(dy, device=dev), f0, df, nf).cpu().numpy()
+    plan.close()
+    series = [W.Series(t, Y[i], dy, f0, df, nf) for i in range(Y.shape[0])]
+    Prep = _run_batch(nl, series, eps, prec)
+    for i in range(Y.shape[0]):
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.max(np.abs(Pshared[i] - Prep[i])) <= tol
+    for i in (0, 39):
+        P_o = oracle_mod.periodogram(t, Y[i], dy, f0, df, np.arange(nf))
+        if prec == "fp64":
+            assert np.max(np.abs(Pshared[i] - P_o)) <= 1e-9
+        else:
+            assert np.linalg.norm(Pshared[i] - P_o) / np.linalg.norm(P_o) <= 1e-5
