@@ -1,0 +1,304 @@
+"""Serving: periodogram requests admitted as they arrive, batched continuously.
+
+A request is one series (t, y, dy) with its frequency grid and a precision.
+`Scheduler` is the host-side policy, free of CUDA so it can be tested alone:
+FIFO admission under a device-memory budget, grouping of admitted requests by
+(precision, tolerance) into batches, cancellation before admission, and the
+bookkeeping of bytes in flight.  `PeriodogramServer` drives the GPU: one loop
+thread keeps a plan per (precision, tolerance) and per stream resident (their
+fine-grid tables and workspaces stay allocated between batches), launches each
+batch through `ls_execute_batch` on one of several CUDA streams, and admits the
+next requests while earlier batches are still running, so their work overlaps
+on the device.  Latency (arrival to result) and throughput are recorded per
+request.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import itertools
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = ["Request", "Scheduler", "PeriodogramServer", "request_bytes"]
+
+_ids = itertools.count()
+
+
+def request_bytes(nd: int, nf: int, precision: str) -> int:
+    """Device bytes a request holds while in flight: its inputs (t, y, dy), its
+    output, its point records and its share of the fine grids (three grids of
+    about 2 nf complex cells)."""
+    cx = 8 if precision == "fp32" else 16
+    rec = (4 + cx // 2 + cx) * 4
+    return int(24 * nd + 8 * nf + rec * nd + 3 * 2 * nf * cx)
+
+
+@dataclass
+class Request:
+    t: np.ndarray
+    y: np.ndarray
+    dy: np.ndarray | None
+    f0: float
+    df: float
+    nf: int
+    precision: str = "fp32"
+    eps: float = 1e-6
+    id: int = field(default_factory=lambda: next(_ids))
+    arrival: float = field(default_factory=time.perf_counter)
+    future: cf.Future = field(default_factory=cf.Future)
+    done: float | None = None
+
+    @property
+    def nd(self) -> int:
+        return int(self.t.shape[0])
+
+    @property
+    def nbytes(self) -> int:
+        return request_bytes(self.nd, self.nf, self.precision)
+
+    @property
+    def key(self):
+        return (self.precision, float(self.eps))
+
+
+class Scheduler:
+    """Admission and batching policy (host only).
+
+    * FIFO: a request is admitted only after every earlier one; when the head
+      does not fit the free budget, admission waits for memory to be released
+      (no overtaking, so large requests are not starved).
+    * A request larger than the whole budget is rejected with MemoryError.
+    * Admitted requests with the same (precision, eps) form a batch of at most
+      `max_batch` series; `next_batch` returns the largest group first.
+    * Cancelled requests (future.cancel() before admission) are dropped.
+    """
+
+    def __init__(self, budget_bytes: int, max_batch: int = 4096):
+        self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.in_use = 0
+        self.pending: collections.deque[Request] = collections.deque()
+        self.admitted: list[Request] = []
+        self.lock = threading.Lock()
+
+    def submit(self, req: Request) -> cf.Future:
+        if req.nbytes > self.budget:
+            req.future.set_exception(MemoryError(
+                f"request needs {req.nbytes} B of device memory, budget {self.budget} B"))
+            return req.future
+        with self.lock:
+            self.pending.append(req)
+        return req.future
+
+    def _admit(self):
+        while self.pending:
+            head = self.pending[0]
+            if head.future.cancelled():
+                self.pending.popleft()
+                continue
+            if self.in_use + head.nbytes > self.budget:
+                break
+            if not head.future.set_running_or_notify_cancel():
+                self.pending.popleft()
+                continue
+            self.pending.popleft()
+            self.in_use += head.nbytes
+            self.admitted.append(head)
+
+    def next_batch(self) -> list[Request]:
+        """Admit what fits, then take one batch of admitted requests."""
+        with self.lock:
+            self._admit()
+            if not self.admitted:
+                return []
+            groups = collections.OrderedDict()
+            for r in self.admitted:
+                groups.setdefault(r.key, []).append(r)
+            key = max(groups, key=lambda k: len(groups[k]))
+            batch = groups[key][: self.max_batch]
+            taken = set(id(r) for r in batch)
+            self.admitted = [r for r in self.admitted if id(r) not in taken]
+            return batch
+
+    def release(self, batch: list[Request]):
+        with self.lock:
+            for r in batch:
+                self.in_use -= r.nbytes
+
+    def idle(self) -> bool:
+        with self.lock:
+            return not self.pending and not self.admitted
+
+
+class _Slot:
+    """One CUDA stream with its own plans (a plan is not thread-safe and owns
+    one workspace, so each stream has its own)."""
+
+    def __init__(self, device: int):
+        import torch
+        self.stream = torch.cuda.Stream(device=device)
+        self.plans = {}
+        self.batch = None
+        self.done_event = None
+        self.out_host = None
+        self.plan = None
+        self.keep = None        # device tensors alive until the batch completes
+
+
+class PeriodogramServer:
+    """Continuous-batching periodogram server on one GPU.
+
+    submit() returns a Future resolved with the float64 numpy power array.
+    `streams` batches can be on the GPU at once; requests arriving meanwhile
+    are admitted (memory permitting) into the next batch.
+    """
+
+    def __init__(self, device: int = 0, memory_budget: int = 60 << 30, streams: int = 2,
+                 max_batch: int = 4096):
+        import torch
+
+        import paper_2409_08090_gb300 as nl
+        self._nl = nl
+        nl.load_library()
+        self.device = int(device)
+        torch.cuda.set_device(self.device)
+        self.sched = Scheduler(memory_budget, max_batch)
+        self.slots = [_Slot(self.device) for _ in range(max(1, int(streams)))]
+        self.cv = threading.Condition()
+        self.stop = False
+        self.completed: list[Request] = []
+        self.batches = 0
+        self.thread = threading.Thread(target=self._loop, name="periodogram-server", daemon=True)
+        self.thread.start()
+
+    # ---- client side -------------------------------------------------------
+    def submit(self, t, y, dy, f0: float, df: float, nf: int, precision: str = "fp32",
+               eps: float | None = None) -> cf.Future:
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        dy = None if dy is None else np.ascontiguousarray(np.broadcast_to(dy, t.shape),
+                                                          dtype=np.float64)
+        eps = (1e-6 if precision == "fp32" else 1e-9) if eps is None else float(eps)
+        req = Request(t, y, dy, float(f0), float(df), int(nf), precision, eps)
+        bad = (t.ndim != 1 or t.shape != y.shape or t.shape[0] < 2 or req.nf < 1
+               or not (req.df > 0) or not np.all(np.isfinite(t)) or not np.all(np.isfinite(y))
+               or (dy is not None and not np.all(dy > 0)))
+        if bad:
+            req.future.set_exception(ValueError("invalid request"))
+            return req.future
+        self.sched.submit(req)
+        with self.cv:
+            self.cv.notify()
+        return req.future
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify()
+        self.thread.join()
+        for s in self.slots:
+            for p in s.plans.values():
+                p.close()
+
+    def drain(self, timeout: float | None = None):
+        t0 = time.perf_counter()
+        while not self.sched.idle() or any(s.batch for s in self.slots):
+            if timeout is not None and time.perf_counter() - t0 > timeout:
+                raise TimeoutError("server did not drain")
+            time.sleep(0.001)
+
+    def stats(self) -> dict:
+        lat = np.array([r.done - r.arrival for r in self.completed if r.done is not None])
+        if lat.size == 0:
+            return {"requests": 0}
+        span = max(r.done for r in self.completed) - min(r.arrival for r in self.completed)
+        return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "periodograms_per_s": float(lat.size / span) if span > 0 else None,
+                "batches": self.batches}
+
+    # ---- GPU loop ----------------------------------------------------------
+    def _plan(self, slot: _Slot, key):
+        p = slot.plans.get(key)
+        if p is None:
+            p = self._nl.Plan(2, 1, key[1], key[0], device=self.device)
+            slot.plans[key] = p
+        return p
+
+    def _launch(self, slot: _Slot, batch: list[Request]):
+        import torch
+        nl = self._nl
+        offsets = np.zeros(len(batch) + 1, dtype=np.int64)
+        offsets[1:] = np.cumsum([r.nd for r in batch])
+        nfs = np.array([r.nf for r in batch], dtype=np.int64)
+        host = torch.empty(3 * int(offsets[-1]), dtype=torch.float64).pin_memory()
+        hv = host.numpy()
+        n = int(offsets[-1])
+        hv[:n] = np.concatenate([r.t for r in batch])
+        hv[n:2 * n] = np.concatenate([r.y for r in batch])
+        hv[2 * n:] = np.concatenate([np.ones(r.nd) if r.dy is None else r.dy for r in batch])
+        plan = self._plan(slot, batch[0].key)
+        with torch.cuda.stream(slot.stream):
+            dev = host.to(self.device, non_blocking=True)
+            out = torch.empty(int(nfs.sum()), dtype=torch.float64, device=self.device)
+            _, out_off = plan.execute_batch(dev[:n], dev[n:2 * n], dev[2 * n:], offsets,
+                                            [r.f0 for r in batch], [r.df for r in batch], nfs,
+                                            out=out, sync=False)
+            out_host = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
+            out_host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        slot.batch = batch
+        slot.done_event = ev
+        slot.out_host = (out_host, out_off)
+        slot.plan = plan
+        slot.keep = (host, dev, out)
+        self.batches += 1
+
+    def _finish(self, slot: _Slot):
+        nl = self._nl
+        batch, (out_host, out_off) = slot.batch, slot.out_host
+        st = nl.ls_sync(slot.plan.handle)
+        now = time.perf_counter()
+        res = out_host.numpy()
+        for r, o in zip(batch, out_off):
+            r.done = now
+            if st != nl.LS_OK:
+                r.future.set_exception(nl.LSError(st, "batch"))
+            else:
+                r.future.set_result(res[o:o + r.nf].copy())
+        self.completed.extend(batch)
+        self.sched.release(batch)
+        slot.batch = slot.done_event = slot.out_host = slot.keep = None
+
+    def _loop(self):
+        import torch
+        torch.cuda.set_device(self.device)
+        while True:
+            progressed = False
+            for slot in self.slots:
+                if slot.batch is not None and slot.done_event.query():
+                    self._finish(slot)
+                    progressed = True
+            for slot in self.slots:
+                if slot.batch is None:
+                    batch = self.sched.next_batch()
+                    if batch:
+                        try:
+                            self._launch(slot, batch)
+                        except Exception as exc:      # pragma: no cover - reported per request
+                            for r in batch:
+                                r.future.set_exception(exc)
+                            self.sched.release(batch)
+                            slot.batch = None
+                        progressed = True
+            busy = any(s.batch is not None for s in self.slots)
+            with self.cv:
+                if self.stop and not busy and self.sched.idle():
+                    return
+                if not progressed:
+                    self.cv.wait(timeout=0.0005 if busy else 0.01)

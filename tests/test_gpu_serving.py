@@ -1,0 +1,84 @@
+"""The continuous-batching server: every result is the same as the request
+computed alone (single-series ls_execute) within the parity tolerances, while
+requests of mixed sizes and precisions arrive from several threads and share
+batches and streams."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2409_08090_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nl():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2409_08090_gb300 as m
+    m.build.build()
+    m.load_library()
+    return m
+
+
+def _alone(nl, s, prec, eps):
+    import torch
+    dev = torch.device("cuda:0")
+    plan = nl.Plan(s.nd, s.nf, eps, prec)
+    P = plan.execute(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
+                     torch.tensor(s.dy, device=dev), s.f0, s.df).cpu().numpy()
+    plan.close()
+    return P
+
+
+def test_results_in_the_mix_equal_results_alone(nl):
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(36):
+        s = W.ragged_series(1000 + i, nd_lo=50, nd_hi=4000)
+        prec = "fp32" if i % 2 else "fp64"
+        eps = 1e-6 if prec == "fp32" else 1e-9
+        reqs.append((s, prec, eps))
+    srv = PeriodogramServer(memory_budget=64 << 20, streams=2, max_batch=8)
+    futs = [None] * len(reqs)
+
+    def client(idx):
+        for i in idx:
+            s, prec, eps = reqs[i]
+            futs[i] = srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, prec, eps)
+            time.sleep(float(rng.exponential(0.002)))
+
+    th = [threading.Thread(target=client, args=(list(range(k, len(reqs), 3)),)) for k in range(3)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    got = [f.result(timeout=120) for f in futs]
+    stats = srv.stats()
+    srv.close()
+    assert stats["requests"] == len(reqs) and stats["batches"] >= 2
+    assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    for (s, prec, eps), P in zip(reqs, got):
+        A = _alone(nl, s, prec, eps)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert P.shape == (s.nf,)
+        assert np.max(np.abs(P - A)) <= tol
+
+
+def test_invalid_and_oversized_requests_fail_their_futures_only(nl):
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    srv = PeriodogramServer(memory_budget=8 << 20, streams=1)
+    s = W.random_case(3, 500, 2000)
+    ok = srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, "fp64", 1e-9)
+    bad = srv.submit(s.t, s.y * np.nan, s.dy, s.f0, s.df, s.nf)
+    big = srv.submit(s.t, s.y, s.dy, s.f0, s.df, 50_000_000)
+    with pytest.raises(ValueError):
+        bad.result(timeout=60)
+    with pytest.raises(MemoryError):
+        big.result(timeout=60)
+    P = ok.result(timeout=60)
+    srv.close()
+    assert np.max(np.abs(P - _alone(nl, s, "fp64", 1e-9))) <= 1e-12

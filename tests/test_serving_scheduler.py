@@ -1,0 +1,98 @@
+"""Host-side serving policy (no GPU): FIFO admission under a device-memory
+budget, budget exhaustion, cancellation before admission, grouping by
+(precision, tolerance), and concurrent submitters."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2409_08090_gb300.serving import Request, Scheduler, request_bytes
+
+
+def _req(nd=100, nf=1200, precision="fp32", eps=1e-6):
+    t = np.linspace(0, 10, nd)
+    return Request(t, np.sin(t), None, 0.1, 0.01, nf, precision, eps)
+
+
+def test_fifo_admission_waits_for_memory():
+    a, b, c = _req(nf=1000), _req(nf=5000), _req(nf=1000)
+    budget = a.nbytes + b.nbytes - 1          # a and b do not fit together
+    s = Scheduler(budget)
+    for r in (a, b, c):
+        s.submit(r)
+    first = s.next_batch()
+    assert first == [a]                       # b waits; c may not overtake it
+    assert s.next_batch() == []
+    s.release(first)
+    second = s.next_batch()
+    assert second == [b]
+    s.release(second)
+    assert s.next_batch() == [c]
+    assert s.in_use == c.nbytes
+
+
+def test_oversized_request_is_rejected():
+    s = Scheduler(1000)
+    r = _req(nd=1000, nf=100_000)
+    fut = s.submit(r)
+    with pytest.raises(MemoryError):
+        fut.result(timeout=1)
+    assert s.idle()
+
+
+def test_cancelled_requests_are_dropped():
+    s = Scheduler(1 << 30)
+    rs = [_req() for _ in range(5)]
+    for r in rs:
+        s.submit(r)
+    assert rs[1].future.cancel() and rs[3].future.cancel()
+    batch = s.next_batch()
+    assert batch == [rs[0], rs[2], rs[4]]
+    assert all(r.future.running() for r in batch)
+    # admitted requests can no longer be cancelled
+    assert not batch[0].future.cancel()
+
+
+def test_batches_group_by_precision_and_tolerance():
+    s = Scheduler(1 << 30, max_batch=3)
+    rs = [_req(precision="fp32", eps=1e-6) for _ in range(5)] + \
+         [_req(precision="fp64", eps=1e-9) for _ in range(2)]
+    for r in rs:
+        s.submit(r)
+    b1 = s.next_batch()
+    assert len(b1) == 3 and all(r.key == ("fp32", 1e-6) for r in b1)
+    b2 = s.next_batch()
+    assert len(b2) == 2 and all(r.key == b2[0].key for r in b2)
+    b3 = s.next_batch()
+    assert len(b3) == 2 and {r.key for r in b2 + b3} == {("fp32", 1e-6), ("fp64", 1e-9)}
+    assert s.next_batch() == []
+
+
+def test_concurrent_submitters_and_release_balance():
+    s = Scheduler(50 * request_bytes(100, 1200, "fp32"), max_batch=7)
+    subs = []
+
+    def worker(k):
+        for i in range(40):
+            r = _req()
+            subs.append(r)
+            s.submit(r)
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for x in th:
+        x.start()
+    seen = []
+    while len(seen) < 160:
+        b = s.next_batch()
+        assert s.in_use <= s.budget
+        seen.extend(b)
+        s.release(b)
+    for x in th:
+        x.join()
+    assert len(set(id(r) for r in seen)) == 160
+    assert s.in_use == 0 and s.idle()
+
+
+def test_request_bytes_scale():
+    assert request_bytes(1000, 12000, "fp64") > request_bytes(1000, 12000, "fp32")
+    assert request_bytes(10, 100, "fp32") > 0
