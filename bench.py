@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="single_large",
                     choices=["single_large", "single_medium", "single_small", "uniform_batch",
-                             "ragged_batch"])
+                             "ragged_batch", "serving"])
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of the batch workloads' series (4096 uniform, 10,000 ragged)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -629,12 +629,105 @@ def run_batch(args):
     return 0
 
 
+def run_serving(args):
+    """Poisson arrivals of ragged-mix requests (half FP32 at eps 1e-6, half FP64
+    at eps 1e-9) into the continuous-batching server; p50/p99 latency and
+    periodograms/s per arrival rate, beside the plain one-at-a-time FP64 path."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2409_08090_gb300 as nl
+    from paper_2409_08090_gb300 import workloads as W
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    nl.build.build()
+    nl.load_library()
+    pool = W.ragged_batch(seed=W.BASE_SEED + 4, nseries=max(64, int(600 * args.batch_scale)))
+    rates = [200.0, 1000.0, 5000.0]
+    duration = 2.0 * args.batch_scale
+    srv = PeriodogramServer(memory_budget=60 << 30, streams=2, max_batch=4096)
+    # warm the plans and grid classes once
+    warm = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, p) for s in pool[:32]
+            for p in ("fp32", "fp64")]
+    for f in warm:
+        f.result(timeout=600)
+    per_rate = {}
+    for rate in rates:
+        n = max(16, int(rate * duration))
+        arrivals = W.poisson_arrivals(rate, n, seed=int(rate))
+        rng = np.random.default_rng(int(rate) + 1)
+        picks = rng.integers(0, len(pool), n)
+        precs = np.where(rng.random(n) < 0.5, "fp32", "fp64")
+        futs = []
+        srv.completed.clear()
+        t0 = time.perf_counter()
+
+        def client():
+            for i in range(n):
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                s = pool[picks[i]]
+                futs.append(srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, str(precs[i])))
+
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        for f in futs:
+            f.result(timeout=600)
+        st = srv.stats()
+        st["offered_rate"] = rate
+        st["frequencies_per_request_mean"] = float(np.mean([pool[k].nf for k in picks]))
+        per_rate[str(int(rate))] = st
+    srv.close()
+    # plain one-at-a-time FP64 path (plans reused, plan creation not timed)
+    plans = {}
+    sample = pool[:48]
+    dev = torch.device("cuda:0")
+    tens = [(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
+             torch.tensor(s.dy, device=dev)) for s in sample]
+    for s in sample:
+        if s.nf not in plans:
+            plans[s.nf] = nl.Plan(s.nd, s.nf, 1e-9, "fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, (t, y, dy) in zip(sample, tens):
+        plans[s.nf].execute(t, y, dy, s.f0, s.df)
+    torch.cuda.synchronize()
+    plain = len(sample) / (time.perf_counter() - t0)
+    for p in plans.values():
+        p.close()
+    top = per_rate[str(int(rates[-1]))]
+    line = {
+        "metric": METRIC, "value": top.get("periodograms_per_s"), "unit": UNIT, "n_gpus": world,
+        "steps": None, "warmup": 1, "p50_ms": top.get("p50_ms"), "p99_ms": top.get("p99_ms"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals of ragged-mix series (Nd log-uniform "
+                               "in [100, 1e5], Nf = 12 Nd), 50/50 FP32 eps 1e-6 / FP64 eps 1e-9, "
+                               "60 GB admission budget, 2 streams",
+                   "pool_series": len(pool), "duration_s": duration},
+        "per_rate": per_rate,
+        "plain_fp64_one_at_a_time": {"value": plain, "unit": UNIT, "series": len(sample)},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("uniform_batch", "ragged_batch"):
         return run_batch(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 
