@@ -688,7 +688,7 @@ def run_serving(args):
     srv.close()
     # plain one-at-a-time FP64 path (plans reused, plan creation not timed)
     plans = {}
-    sample = pool[:48]
+    sample = [pool[k] for k in np.random.default_rng(3).integers(0, len(pool), 96)]
     dev = torch.device("cuda:0")
     tens = [(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
              torch.tensor(s.dy, device=dev)) for s in sample]

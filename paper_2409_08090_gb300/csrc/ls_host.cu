@@ -1019,13 +1019,16 @@ ls_status ls_sync(ls_plan_t p)
     if (!p) return LS_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return LS_ERR_CUDA;
-    cudaError_t e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    // Everything on the plan's own stream: a copy on the legacy default stream
+    // would also wait for work that other plans have queued on other streams.
     int h = 0;
-    e = cudaMemcpy(&h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(&h, p->ws.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                    p->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_status(e);
     if (h) {
-        e = cudaMemset(p->ws.status, 0, sizeof(int));
+        e = cudaMemsetAsync(p->ws.status, 0, sizeof(int), p->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (h & kStatBadInput) return LS_ERR_ARG;

@@ -147,6 +147,16 @@ class _Slot:
         self.out_host = None
         self.plan = None
         self.keep = None        # device tensors alive until the batch completes
+        self.pin_in = None      # pinned staging reused across batches
+        self.pin_out = None
+
+    def pinned(self, which: str, n: int):
+        import torch
+        buf = getattr(self, which)
+        if buf is None or buf.numel() < n:
+            buf = torch.empty(max(n, 1 << 16) * 5 // 4, dtype=torch.float64).pin_memory()
+            setattr(self, which, buf)
+        return buf[:n]
 
 
 class PeriodogramServer:
@@ -235,12 +245,13 @@ class PeriodogramServer:
         offsets = np.zeros(len(batch) + 1, dtype=np.int64)
         offsets[1:] = np.cumsum([r.nd for r in batch])
         nfs = np.array([r.nf for r in batch], dtype=np.int64)
-        host = torch.empty(3 * int(offsets[-1]), dtype=torch.float64).pin_memory()
-        hv = host.numpy()
         n = int(offsets[-1])
-        hv[:n] = np.concatenate([r.t for r in batch])
-        hv[n:2 * n] = np.concatenate([r.y for r in batch])
-        hv[2 * n:] = np.concatenate([np.ones(r.nd) if r.dy is None else r.dy for r in batch])
+        host = slot.pinned("pin_in", 3 * n)
+        hv = host.numpy()
+        for r, a in zip(batch, offsets[:-1]):
+            hv[a:a + r.nd] = r.t
+            hv[n + a:n + a + r.nd] = r.y
+            hv[2 * n + a:2 * n + a + r.nd] = 1.0 if r.dy is None else r.dy
         plan = self._plan(slot, batch[0].key)
         with torch.cuda.stream(slot.stream):
             dev = host.to(self.device, non_blocking=True)
@@ -248,7 +259,7 @@ class PeriodogramServer:
             _, out_off = plan.execute_batch(dev[:n], dev[n:2 * n], dev[2 * n:], offsets,
                                             [r.f0 for r in batch], [r.df for r in batch], nfs,
                                             out=out, sync=False)
-            out_host = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
+            out_host = slot.pinned("pin_out", out.numel())
             out_host.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(slot.stream)
