@@ -658,12 +658,16 @@ def run_serving(args):
     for f in warm:
         f.result(timeout=600)
     per_rate = {}
-    for rate in rates:
+    runs = [(r, "mixed") for r in rates] + [(rates[-1], "fp32"), (4 * rates[-1], "fp32")]
+    for rate, mix in runs:
         n = max(16, int(rate * duration))
         arrivals = W.poisson_arrivals(rate, n, seed=int(rate))
         rng = np.random.default_rng(int(rate) + 1)
         picks = rng.integers(0, len(pool), n)
-        precs = np.where(rng.random(n) < 0.5, "fp32", "fp64")
+        if mix == "mixed":
+            precs = np.where(rng.random(n) < 0.5, "fp32", "fp64")
+        else:
+            precs = np.full(n, "fp32")
         futs = []
         srv.completed.clear()
         t0 = time.perf_counter()
@@ -683,8 +687,9 @@ def run_serving(args):
             f.result(timeout=600)
         st = srv.stats()
         st["offered_rate"] = rate
+        st["precisions"] = "50/50 fp32 eps 1e-6 / fp64 eps 1e-9" if mix == "mixed" else "fp32 eps 1e-6"
         st["frequencies_per_request_mean"] = float(np.mean([pool[k].nf for k in picks]))
-        per_rate[str(int(rate))] = st
+        per_rate[(str(int(rate)) if mix == "mixed" else f"{int(rate)}_fp32")] = st
     srv.close()
     # plain one-at-a-time FP64 path (plans reused, plan creation not timed)
     plans = {}
@@ -692,15 +697,17 @@ def run_serving(args):
     dev = torch.device("cuda:0")
     tens = [(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
              torch.tensor(s.dy, device=dev)) for s in sample]
-    for s in sample:
-        if s.nf not in plans:
-            plans[s.nf] = nl.Plan(s.nd, s.nf, 1e-9, "fp64")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, (t, y, dy) in zip(sample, tens):
-        plans[s.nf].execute(t, y, dy, s.f0, s.df)
-    torch.cuda.synchronize()
-    plain = len(sample) / (time.perf_counter() - t0)
+    plain = {}
+    for eps64 in (1e-9, 1e-6):
+        for s in sample:
+            if (s.nf, eps64) not in plans:
+                plans[(s.nf, eps64)] = nl.Plan(s.nd, s.nf, eps64, "fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s, (t, y, dy) in zip(sample, tens):
+            plans[(s.nf, eps64)].execute(t, y, dy, s.f0, s.df)
+        torch.cuda.synchronize()
+        plain[f"eps_{eps64:g}"] = len(sample) / (time.perf_counter() - t0)
     for p in plans.values():
         p.close()
     top = per_rate[str(int(rates[-1]))]
@@ -714,7 +721,8 @@ def run_serving(args):
                                "60 GB admission budget, 2 streams",
                    "pool_series": len(pool), "duration_s": duration},
         "per_rate": per_rate,
-        "plain_fp64_one_at_a_time": {"value": plain, "unit": UNIT, "series": len(sample)},
+        "plain_fp64_one_at_a_time": {"value_by_eps": plain, "unit": UNIT, "series": len(sample),
+                                     "note": "ls_execute per request, plans reused, same pool"},
     }
     print(json.dumps(line), flush=True)
     return 0
