@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--upsampling", type=float, default=0.0,
                     help="fine-grid upsampling: 0 (plan chooses), 2.0 or 1.5")
+    ap.add_argument("--serving-results", default="host", choices=["host", "device"],
+                    help="serving: deliver results as host arrays or device tensor views")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -651,7 +653,8 @@ def run_serving(args):
     pool = W.ragged_batch(seed=W.BASE_SEED + 4, nseries=max(64, int(600 * args.batch_scale)))
     rates = [200.0, 1000.0, 5000.0]
     duration = 2.0 * args.batch_scale
-    srv = PeriodogramServer(memory_budget=60 << 30, streams=2, max_batch=4096)
+    srv = PeriodogramServer(memory_budget=60 << 30, streams=2, max_batch=4096,
+                            results=args.serving_results)
     # warm the plans and grid classes once
     warm = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, p) for s in pool[:32]
             for p in ("fp32", "fp64")]
@@ -719,6 +722,7 @@ def run_serving(args):
         "config": {"workload": "serving: Poisson arrivals of ragged-mix series (Nd log-uniform "
                                "in [100, 1e5], Nf = 12 Nd), 50/50 FP32 eps 1e-6 / FP64 eps 1e-9, "
                                "60 GB admission budget, 2 streams",
+                   "results": args.serving_results,
                    "pool_series": len(pool), "duration_s": duration},
         "per_rate": per_rate,
         "plain_fp64_one_at_a_time": {"value_by_eps": plain, "unit": UNIT, "series": len(sample),

@@ -930,8 +930,15 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
-    err = cudaFuncSetAttribute(k_passA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
-    if (err != cudaSuccess) return err;
+    static thread_local int smA_set[64];   // attribute already raised to this size, per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || smA_set[dev] < (int)smA) {
+        err = cudaFuncSetAttribute(k_passA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smA);
+        if (err != cudaSuccess) return err;
+        if (dev >= 0 && dev < 64) smA_set[dev] = (int)smA;
+    }
     k_passA<T><<<dim3(g.nbins, shared ? S + 2 : 3 * S), kThreadsA, smA, st>>>(A);
 
     if (ev) cudaEventRecord(ev[3], st);
@@ -951,8 +958,13 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // arithmetic uses 1e-15).
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
-    err = cudaFuncSetAttribute(k_passB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
-    if (err != cudaSuccess) return err;
+    static thread_local int smB_set[64];
+    if (dev < 0 || dev >= 64 || smB_set[dev] < (int)smB) {
+        err = cudaFuncSetAttribute(k_passB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smB);
+        if (err != cudaSuccess) return err;
+        if (dev >= 0 && dev < 64) smB_set[dev] = (int)smB;
+    }
     k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();

@@ -162,13 +162,15 @@ class _Slot:
 class PeriodogramServer:
     """Continuous-batching periodogram server on one GPU.
 
-    submit() returns a Future resolved with the float64 numpy power array.
+    submit() returns a Future resolved with the float64 power: a numpy array
+    (results="host"), or a view of the batch's CUDA tensor (results="device",
+    no host copy; the batch's device memory lives as long as any view).
     `streams` batches can be on the GPU at once; requests arriving meanwhile
     are admitted (memory permitting) into the next batch.
     """
 
     def __init__(self, device: int = 0, memory_budget: int = 60 << 30, streams: int = 2,
-                 max_batch: int = 4096):
+                 max_batch: int = 4096, results: str = "host"):
         import torch
 
         import paper_2409_08090_gb300 as nl
@@ -176,6 +178,9 @@ class PeriodogramServer:
         nl.load_library()
         self.device = int(device)
         torch.cuda.set_device(self.device)
+        if results not in ("host", "device"):
+            raise ValueError("results must be 'host' (numpy arrays) or 'device' (CUDA tensors)")
+        self.results = results
         self.sched = Scheduler(memory_budget, max_batch)
         self.slots = [_Slot(self.device) for _ in range(max(1, int(streams)))]
         self.cv = threading.Condition()
@@ -259,8 +264,11 @@ class PeriodogramServer:
             _, out_off = plan.execute_batch(dev[:n], dev[n:2 * n], dev[2 * n:], offsets,
                                             [r.f0 for r in batch], [r.df for r in batch], nfs,
                                             out=out, sync=False)
-            out_host = slot.pinned("pin_out", out.numel())
-            out_host.copy_(out, non_blocking=True)
+            if self.results == "host":
+                out_host = slot.pinned("pin_out", out.numel())
+                out_host.copy_(out, non_blocking=True)
+            else:
+                out_host = out
             ev = torch.cuda.Event()
             ev.record(slot.stream)
         slot.batch = batch
@@ -275,13 +283,15 @@ class PeriodogramServer:
         batch, (out_host, out_off) = slot.batch, slot.out_host
         st = nl.ls_sync(slot.plan.handle)
         now = time.perf_counter()
-        res = out_host.numpy()
+        res = out_host.numpy() if self.results == "host" else out_host
         for r, o in zip(batch, out_off):
             r.done = now
             if st != nl.LS_OK:
                 r.future.set_exception(nl.LSError(st, "batch"))
-            else:
+            elif self.results == "host":
                 r.future.set_result(res[o:o + r.nf].copy())
+            else:
+                r.future.set_result(res[int(o):int(o) + r.nf])
         self.completed.extend(batch)
         self.sched.release(batch)
         slot.batch = slot.done_event = slot.out_host = slot.keep = None
