@@ -49,6 +49,11 @@ def _load():
                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p]
+            lib.ls_oracle_power_ex.restype = ctypes.c_int
+            lib.ls_oracle_power_ex.argtypes = [
+                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_void_p,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.ls_oracle_threads.restype = ctypes.c_int
             lib.ls_oracle_threads.argtypes = []
             _lib = lib
@@ -60,11 +65,19 @@ def threads() -> int:
     return int(_load().ls_oracle_threads())
 
 
-def periodogram(t, y, dy, f0: float, df: float, k, return_sums: bool = False):
+NORMALIZATIONS = ("standard", "model", "log", "psd")
+
+
+def periodogram(t, y, dy, f0: float, df: float, k, return_sums: bool = False,
+                fit_mean: bool = True, center_data: bool = True,
+                normalization: str = "standard"):
     """Direct FP64 periodogram at frequencies ``f0 + k*df`` for integer array ``k``.
 
-    ``dy`` may be None (unit errors).  Returns ``P`` (float64, len(k)), and with
-    ``return_sums`` also an array (len(k), 7) of (Ch, Sh, C, S, C2, S2, YY).
+    ``dy`` may be None (unit errors).  ``fit_mean``, ``center_data`` and
+    ``normalization`` select the model variant of the Astropy interface (the
+    definitions are in ``ls_oracle.c``'s header).  Returns ``P`` (float64,
+    len(k)), and with ``return_sums`` also an array (len(k), 7) of
+    (Ch, Sh, C, S, C2, S2, YY).
     """
     lib = _load()
     t = np.ascontiguousarray(t, dtype=np.float64)
@@ -78,9 +91,13 @@ def periodogram(t, y, dy, f0: float, df: float, k, return_sums: bool = False):
     k = np.ascontiguousarray(k, dtype=np.int64)
     P = np.empty(k.shape[0], dtype=np.float64)
     sums = np.empty((k.shape[0], 7), dtype=np.float64) if return_sums else None
-    rc = lib.ls_oracle_power(t.shape[0], t.ctypes.data, y.ctypes.data, dyp,
-                             float(f0), float(df), k.shape[0], k.ctypes.data,
-                             P.ctypes.data, sums.ctypes.data if sums is not None else None)
+    if normalization not in NORMALIZATIONS:
+        raise ValueError(f"normalization must be one of {NORMALIZATIONS}")
+    rc = lib.ls_oracle_power_ex(t.shape[0], t.ctypes.data, y.ctypes.data, dyp,
+                                float(f0), float(df), k.shape[0], k.ctypes.data,
+                                int(bool(fit_mean)), int(bool(center_data)),
+                                NORMALIZATIONS.index(normalization),
+                                P.ctypes.data, sums.ctypes.data if sums is not None else None)
     if rc != 0:
-        raise ValueError("oracle rejected the input (N_d < 1, dy <= 0 or constant y)")
+        raise ValueError("oracle rejected the input (N_d < 1, dy <= 0 or vanishing YY)")
     return (P, sums) if return_sums else P

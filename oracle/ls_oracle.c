@@ -25,6 +25,21 @@
  *     CC_tau = (1 + C2 cos2 + S2 sin2)/2 - C_tau^2,
  *     SS_tau = (1 - C2 cos2 - S2 sin2)/2 - S_tau^2,  YY = sum w^ (y-ybar)^2.
  *
+ *
+ * Model variants (ls_oracle_power_ex).  The package is a backend of the Astropy
+ * Lomb-Scargle interface (Sec. 1), whose options select the model and the
+ * normalisation.  With p = YC_tau^2/CC_tau + YS_tau^2/SS_tau:
+ *   - fit_mean = 0: no offset in the model, so C and S drop out:
+ *     tan(2 w tau) = S2 / C2, CC_tau = (1 + C2 cos2 + S2 sin2)/2,
+ *     SS_tau = (1 - C2 cos2 - S2 sin2)/2.
+ *   - center = 0 (meaningful only with fit_mean = 0; a fitted offset always
+ *     works on centred data): y' = y and YY = sum w^ y^2.
+ *   - normalisation 0 standard p / YY; 1 model p / (YY - p);
+ *     2 log -ln(1 - p / YY); 3 psd p W / 2 with W = sum w (unnormalised).
+ *   In least-squares terms (chi2 with the unnormalised weights w, chi2_ref of
+ *   the model without its sinusoid): standard 1 - chi2/chi2_ref, model
+ *   chi2_ref/chi2 - 1, log ln(chi2_ref/chi2), psd (chi2_ref - chi2)/2.
+ *
  * Arithmetic: FP64 throughout.  The inputs are treated as exact reals: the
  * phase f_k t_j (in cycles) is formed with error-free products (fma) in
  * double-double and reduced modulo 1 before sin/cos, so the long-baseline
@@ -55,10 +70,10 @@ static double phase_cycles(double f0, double df, int64_t k, double t)
     return s - rint(s);
 }
 
-/* Weighted mean and normalised weights (shared by every frequency).
- * Returns 0 on success, -1 if the inputs are unusable. */
-static int prepare(int64_t nd, const double *y, const double *dy,
-                   double *what, double *yc, double *yy_out)
+/* Weighted mean and normalised weights (shared by every frequency); y' = y - ybar
+ * when centring, else y.  Returns 0 on success, -1 if the inputs are unusable. */
+static int prepare(int64_t nd, const double *y, const double *dy, int center,
+                   double *what, double *yc, double *yy_out, double *W_out)
 {
     double W = 0.0;
     for (int64_t j = 0; j < nd; ++j) {
@@ -72,6 +87,7 @@ static int prepare(int64_t nd, const double *y, const double *dy,
         what[j] /= W;
         ybar += what[j] * y[j];
     }
+    if (!center) ybar = 0.0;
     double yy = 0.0, y2 = 0.0;
     for (int64_t j = 0; j < nd; ++j) {
         yc[j] = y[j] - ybar;
@@ -82,49 +98,64 @@ static int prepare(int64_t nd, const double *y, const double *dy,
      * periodogram. */
     if (!(yy > 1e-24 * y2)) return -1;
     *yy_out = yy;
+    *W_out = W;
     return 0;
 }
 
-/* Power from the six sums and YY (see the file header). */
+/* Power from the six sums, YY and W (see the file header). */
 static double power_from_sums(double Ch, double Sh, double C, double S,
-                              double C2, double S2, double YY)
+                              double C2, double S2, double YY, double W,
+                              int fit_mean, int norm)
 {
-    double two_wtau = atan2(S2 - 2.0 * C * S, C2 - (C * C - S * S));
+    double two_wtau = fit_mean ? atan2(S2 - 2.0 * C * S, C2 - (C * C - S * S))
+                               : atan2(S2, C2);
     double wtau = 0.5 * two_wtau;
     double c = cos(wtau), s = sin(wtau);
     double c2 = cos(two_wtau), s2 = sin(two_wtau);
     double YC = Ch * c + Sh * s;
     double YS = Sh * c - Ch * s;
-    double Ct = C * c + S * s;
-    double St = S * c - C * s;
-    double CC = 0.5 * (1.0 + C2 * c2 + S2 * s2) - Ct * Ct;
-    double SS = 0.5 * (1.0 - C2 * c2 - S2 * s2) - St * St;
+    double CC = 0.5 * (1.0 + C2 * c2 + S2 * s2);
+    double SS = 0.5 * (1.0 - C2 * c2 - S2 * s2);
+    if (fit_mean) {
+        double Ct = C * c + S * s;
+        double St = S * c - C * s;
+        CC -= Ct * Ct;
+        SS -= St * St;
+    }
     /* A vanishing CC or SS (all phases equal mod pi) carries no information:
      * that term of the fit is absent. */
     double p = 0.0;
     if (CC > 1e-15) p += YC * YC / CC;
     if (SS > 1e-15) p += YS * YS / SS;
-    return p / YY;
+    switch (norm) {
+    case 1: return p / (YY - p);
+    case 2: return -log(1.0 - p / YY);
+    case 3: return 0.5 * W * p;
+    default: return p / YY;
+    }
 }
 
 /*
- * ls_oracle_power: periodogram at the frequencies f0 + k[i] df, i < nk.
+ * ls_oracle_power_ex: periodogram at the frequencies f0 + k[i] df, i < nk.
  *   t, y: nd FP64 values; dy: nd FP64 values or NULL (all ones).
+ *   fit_mean, center, norm: the model variant (file header); fit_mean = 1
+ *   always centres.
  *   power: nk outputs.  sums: NULL or nk*7 outputs, per frequency
  *   (Ch, Sh, C, S, C2, S2, YY) as defined in the file header.
- * Returns 0, or -1 for nd < 1, a non-positive dy, or a constant y
- * (YY <= 1e-24 sum w^ y^2, i.e. zero up to rounding).
+ * Returns 0, or -1 for nd < 1, a non-positive dy, an unknown norm, or a
+ * vanishing YY (YY <= 1e-24 sum w^ y^2, i.e. zero up to rounding).
  */
-int ls_oracle_power(int64_t nd, const double *t, const double *y, const double *dy,
-                    double f0, double df, int64_t nk, const int64_t *k,
-                    double *power, double *sums)
+int ls_oracle_power_ex(int64_t nd, const double *t, const double *y, const double *dy,
+                       double f0, double df, int64_t nk, const int64_t *k,
+                       int fit_mean, int center, int norm, double *power, double *sums)
 {
-    if (nd < 1 || nk < 0) return -1;
+    if (nd < 1 || nk < 0 || norm < 0 || norm > 3) return -1;
+    if (fit_mean) center = 1;
     double *what = (double *)malloc(sizeof(double) * (size_t)nd);
     double *yc = (double *)malloc(sizeof(double) * (size_t)nd);
     if (!what || !yc) { free(what); free(yc); return -1; }
-    double YY;
-    int rc = prepare(nd, y, dy, what, yc, &YY);
+    double YY, W;
+    int rc = prepare(nd, y, dy, center, what, yc, &YY, &W);
     if (rc == 0) {
 #pragma omp parallel for schedule(dynamic, 4)
         for (int64_t i = 0; i < nk; ++i) {
@@ -142,7 +173,7 @@ int ls_oracle_power(int64_t nd, const double *t, const double *y, const double *
                 C2 += what[j] * cs2;
                 S2 += what[j] * sn2;
             }
-            power[i] = power_from_sums(Ch, Sh, C, S, C2, S2, YY);
+            power[i] = power_from_sums(Ch, Sh, C, S, C2, S2, YY, W, fit_mean, norm);
             if (sums) {
                 double *o = sums + 7 * i;
                 o[0] = Ch; o[1] = Sh; o[2] = C; o[3] = S; o[4] = C2; o[5] = S2; o[6] = YY;
@@ -152,6 +183,14 @@ int ls_oracle_power(int64_t nd, const double *t, const double *y, const double *
     free(what);
     free(yc);
     return rc;
+}
+
+/* The default model: floating mean, standard normalisation. */
+int ls_oracle_power(int64_t nd, const double *t, const double *y, const double *dy,
+                    double f0, double df, int64_t nk, const int64_t *k,
+                    double *power, double *sums)
+{
+    return ls_oracle_power_ex(nd, t, y, dy, f0, df, nk, k, 1, 1, 0, power, sums);
 }
 
 /* Number of threads the parallel loop above uses. */

@@ -68,6 +68,21 @@ def test_results_in_the_mix_equal_results_alone(nl):
         assert np.max(np.abs(P - A)) <= tol
 
 
+def test_device_results_equal_host_results(nl):
+    import torch
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    reqs = [W.ragged_series(2000 + i, nd_lo=100, nd_hi=3000) for i in range(10)]
+    out = {}
+    for mode in ("host", "device"):
+        srv = PeriodogramServer(memory_budget=256 << 20, streams=2, max_batch=4, results=mode)
+        futs = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, "fp32", 1e-6) for s in reqs]
+        out[mode] = [f.result(timeout=120) for f in futs]
+        srv.close()
+    for s, a, b in zip(reqs, out["host"], out["device"]):
+        assert isinstance(b, torch.Tensor) and b.is_cuda and b.shape == (s.nf,)
+        assert np.max(np.abs(a - b.cpu().numpy())) <= 1e-6
+
+
 def test_invalid_and_oversized_requests_fail_their_futures_only(nl):
     from paper_2409_08090_gb300.serving import PeriodogramServer
     srv = PeriodogramServer(memory_budget=8 << 20, streams=1)
