@@ -49,7 +49,26 @@ typedef enum {
     LS_ERR_UNSUPPORTED = 6  /* valid request outside what this build implements  */
 } ls_status;
 
-typedef enum { LS_NORM_STANDARD = 0 } ls_norm;
+/*
+ * Normalisation and model (the `norm` argument of the execute calls): one
+ * ls_norm value, optionally OR'ed with the model flags below.  These are the
+ * options of the Astropy Lomb-Scargle interface that nifty-ls backs (Sec. 1).
+ * With chi2 the weighted residual (w = 1/dy^2) of the best sinusoid model at
+ * f_k and chi2_ref that of the model without the sinusoid:
+ */
+typedef enum {
+    LS_NORM_STANDARD = 0,   /* 1 - chi2/chi2_ref, in [0, 1]                         */
+    LS_NORM_MODEL = 1,      /* chi2_ref/chi2 - 1 = P/(1 - P)                         */
+    LS_NORM_LOG = 2,        /* ln(chi2_ref/chi2) = -ln(1 - P) (P >= 1 gives inf/NaN) */
+    LS_NORM_PSD = 3         /* (chi2_ref - chi2)/2                                  */
+} ls_norm;
+/* Model flags.  Default: floating mean (y ~ a cos + b sin + c on centred y).
+ * LS_NO_FIT_MEAN: y ~ a cos + b sin, no offset; the transform of w^ at f is
+ *   then not needed and is skipped (two transforms per series, not three).
+ * LS_NO_CENTER: with LS_NO_FIT_MEAN, y is used as given instead of y - ybar;
+ *   ignored with a fitted mean (the offset absorbs the mean). */
+#define LS_NO_FIT_MEAN 0x100
+#define LS_NO_CENTER 0x200
 
 /* Arithmetic of the spread, the fine-grid FFT and the deconvolution.  In both
  * precisions the phase reduction t*df mod 1, the pre-phase exp(2 pi i fc t),
@@ -121,8 +140,9 @@ ls_status ls_set_stream(ls_plan_t plan, void *stream);
  *   f0, df   grid f_k = f0 + k df; df > 0; both finite.
  *   nf       1 <= nf <= the plan's nf.
  *   eps      >= the plan's eps (the plan's accuracy is then sufficient).
- *   norm     LS_NORM_STANDARD (others: LS_ERR_UNSUPPORTED).
- *   power    nf outputs, P_k in [0, 1].
+ *   norm     an ls_norm value OR'ed with model flags (LS_NO_FIT_MEAN,
+ *            LS_NO_CENTER); other bits: LS_ERR_UNSUPPORTED.
+ *   power    nf outputs (standard normalisation: P_k in [0, 1]).
  * The inputs are taken as exact reals: phases are reduced in double-double,
  * so a time offset does not cost accuracy.
  */
@@ -135,7 +155,9 @@ ls_status ls_execute(ls_plan_t plan, const double *t, const double *y, const dou
  * Eq. 1 for every frequency, sums[6*k + {0..5}] = (Ch, Sh, C, S, C2, S2) with
  * Ch + i Sh = sum_j w^_j (y_j - ybar) e^{2 pi i f_k t_j},
  * C + i S = sum_j w^_j e^{2 pi i f_k t_j}, C2 + i S2 = sum_j w^_j e^{4 pi i f_k t_j}.
- * `power` may be NULL.  Meant for validating the NUFFT stage.
+ * `power` may be NULL.  Meant for validating the NUFFT stage.  With
+ * LS_NO_FIT_MEAN the transform of w^ at f is skipped and C, S are written as 0;
+ * with LS_NO_CENTER, Ch and Sh use y instead of y - ybar.
  */
 ls_status ls_execute_sums(ls_plan_t plan, const double *t, const double *y, const double *dy,
                           int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
@@ -157,7 +179,7 @@ ls_status ls_execute_sums(ls_plan_t plan, const double *t, const double *y, cons
  *   nf           host int64[nseries] (>= 1).
  *   out_offsets  host int64[nseries]: P_k of series s goes to
  *                power[out_offsets[s] + k], k < nf[s].
- *   eps          >= the plan's eps.  norm: LS_NORM_STANDARD.
+ *   eps          >= the plan's eps.  norm: as for ls_execute, for every series.
  *   power        device array.
  * Asynchronous like ls_execute with device buffers; a non-finite value,
  * dy <= 0 or a constant series in any series is reported by ls_sync.

@@ -17,13 +17,16 @@ import threading
 from . import build as _build
 
 __all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
-           "LS_NORM_STANDARD", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
+           "LS_NORM_STANDARD", "LS_NORM_MODEL", "LS_NORM_LOG", "LS_NORM_PSD",
+           "LS_NO_FIT_MEAN", "LS_NO_CENTER", "NORMALIZATIONS", "mode_word", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
            "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_execute_batch_shared", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES"]
 
 LS_FP64, LS_FP32 = 0, 1
-LS_NORM_STANDARD = 0
+LS_NORM_STANDARD, LS_NORM_MODEL, LS_NORM_LOG, LS_NORM_PSD = range(4)
+LS_NO_FIT_MEAN, LS_NO_CENTER = 0x100, 0x200
+NORMALIZATIONS = ("standard", "model", "log", "psd")
 LS_OK, LS_ERR_ARG, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT, LS_ERR_DEGENERATE, \
     LS_ERR_UNSUPPORTED = range(7)
 
@@ -242,8 +245,26 @@ def _prec_code(precision) -> int:
     raise ValueError(f"unknown precision {precision!r}")
 
 
+def mode_word(normalization: str = "standard", fit_mean: bool = True,
+              center_data: bool = True) -> int:
+    """The ``norm`` argument of the execute calls: an ls_norm value OR'ed with
+    LS_NO_FIT_MEAN / LS_NO_CENTER (the Astropy interface's options)."""
+    if normalization not in NORMALIZATIONS:
+        raise ValueError(f"normalization must be one of {NORMALIZATIONS}")
+    word = NORMALIZATIONS.index(normalization)
+    if not fit_mean:
+        word |= LS_NO_FIT_MEAN
+        if not center_data:
+            word |= LS_NO_CENTER
+    return word
+
+
 class Plan:
-    """Owns one ``ls_plan`` (workspace + tables for ``nf`` frequencies at ``eps``)."""
+    """Owns one ``ls_plan`` (workspace + tables for ``nf`` frequencies at ``eps``).
+
+    Every execute method takes the model options as keywords:
+    ``normalization`` ("standard", "model", "log", "psd"), ``fit_mean`` and
+    ``center_data`` (see ``mode_word``)."""
 
     def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
                  device: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0):
@@ -269,7 +290,7 @@ class Plan:
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def execute(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
-                out=None, sums=None, sync: bool = True):
+                out=None, sums=None, sync: bool = True, **model):
         """Periodogram of one series.  ``t, y, dy`` are float64 CUDA tensors on the
         plan's device (``dy`` may be None); returns ``out`` (float64, nf)."""
         import torch
@@ -285,17 +306,17 @@ class Plan:
         dyp = dy.data_ptr() if dy is not None else None
         if sums is not None:
             st = ls_execute_sums(self.handle, t.data_ptr(), y.data_ptr(), dyp, nd, f0, df, nf,
-                                 eps, LS_NORM_STANDARD, out.data_ptr(), sums.data_ptr())
+                                 eps, mode_word(**model), out.data_ptr(), sums.data_ptr())
         else:
             st = ls_execute(self.handle, t.data_ptr(), y.data_ptr(), dyp, nd, f0, df, nf, eps,
-                            LS_NORM_STANDARD, out.data_ptr())
+                            mode_word(**model), out.data_ptr())
         _check(st, "ls_execute")
         if sync:
             _check(ls_sync(self.handle), "ls_execute (device status)")
         return out
 
     def execute_batch(self, t, y, dy, offsets, f0, df, nf, eps=None, out=None,
-                      sync: bool = True):
+                      sync: bool = True, **model):
         """Periodograms of a ragged batch.  ``t, y, dy``: concatenated float64 CUDA
         tensors (``dy`` may be None); ``offsets``: nseries+1 point offsets;
         ``f0, df, nf``: per-series grids (sequences).  Returns ``(power, out_offsets)``
@@ -318,14 +339,14 @@ class Plan:
         st = ls_execute_batch(self.handle, ns, offsets.ctypes.data, t.data_ptr(), y.data_ptr(),
                               dy.data_ptr() if dy is not None else None, f0.ctypes.data,
                               df.ctypes.data, nf.ctypes.data, out_off.ctypes.data, eps,
-                              LS_NORM_STANDARD, out.data_ptr())
+                              mode_word(**model), out.data_ptr())
         _check(st, "ls_execute_batch")
         if sync:
             _check(ls_sync(self.handle), "ls_execute_batch (device status)")
         return out, out_off
 
     def execute_shared(self, t, Y, dy, f0: float, df: float, nf: int, eps=None, out=None,
-                       sync: bool = True):
+                       sync: bool = True, **model):
         """Uniform batch: series Y[s] (a 2-D float64 CUDA tensor, one row per
         series) all observed at times ``t`` with uncertainties ``dy`` (or None).
         Returns power as a (nseries, nf) tensor."""
@@ -337,14 +358,14 @@ class Plan:
         ls_set_stream(self.handle, self._stream())
         st = ls_execute_batch_shared(self.handle, ns, nd, t.data_ptr(), Y.data_ptr(),
                                      dy.data_ptr() if dy is not None else None, f0, df, nf, eps,
-                                     LS_NORM_STANDARD, out.data_ptr())
+                                     mode_word(**model), out.data_ptr())
         _check(st, "ls_execute_batch_shared")
         if sync:
             _check(ls_sync(self.handle), "ls_execute_batch_shared (device status)")
         return out
 
     def execute_host(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None,
-                     out=None):
+                     out=None, **model):
         """Same, with host (numpy float64) buffers: the library copies in and out."""
         import numpy as np
         nf = int(self.info.nf if nf is None else nf)
@@ -359,7 +380,7 @@ class Plan:
             out = np.empty(nf, dtype=np.float64)
         ls_set_stream(self.handle, self._stream())
         st = ls_execute(self.handle, t.ctypes.data, y.ctypes.data, dyp, t.shape[0], f0, df, nf,
-                        eps, LS_NORM_STANDARD, out.ctypes.data)
+                        eps, mode_word(**model), out.ctypes.data)
         _check(st, "ls_execute")
         return out
 
@@ -368,8 +389,10 @@ _plan_cache: dict = {}
 
 
 def lombscargle(t, y, dy=None, *, f0: float, df: float, nf: int, eps: float = 1e-9,
-                precision="fp64", device: int = 0):
-    """Floating-mean, standard-normalised Lomb-Scargle power at f0 + k df, k < nf.
+                precision="fp64", device: int = 0, normalization: str = "standard",
+                fit_mean: bool = True, center_data: bool = True):
+    """Lomb-Scargle power at f0 + k df, k < nf (default: floating mean,
+    standard normalisation; the keywords select the other variants).
 
     Accepts float64 CUDA tensors (result: CUDA tensor) or array-likes (result:
     numpy array, host buffers copied by the library).  Plans are cached per
@@ -389,6 +412,7 @@ def lombscargle(t, y, dy=None, *, f0: float, df: float, nf: int, eps: float = 1e
             plan.close()
         plan = Plan(max(nd, 2), nf, eps, prec, device)
         _plan_cache[key] = plan
+    model = dict(normalization=normalization, fit_mean=fit_mean, center_data=center_data)
     if is_tensor:
-        return plan.execute(t, y, dy, f0, df, nf, eps)
-    return plan.execute_host(t, y, dy, f0, df, nf, eps)
+        return plan.execute(t, y, dy, f0, df, nf, eps, **model)
+    return plan.execute_host(t, y, dy, f0, df, nf, eps, **model)

@@ -480,6 +480,16 @@ void destroy_timing(ls_plan_s *p)
     p->t_pending = 0;
 }
 
+static_assert(LS_NO_FIT_MEAN == kModeNoFit && LS_NO_CENTER == kModeNoCenter,
+              "model flags of the C-ABI and the kernels agree");
+
+// The norm word: a normalisation in bits 0-7 plus model flags.
+bool mode_supported(int norm)
+{
+    return (norm & ~(kModeNormMask | kModeNoFit | kModeNoCenter)) == 0 &&
+           (norm & kModeNormMask) <= LS_NORM_PSD;
+}
+
 ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const double *dy,
                        int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
                        double *power, double *sums)
@@ -490,7 +500,7 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
     if (nf < 1 || nf > p->nf) return LS_ERR_ARG;
     if (!(df > 0.0) || !isfinite(df) || !isfinite(f0)) return LS_ERR_ARG;
     if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
-    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    if (!mode_supported(norm)) return LS_ERR_UNSUPPORTED;
     DeviceGuard guard(p->device);
     if (!guard.ok) return LS_ERR_CUDA;
     cudaStream_t st = p->stream;
@@ -537,9 +547,9 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
     }
     e = (p->prec == LS_FP32)
             ? launch_pipeline<float>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
-                                     dev_in[2], dpow, dsums, nred, st, ev)
+                                     dev_in[2], dpow, dsums, nred, st, ev, 0, norm)
             : launch_pipeline<double>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
-                                      dev_in[2], dpow, dsums, nred, st, ev);
+                                      dev_in[2], dpow, dsums, nred, st, ev, 0, norm);
     if (e != cudaSuccess) return cuda_status(e);
     if (host_power || host_sums) {
         if (host_power) {
@@ -728,7 +738,7 @@ ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s 
 template <typename T>
 ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
                        int64_t points, int64_t max_nd, const double *t, const double *y,
-                       const double *dy, double *power, int shared = 0)
+                       const double *dy, double *power, int shared, int mode)
 {
     const Geometry &g = sub->g;
     const int S = (int)descs.size();
@@ -754,7 +764,7 @@ ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDes
     bt.many = b.desc;
     bt.one = descs[0];
     e = launch_pipeline<T>(g, ws, b.cap_points, bt, max_nd, t, y, dy, power, nullptr, nred,
-                           p->stream, nullptr, shared);
+                           p->stream, nullptr, shared, mode);
     return cuda_status(e);
 }
 
@@ -859,7 +869,7 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
     if (!p || nseries < 0 || !offsets || !f0 || !df || !nf || !out_offsets) return LS_ERR_ARG;
     if (nseries == 0) return LS_OK;
     if (!t || !y || !power) return LS_ERR_ARG;
-    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    if (!mode_supported(norm)) return LS_ERR_UNSUPPORTED;
     if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return LS_ERR_CUDA;
@@ -929,8 +939,8 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
                 ++k;
             }
             st = (p->prec == LS_FP32)
-                     ? batch_launch<float>(p, sub, descs, points, max_nd, t, y, dy, power)
-                     : batch_launch<double>(p, sub, descs, points, max_nd, t, y, dy, power);
+                     ? batch_launch<float>(p, sub, descs, points, max_nd, t, y, dy, power, 0, norm)
+                     : batch_launch<double>(p, sub, descs, points, max_nd, t, y, dy, power, 0, norm);
             if (st != LS_OK) return st;
         }
         i = j;
@@ -946,7 +956,7 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     if (nseries == 0) return LS_OK;
     if (!t || !Y || !power || nd < 2 || nf < 1) return LS_ERR_ARG;
     if (!(df > 0.0) || !isfinite(df) || !isfinite(f0)) return LS_ERR_ARG;
-    if (norm != LS_NORM_STANDARD) return LS_ERR_UNSUPPORTED;
+    if (!mode_supported(norm)) return LS_ERR_UNSUPPORTED;
     if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
     DeviceGuard guard(p->device);
     if (!guard.ok) return LS_ERR_CUDA;
@@ -984,8 +994,8 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
             descs.push_back(d);
         }
         st = (p->prec == LS_FP32)
-                 ? batch_launch<float>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1)
-                 : batch_launch<double>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1);
+                 ? batch_launch<float>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm)
+                 : batch_launch<double>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm);
         if (st != LS_OK) return st;
         s0 += S;
     }

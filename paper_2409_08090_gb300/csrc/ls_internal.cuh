@@ -16,6 +16,13 @@ constexpr int kThreadsB = 256;
 constexpr int kMinN1 = 32;        // keeps every kernel footprint (w <= 16) within two columns
 
 // Device status word bits (sticky until ls_sync).
+// Model/normalisation word of the execute calls (the `norm` argument of the
+// C-ABI): bits 0-7 the normalisation (0 standard, 1 model, 2 log, 3 psd),
+// kModeNoFit: no offset in the model (C = S = 0, the w^ transform at f is not
+// taken), kModeNoCenter: with kModeNoFit, y is not centred.
+constexpr int kModeNormMask = 0xFF;
+constexpr int kModeNoFit = 0x100;
+constexpr int kModeNoCenter = 0x200;
 constexpr int kStatBadInput = 1;
 constexpr int kStatDegenerate = 2;
 
@@ -135,7 +142,7 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &b, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev, int shared = 0);
+                            cudaStream_t st, cudaEvent_t *ev, int shared = 0, int mode = 0);
 
 template <typename T>
 cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,

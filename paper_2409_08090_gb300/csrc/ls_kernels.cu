@@ -119,11 +119,12 @@ __device__ void reduce_partials(const double *partials, int nparts, int width, d
 // K1a: weights and weighted mean (FP64).  W = sum 1/dy^2, WY = sum y/dy^2,
 // WY2 = sum y^2/dy^2.  The one-pass variance WY2/W - ybar^2 only sets the
 // scale of the strengths (the power does not depend on it); the exact YY
-// comes from the second pass.
+// comes from the second pass.  Without centring (center = 0) ybar is taken as
+// 0 and the scale follows the mean square.
 // ---------------------------------------------------------------------------
 __global__ void k_stats(const double *__restrict__ t, const double *__restrict__ y,
                         const double *__restrict__ dy, Batch bt, double *partials,
-                        unsigned int *counter, Stats *st, int *status)
+                        unsigned int *counter, Stats *st, int *status, int center)
 {
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
@@ -165,7 +166,7 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
             st->W = W;
             st->WY = WY;
             st->WY2 = WY2;
-            st->ybar = WY / W;
+            st->ybar = center ? WY / W : 0.0;
             st->invW = 1.0 / W;
             const double m2 = WY2 / W;
             const double var = fmax(m2 - st->ybar * st->ybar, 1e-20 * m2);
@@ -450,6 +451,7 @@ struct PassAArgs {
     Geometry g;
     Batch bt;
     int shared;            // 1: series share t and dy, so s2 and s3 are transformed once
+    int nofit;             // 1: the model has no offset; s2 is not needed
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
     const Cplx<T> *twA;    // two-level root table, length N2
@@ -492,6 +494,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
         grid = blockIdx.y - 3 * ser;
         slot = blockIdx.y;
     }
+    if (A.nofit && grid == 1) return;    // whole block: before any barrier
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
     const int64_t pt_off = series_of(A.bt, ser).rec_off;
@@ -723,7 +726,25 @@ struct PassBArgs {
     double *power;
     double *sums;
     double lam_tol;        // eigenvalues of M at or below this count as zero
+    int nofit;             // 1: no offset in the model: C = S = 0, grid s2 absent
+    int norm;              // 0 standard, 1 model, 2 log, 3 psd
 };
+
+// Normalisation of the standard power P = p / YY (p the explained weighted
+// sum of squares with w^): model p / (YY - p) = P / (1 - P); log -ln(1 - P);
+// psd p W / 2 = P YY W / 2 with the unscaled YY and W = sum w.
+template <typename T>
+__device__ __forceinline__ double ls_normalise(double P, int norm, double psd_factor)
+{
+    switch (norm) {
+    case 1: return P * rcp_fp64(1.0 - P);
+    case 2:
+        if (sizeof(T) == 4) return -(double)logf((float)(1.0 - P));
+        return -log1p(-P);
+    case 3: return P * psd_factor;
+    default: return P;
+    }
+}
 
 template <typename T> struct PowerOut;
 
@@ -768,6 +789,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     {
         const int half = N1 >> 1;
         for (int gi = 0; gi < 3; ++gi) {
+            if (B.nofit && gi == 1) continue;
             const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
             const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
             V *dst = buf + (size_t)gi * Lp;
@@ -795,10 +817,16 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     }
     __syncthreads();
 
-    if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
-    else fft_dif<1>(buf, 3, Lp, g.fb, roots);
+    if (B.nofit) {                          // rows 0 and 2
+        if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
+        else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
+    } else {
+        if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
+        else fft_dif<1>(buf, 3, Lp, g.fb, roots);
+    }
 
     const double YY = stat->YY;
+    const double psd_factor = 0.5 * stat->W * YY / (stat->scale * stat->scale);
     ff YYf;
     YYf.hi = (float)YY;
     YYf.lo = (float)(YY - (double)YYf.hi);
@@ -814,9 +842,13 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         const int64_t kp = (c < c1) ? k : k - n;
         const int sp = pad16(pos);
         const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
-        const V g1 = buf[sp], g2 = buf[Lp + sp], g3 = buf[2 * Lp + sp];
+        const V g1 = buf[sp], g3 = buf[2 * Lp + sp];
+        const V g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
         const int64_t out = kp + K0;
-        if (power) power[out] = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, B.lam_tol);
+        if (power) {
+            const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, B.lam_tol);
+            power[out] = ls_normalise<T>(P, B.norm, psd_factor);
+        }
         if (sums) {
             // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
             const double us = 1.0 / stat->scale;
@@ -898,8 +930,10 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &bt, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev, int shared)
+                            cudaStream_t st, cudaEvent_t *ev, int shared, int mode)
 {
+    const int nofit = (mode & kModeNoFit) ? 1 : 0;
+    const int center = (!nofit || !(mode & kModeNoCenter)) ? 1 : 0;
     cudaError_t err;
     const int S = bt.S;
     PointSet<T> rx = carve<T>(ws.pts_raw[0], capacity), r2 = carve<T>(ws.pts_raw[1], capacity);
@@ -909,7 +943,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     err = cudaMemsetAsync(ws.hist, 0, sizeof(int) * 2 * (size_t)g.nbins * S, st);
     if (err != cudaSuccess) return err;
     k_stats<<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, ws.partials, ws.counter, ws.stats,
-                                           ws.status);
+                                           ws.status, center);
     k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, g, rx, r2, ws.hist, ws.partials,
                                                ws.counter, ws.stats, ws.status);
     if (ev) cudaEventRecord(ev[1], st);
@@ -923,6 +957,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.g = g;
     A.bt = bt;
     A.shared = shared;
+    A.nofit = nofit;
     A.px = sx;
     A.p2 = s2;
     A.binstart = ws.binstart;
@@ -952,6 +987,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.st = ws.stats;
     B.power = power;
     B.sums = sums;
+    B.nofit = nofit;
+    B.norm = mode & kModeNormMask;
     // The sums carry an absolute error of about eps (sum w^ = 1), plus FP32
     // rounding on the FP32 path: an eigenvalue of M within ten times that of
     // zero is indistinguishable from a rank-deficient M (the oracle's exact
@@ -985,11 +1022,11 @@ cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
 template cudaError_t launch_pipeline<float>(const Geometry &, const Workspace &, int64_t,
                                             const Batch &, int64_t, const double *,
                                             const double *, const double *, double *, double *,
-                                            int, cudaStream_t, cudaEvent_t *, int);
+                                            int, cudaStream_t, cudaEvent_t *, int, int);
 template cudaError_t launch_pipeline<double>(const Geometry &, const Workspace &, int64_t,
                                              const Batch &, int64_t, const double *,
                                              const double *, const double *, double *, double *,
-                                             int, cudaStream_t, cudaEvent_t *, int);
+                                             int, cudaStream_t, cudaEvent_t *, int, int);
 template cudaError_t launch_deconv_table<float>(const Geometry &, void *, int64_t, const double *,
                                                 const double *, int, cudaStream_t);
 template cudaError_t launch_deconv_table<double>(const Geometry &, void *, int64_t, const double *,

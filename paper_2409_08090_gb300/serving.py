@@ -47,6 +47,7 @@ class Request:
     nf: int
     precision: str = "fp32"
     eps: float = 1e-6
+    mode: int = 0           # normalisation and model flags (the C-ABI's norm word)
     id: int = field(default_factory=lambda: next(_ids))
     arrival: float = field(default_factory=time.perf_counter)
     future: cf.Future = field(default_factory=cf.Future)
@@ -62,7 +63,7 @@ class Request:
 
     @property
     def key(self):
-        return (self.precision, float(self.eps))
+        return (self.precision, float(self.eps), int(self.mode))
 
 
 class Scheduler:
@@ -72,7 +73,7 @@ class Scheduler:
       does not fit the free budget, admission waits for memory to be released
       (no overtaking, so large requests are not starved).
     * A request larger than the whole budget is rejected with MemoryError.
-    * Admitted requests with the same (precision, eps) form a batch of at most
+    * Admitted requests with the same (precision, eps, model) form a batch of at most
       `max_batch` series; `next_batch` returns the largest group first.
     * Cancelled requests (future.cancel() before admission) are dropped.
     """
@@ -192,13 +193,20 @@ class PeriodogramServer:
 
     # ---- client side -------------------------------------------------------
     def submit(self, t, y, dy, f0: float, df: float, nf: int, precision: str = "fp32",
-               eps: float | None = None) -> cf.Future:
+               eps: float | None = None, normalization: str = "standard",
+               fit_mean: bool = True, center_data: bool = True) -> cf.Future:
+        try:
+            mode = self._nl.mode_word(normalization, fit_mean, center_data)
+        except ValueError as exc:
+            fut = cf.Future()
+            fut.set_exception(exc)
+            return fut
         t = np.ascontiguousarray(t, dtype=np.float64)
         y = np.ascontiguousarray(y, dtype=np.float64)
         dy = None if dy is None else np.ascontiguousarray(np.broadcast_to(dy, t.shape),
                                                           dtype=np.float64)
         eps = (1e-6 if precision == "fp32" else 1e-9) if eps is None else float(eps)
-        req = Request(t, y, dy, float(f0), float(df), int(nf), precision, eps)
+        req = Request(t, y, dy, float(f0), float(df), int(nf), precision, eps, mode)
         bad = (t.ndim != 1 or t.shape != y.shape or t.shape[0] < 2 or req.nf < 1
                or not (req.df > 0) or not np.all(np.isfinite(t)) or not np.all(np.isfinite(y))
                or (dy is not None and not np.all(dy > 0)))
@@ -238,10 +246,11 @@ class PeriodogramServer:
 
     # ---- GPU loop ----------------------------------------------------------
     def _plan(self, slot: _Slot, key):
-        p = slot.plans.get(key)
+        pk = key[:2]            # (precision, eps): the model word is per call
+        p = slot.plans.get(pk)
         if p is None:
             p = self._nl.Plan(2, 1, key[1], key[0], device=self.device)
-            slot.plans[key] = p
+            slot.plans[pk] = p
         return p
 
     def _launch(self, slot: _Slot, batch: list[Request]):
@@ -261,9 +270,13 @@ class PeriodogramServer:
         with torch.cuda.stream(slot.stream):
             dev = host.to(self.device, non_blocking=True)
             out = torch.empty(int(nfs.sum()), dtype=torch.float64, device=self.device)
-            _, out_off = plan.execute_batch(dev[:n], dev[n:2 * n], dev[2 * n:], offsets,
-                                            [r.f0 for r in batch], [r.df for r in batch], nfs,
-                                            out=out, sync=False)
+            word = batch[0].mode
+            _, out_off = plan.execute_batch(
+                dev[:n], dev[n:2 * n], dev[2 * n:], offsets, [r.f0 for r in batch],
+                [r.df for r in batch], nfs, out=out, sync=False,
+                normalization=nl.NORMALIZATIONS[word & 0xFF],
+                fit_mean=not (word & nl.LS_NO_FIT_MEAN),
+                center_data=not (word & nl.LS_NO_CENTER))
             if self.results == "host":
                 out_host = slot.pinned("pin_out", out.numel())
                 out_host.copy_(out, non_blocking=True)

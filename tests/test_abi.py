@@ -38,6 +38,23 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_model_words_match_the_header():
+    import paper_2409_08090_gb300 as nl
+    src = open(HEADER).read()
+    for name in ("LS_NORM_STANDARD", "LS_NORM_MODEL", "LS_NORM_LOG", "LS_NORM_PSD"):
+        m = re.search(name + r"\s*=\s*(\d+)", src)
+        assert m and int(m.group(1)) == getattr(nl, name), name
+    for name in ("LS_NO_FIT_MEAN", "LS_NO_CENTER"):
+        m = re.search(r"#define\s+" + name + r"\s+(0x[0-9a-fA-F]+)", src)
+        assert m and int(m.group(1), 16) == getattr(nl, name), name
+    assert nl.mode_word() == 0
+    assert nl.mode_word("psd", fit_mean=False, center_data=False) == 3 | 0x100 | 0x200
+    # centring is implied by a fitted mean
+    assert nl.mode_word("log", fit_mean=True, center_data=False) == 2
+    with pytest.raises(ValueError):
+        nl.mode_word("power")
+
+
 def test_status_strings():
     import paper_2409_08090_gb300 as nl
     assert nl.ls_status_str(0) == "ok"

@@ -83,6 +83,29 @@ def test_device_results_equal_host_results(nl):
         assert np.max(np.abs(a - b.cpu().numpy())) <= 1e-6
 
 
+def test_model_variants_in_the_mix(nl):
+    import torch
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    reqs = [W.ragged_series(3000 + i, nd_lo=100, nd_hi=2000) for i in range(6)]
+    variants = [dict(normalization="psd", fit_mean=False, center_data=False),
+                dict(normalization="model"), dict()]
+    srv = PeriodogramServer(memory_budget=256 << 20, streams=2, max_batch=4)
+    futs = [(s, v, srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, "fp64", 1e-9, **v))
+            for s in reqs for v in variants]
+    bad = srv.submit(reqs[0].t, reqs[0].y, None, 0.1, 0.1, 10, normalization="power")
+    got = [(s, v, f.result(timeout=120)) for s, v, f in futs]
+    srv.close()
+    with pytest.raises(ValueError):
+        bad.result(timeout=1)
+    dev = torch.device("cuda:0")
+    for s, v, P in got:
+        plan = nl.Plan(s.nd, s.nf, 1e-9, "fp64")
+        A = plan.execute(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
+                         torch.tensor(s.dy, device=dev), s.f0, s.df, **v).cpu().numpy()
+        plan.close()
+        assert np.max(np.abs(P - A)) <= 1e-12 * max(1.0, float(np.max(np.abs(A))))
+
+
 def test_invalid_and_oversized_requests_fail_their_futures_only(nl):
     from paper_2409_08090_gb300.serving import PeriodogramServer
     srv = PeriodogramServer(memory_budget=8 << 20, streams=1)

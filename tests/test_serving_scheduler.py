@@ -60,11 +60,11 @@ def test_batches_group_by_precision_and_tolerance():
     for r in rs:
         s.submit(r)
     b1 = s.next_batch()
-    assert len(b1) == 3 and all(r.key == ("fp32", 1e-6) for r in b1)
+    assert len(b1) == 3 and all(r.key == ("fp32", 1e-6, 0) for r in b1)
     b2 = s.next_batch()
     assert len(b2) == 2 and all(r.key == b2[0].key for r in b2)
     b3 = s.next_batch()
-    assert len(b3) == 2 and {r.key for r in b2 + b3} == {("fp32", 1e-6), ("fp64", 1e-9)}
+    assert len(b3) == 2 and {r.key for r in b2 + b3} == {("fp32", 1e-6, 0), ("fp64", 1e-9, 0)}
     assert s.next_batch() == []
 
 
@@ -96,3 +96,13 @@ def test_concurrent_submitters_and_release_balance():
 def test_request_bytes_scale():
     assert request_bytes(1000, 12000, "fp64") > request_bytes(1000, 12000, "fp32")
     assert request_bytes(10, 100, "fp32") > 0
+
+
+def test_model_variants_are_batched_apart():
+    s = Scheduler(1 << 30)
+    a, b = _req(), _req()
+    b.mode = 0x103                      # psd, no fitted mean
+    s.submit(a)
+    s.submit(b)
+    first, second = s.next_batch(), s.next_batch()
+    assert len(first) == 1 and len(second) == 1 and first[0].key != second[0].key
