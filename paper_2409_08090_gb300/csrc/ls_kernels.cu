@@ -20,6 +20,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "ls_fft.cuh"
 #include "ls_internal.cuh"
 
@@ -926,6 +930,32 @@ void decompose_double(double x, uint64_t &m, int &e, int &neg)
     e = (ex ? ex : 1) - 1075;
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per (kernel, device) for the whole process.  The limit only permits:
+// occupancy follows the size each launch asks for, so one setting serves every
+// plan, and no thread can lower it under another's launch.
+static cudaError_t allow_max_dynamic_smem(const void *fn)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+        if (d.first == fn && d.second == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    done.emplace_back(fn, dev);
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &bt, int64_t max_nd, const double *t, const double *y,
@@ -965,15 +995,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
-    static thread_local int smA_set[64];   // attribute already raised to this size, per device
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64 || smA_set[dev] < (int)smA) {
-        err = cudaFuncSetAttribute(k_passA<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smA);
-        if (err != cudaSuccess) return err;
-        if (dev >= 0 && dev < 64) smA_set[dev] = (int)smA;
-    }
+    if ((err = allow_max_dynamic_smem((const void *)k_passA<T>)) != cudaSuccess) return err;
     k_passA<T><<<dim3(g.nbins, shared ? S + 2 : 3 * S), kThreadsA, smA, st>>>(A);
 
     if (ev) cudaEventRecord(ev[3], st);
@@ -995,13 +1017,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // arithmetic uses 1e-15).
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
-    static thread_local int smB_set[64];
-    if (dev < 0 || dev >= 64 || smB_set[dev] < (int)smB) {
-        err = cudaFuncSetAttribute(k_passB<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smB);
-        if (err != cudaSuccess) return err;
-        if (dev >= 0 && dev < 64) smB_set[dev] = (int)smB;
-    }
+    if ((err = allow_max_dynamic_smem((const void *)k_passB<T>)) != cudaSuccess) return err;
     k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();

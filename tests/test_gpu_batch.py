@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2409_08090_gb300 import workloads as W
+from tests.rerun_tolerance import assert_rerun_close
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +80,7 @@ def test_ragged_batch_matches_oracle_and_single(nl, oracle_mod, prec, eps):
             if s.nd >= 500:
                 assert np.linalg.norm(P - P_o) / np.linalg.norm(P_o) <= 1e-5
         P_1 = _run_single(nl, s, eps, prec)
-        tol = 1e-12 if prec == "fp64" else 1e-6
-        assert np.max(np.abs(P - P_1)) <= tol
+        assert_rerun_close(P, P_1, prec)
 
 
 def test_small_budget_splits_launches_without_changing_results(nl):
@@ -152,8 +152,7 @@ def test_shared_times_batch_matches_replicated_batch(nl, oracle_mod, prec, eps):
     series = [W.Series(t, Y[i], dy, f0, df, nf) for i in range(Y.shape[0])]
     Prep = _run_batch(nl, series, eps, prec)
     for i in range(Y.shape[0]):
-        tol = 1e-12 if prec == "fp64" else 1e-6
-        assert np.max(np.abs(Pshared[i] - Prep[i])) <= tol
+        assert_rerun_close(Pshared[i], Prep[i], prec)
     for i in (0, 39):
         P_o = oracle_mod.periodogram(t, Y[i], dy, f0, df, np.arange(nf))
         if prec == "fp64":

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2409_08090_gb300 import workloads as W
+from tests.rerun_tolerance import assert_rerun_close
 
 pytestmark = pytest.mark.gpu
 
@@ -63,9 +64,8 @@ def test_results_in_the_mix_equal_results_alone(nl):
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
     for (s, prec, eps), P in zip(reqs, got):
         A = _alone(nl, s, prec, eps)
-        tol = 1e-12 if prec == "fp64" else 1e-6
         assert P.shape == (s.nf,)
-        assert np.max(np.abs(P - A)) <= tol
+        assert_rerun_close(P, A, prec)
 
 
 def test_device_results_equal_host_results(nl):
@@ -80,7 +80,7 @@ def test_device_results_equal_host_results(nl):
         srv.close()
     for s, a, b in zip(reqs, out["host"], out["device"]):
         assert isinstance(b, torch.Tensor) and b.is_cuda and b.shape == (s.nf,)
-        assert np.max(np.abs(a - b.cpu().numpy())) <= 1e-6
+        assert_rerun_close(b.cpu().numpy(), a, "fp32")
 
 
 def test_model_variants_in_the_mix(nl):

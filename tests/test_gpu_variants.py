@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2409_08090_gb300 import workloads as W
+from tests.rerun_tolerance import assert_rerun_close
 
 pytestmark = pytest.mark.gpu
 
@@ -103,7 +104,6 @@ def test_batch_variants_match_single_series(nl, prec, eps):
     y = _dev(np.concatenate([s.y + 0.5 for s in series]))
     dy = _dev(np.concatenate([np.ones(s.nd) if s.dy is None else s.dy for s in series]))
     bplan = nl.Plan(2, 1, eps, prec)
-    tol = 1e-12 if prec == "fp64" else 1e-6
     for (fit_mean, center), norm in itertools.product(MODELS, ("standard", "psd")):
         model = dict(normalization=norm, fit_mean=fit_mean, center_data=center)
         P, off = bplan.execute_batch(t, y, dy, offsets, [s.f0 for s in series],
@@ -115,7 +115,7 @@ def test_batch_variants_match_single_series(nl, prec, eps):
                               dy[a:a + s.nd].contiguous(), s.f0, s.df, **model).cpu().numpy()
             plan.close()
             scale = max(1.0, float(np.max(np.abs(P1))))
-            assert np.max(np.abs(P[o:o + s.nf] - P1)) <= tol * scale, (fit_mean, center, norm)
+            assert_rerun_close(P[o:o + s.nf], P1, prec, scale, (fit_mean, center, norm))
     bplan.close()
     torch.cuda.synchronize()
 
