@@ -82,6 +82,24 @@ constexpr int kEvPerSet = LS_NUM_STAGES + 1;
 constexpr int kN1MaxF32 = 4096, kN2MaxF32 = 25600;
 constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
+constexpr size_t kSmemOptin = 232448;             // opt-in shared memory per block (227 KB)
+
+bool build_fft(int L, FftPlan *fp);
+
+// Shared memory of a one-column pass-A block (the smallest block a split can
+// use: padded column, per-column and root tables, slot table) plus 2 KB of
+// margin: a column length above the opt-in limit cannot launch.
+bool passA_column_fits(int64_t N2, int prec)
+{
+    FftPlan fp;
+    if (N2 > (1 << 20) || !build_fft((int)N2, &fp)) return false;
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    const size_t nhi = (size_t)(N2 + 63) / 64;
+    const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
+    const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
+                         sizeof(int) * (size_t)(N2 / fp.Rlast) + 2048;
+    return bytes <= kSmemOptin;
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -174,7 +192,7 @@ ls_status choose_grid(int64_t nf, double sigma, int w, int prec, int64_t *n_out,
                 const int64_t N1 = (int64_t)1 << k1;
                 if (n % N1) break;
                 const int64_t N2 = n / N1;
-                if (N2 > n2max || N2 < 2 || (N2 & 1)) continue;
+                if (N2 > n2max || N2 < 2 || (N2 & 1) || !passA_column_fits(N2, prec)) continue;
                 const double b = fabs(log((double)N1) - log((double)N2));
                 if (b < bal) { bal = b; pick = (int)N1; }
             }

@@ -540,30 +540,48 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     const T halfw = T(0.5) * T(g.w);
     const T zscale = T(2) / T(g.w);
     const T beta = T(g.beta);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
-        const uint32_t ab = P.ab[j];
-        const int aj = (int)(ab & 0xFFFFu);
-        const int bj = (int)(ab >> 16);
-        // footprint columns aj .. aj+w-1 (mod N1) against block a0 .. a0+BA-1
-        int o = aj - a0;
-        if (o < 0) o += N1;
-        int i0, cs;
-        if (o < BA) { i0 = 0; cs = o; }
-        else { i0 = N1 - o; cs = 0; }
-        const int cnt = min(BA - cs, g.w - i0);
-        if (cnt <= 0) continue;
-        const T roff = P.roff[j];
-        const V s = str[j];
-        for (int u = 0; u < cnt; ++u) {
-            const int i = i0 + u;
-            int b = bj + ((aj + i >= N1) ? 1 : 0);
-            if (b >= N2) b -= N2;
-            const T z = (roff - halfw + T(i)) * zscale;
-            const T v = es_kernel(z, beta);
-            V *dst = buf + (size_t)(cs + u) * Lp + pad16(b);
-            atomicAdd(&dst->x, s.x * v);
-            atomicAdd(&dst->y, s.y * v);
+    // kPre records per thread are loaded before any is used, so their global
+    // loads overlap instead of forming one dependent chain per record.
+    constexpr int kPre = 4;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kPre * blockDim.x) {
+        uint32_t abv[kPre];
+        T rv[kPre];
+        V sv[kPre];
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+            const int e = e0 + q * (int)blockDim.x;
+            if (e < total) {
+                const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
+                abv[q] = __ldg(P.ab + j);
+                rv[q] = __ldg(P.roff + j);
+                sv[q] = __ldg(str + j);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+            if (e0 + q * (int)blockDim.x >= total) break;
+            const uint32_t ab = abv[q];
+            const int aj = (int)(ab & 0xFFFFu);
+            const int bj = (int)(ab >> 16);
+            // footprint columns aj .. aj+w-1 (mod N1) against block a0 .. a0+BA-1
+            int o = aj - a0;
+            if (o < 0) o += N1;
+            int i0, cs;
+            if (o < BA) { i0 = 0; cs = o; }
+            else { i0 = N1 - o; cs = 0; }
+            const int cnt = min(BA - cs, g.w - i0);
+            const T roff = rv[q];
+            const V s = sv[q];
+            for (int u = 0; u < cnt; ++u) {
+                const int i = i0 + u;
+                int b = bj + ((aj + i >= N1) ? 1 : 0);
+                if (b >= N2) b -= N2;
+                const T z = (roff - halfw + T(i)) * zscale;
+                const T v = es_kernel(z, beta);
+                V *dst = buf + (size_t)(cs + u) * Lp + pad16(b);
+                atomicAdd(&dst->x, s.x * v);
+                atomicAdd(&dst->y, s.y * v);
+            }
         }
     }
     __syncthreads();
@@ -574,6 +592,27 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     V *H = A.H + (size_t)slot * (size_t)g.n + a0;
+    if constexpr (sizeof(T) == 4) {
+        if ((BA & 1) == 0) {
+            // Column pairs as one 16-byte store: a0, N1 and n are even, so every
+            // pair starts on a 16-byte boundary.  A row of H receives only BA
+            // columns from this block, so wider stores are not available here.
+#pragma unroll 2
+            for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
+                const int d = slot_freq_tab(pos, dtab, g.fa);
+                const int sp = pad16(pos);
+                float4 *dst = reinterpret_cast<float4 *>(H + (size_t)d * N1);
+                for (int c0 = 0; c0 < BA; c0 += 2) {
+                    const V t0 = cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]);
+                    const V t1 = cmul(alo[(c0 + 1) * 64 + (d & 63)], ahi[(c0 + 1) * nhi + (d >> 6)]);
+                    const V v0 = cmul(buf[(size_t)c0 * Lp + sp], t0);
+                    const V v1 = cmul(buf[(size_t)(c0 + 1) * Lp + sp], t1);
+                    dst[c0 >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
+                }
+            }
+            return;
+        }
+    }
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
         const int d = slot_freq_tab(pos, dtab, g.fa);
         const int sp = pad16(pos);
