@@ -397,6 +397,11 @@ ls_status upload_tables(ls_plan_s *p)
     e = launch_deconv_table<T>(g, p->ws.deconv, p->deconv_count, dz, dw, (int)z.size(), 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(dq);
+    if (e != cudaSuccess) return cuda_status(e);
+    // the same table in pass-B order (coalesced reads in pass B)
+    if ((s = plan_alloc(p, &p->ws.deconv_slot, (size_t)g.n * sizeof(T))) != LS_OK) return s;
+    e = launch_deconv_slot<T>(g, p->ws.deconv_slot, p->ws.deconv, p->deconv_count, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return cuda_status(e);
 }
 
@@ -777,6 +782,7 @@ ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDes
     ws.twB = sub->ws.twB;
     ws.tw4 = sub->ws.tw4;
     ws.deconv = sub->ws.deconv;
+    ws.deconv_slot = sub->ws.deconv_slot;
     Batch bt;
     bt.S = S;
     bt.many = b.desc;

@@ -100,6 +100,7 @@ struct Workspace {
     void *twB;            // two-level root table for length N1
     void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
+    void *deconv_slot;    // the same in pass-B order: [d * N1 + slot], n entries
 };
 
 // Frequencies of one series, decomposed for the exact phase reduction:
@@ -148,6 +149,13 @@ template <typename T>
 cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
                                 const double *gl_z, const double *gl_wpsi, int q,
                                 cudaStream_t st);
+
+// Reorder the deconvolution table into pass-B order: entry d * N1 + pos holds
+// 1/phi_hat of the mode min(k, n - k), k = d + N2 * (frequency of slot pos),
+// or 0 past the table's `count` entries (modes no grid of the plan needs).
+template <typename T>
+cudaError_t launch_deconv_slot(const Geometry &g, void *out, const void *compact, int64_t count,
+                               cudaStream_t st);
 
 template <typename T>
 size_t point_record_bytes();

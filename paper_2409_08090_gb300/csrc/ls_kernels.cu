@@ -842,7 +842,7 @@ struct PassBArgs {
     int shared;            // see PassAArgs
     const Cplx<T> *twB;    // two-level root table, length N1
     const Cplx<T> *H;
-    const T *deconv;       // 1/phi_hat(|k'|)
+    const T *deconv;       // 1/phi_hat(|k'|) in pass-B order, [d * N1 + slot]
     const Stats *st;
     double *power;
     double *sums;
@@ -865,6 +865,31 @@ __device__ __forceinline__ double ls_normalise(double P, int norm, double psd_fa
     case 3: return P * psd_factor;
     default: return P;
     }
+}
+
+// Asynchronous global -> shared copies of one complex element (sm_80+):
+// 8 bytes (FP32 complex) through L1, 16 bytes (FP64 complex) bypassing it.
+__device__ __forceinline__ void cp_async_elem(float2 *dst, const float2 *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s),
+                 "l"((unsigned long long)__cvta_generic_to_global(src)) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2 *dst, const double2 *src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s),
+                 "l"((unsigned long long)__cvta_generic_to_global(src)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// Wait until every committed copy of this thread has landed (a hardware wait on
+// the thread's own copies; the block barrier that follows publishes them).
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename T> struct PowerOut;
@@ -902,40 +927,23 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     const Stats *stat = B.st + ser;
     double *power = B.power ? B.power + sd.out_off : nullptr;
     double *sums = B.sums ? B.sums + 6 * sd.out_off : nullptr;
+    // rows of H straight into shared memory with asynchronous copies: every
+    // element of the three rows is in flight at once, without registers.
+    for (int gi = 0; gi < 3; ++gi) {
+        if (B.nofit && gi == 1) continue;
+        const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
+        const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
+        V *dst = buf + (size_t)gi * Lp;
+        for (int i = threadIdx.x; i < N1; i += blockDim.x) cp_async_elem(dst + pad16(i), src + i);
+    }
+    cp_async_commit();
+    // per-series scalars, loaded while the copies run
+    const double YY = stat->YY;
+    const double psd_factor = 0.5 * stat->W * YY / (stat->scale * stat->scale);
+    const double unscale = 1.0 / stat->scale;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
-
-    // rows of H: N1 is a power of two >= 32, so pairs (2i, 2i+1) stay adjacent
-    // after padding; four 16-byte loads in flight per thread.
-    {
-        const int half = N1 >> 1;
-        for (int gi = 0; gi < 3; ++gi) {
-            if (B.nofit && gi == 1) continue;
-            const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
-            const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
-            V *dst = buf + (size_t)gi * Lp;
-            for (int i0 = threadIdx.x; i0 < half; i0 += 4 * blockDim.x) {
-                V v[8];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i < half) {
-                        v[2 * u] = src[2 * i];
-                        v[2 * u + 1] = src[2 * i + 1];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = i0 + u * blockDim.x;
-                    if (i < half) {
-                        const int sp = pad16(2 * i);
-                        dst[sp] = v[2 * u];
-                        dst[sp + 1] = v[2 * u + 1];
-                    }
-                }
-            }
-        }
-    }
+    cp_async_wait_all();
     __syncthreads();
 
     if (B.nofit) {                          // rows 0 and 2
@@ -946,8 +954,6 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         else fft_dif<1>(buf, 3, Lp, g.fb, roots);
     }
 
-    const double YY = stat->YY;
-    const double psd_factor = 0.5 * stat->W * YY / (stat->scale * stat->scale);
     ff YYf;
     YYf.hi = (float)YY;
     YYf.lo = (float)(YY - (double)YYf.hi);
@@ -956,27 +962,41 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     const int64_t lo_end = nf - K0;        // k <  lo_end   -> k' = k >= 0
     const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
     const int c2 = (int)((hi_start - d + N2 - 1) / N2);
-    for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
-        const int c = slot_freq_tab(pos, dtab, g.fb);
-        if (c >= c1 && c < c2) continue;            // mode not requested
-        const int64_t k = d + (int64_t)N2 * c;
-        const int64_t kp = (c < c1) ? k : k - n;
-        const int sp = pad16(pos);
-        const T dc = __ldg(B.deconv + (kp < 0 ? -kp : kp));
-        const V g1 = buf[sp], g3 = buf[2 * Lp + sp];
-        const V g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
-        const int64_t out = kp + K0;
-        if (power) {
-            const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, B.lam_tol);
-            power[out] = ls_normalise<T>(P, B.norm, psd_factor);
+    // kDc deconvolution factors per thread are loaded (coalesced, pass-B order)
+    // before any is used, so their latency is paid once per group.
+    constexpr int kDc = 4;
+    const T *dcrow = B.deconv + (size_t)d * N1;
+    for (int p0 = threadIdx.x; p0 < N1; p0 += kDc * blockDim.x) {
+        T dcv[kDc];
+#pragma unroll
+        for (int r = 0; r < kDc; ++r) {
+            const int pos = p0 + r * (int)blockDim.x;
+            dcv[r] = pos < N1 ? __ldg(dcrow + pos) : T(0);
         }
-        if (sums) {
-            // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
-            const double us = 1.0 / stat->scale;
-            double *o = sums + 6 * out;
-            o[0] = (double)(g1.x * dc) * us; o[1] = (double)(g1.y * dc) * us;
-            o[2] = (double)(g2.x * dc); o[3] = (double)(g2.y * dc);
-            o[4] = (double)(g3.x * dc); o[5] = (double)(g3.y * dc);
+#pragma unroll
+        for (int r = 0; r < kDc; ++r) {
+            const int pos = p0 + r * (int)blockDim.x;
+            if (pos >= N1) break;
+            const int c = slot_freq_tab(pos, dtab, g.fb);
+            if (c >= c1 && c < c2) continue;            // mode not requested
+            const int64_t k = d + (int64_t)N2 * c;
+            const int64_t kp = (c < c1) ? k : k - n;
+            const int sp = pad16(pos);
+            const T dc = dcv[r];
+            const V g1 = buf[sp], g3 = buf[2 * Lp + sp];
+            const V g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
+            const int64_t out = kp + K0;
+            if (power) {
+                const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, B.lam_tol);
+                power[out] = ls_normalise<T>(P, B.norm, psd_factor);
+            }
+            if (sums) {
+                // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
+                double *o = sums + 6 * out;
+                o[0] = (double)(g1.x * dc) * unscale; o[1] = (double)(g1.y * dc) * unscale;
+                o[2] = (double)(g2.x * dc); o[3] = (double)(g2.y * dc);
+                o[4] = (double)(g3.x * dc); o[5] = (double)(g3.y * dc);
+            }
         }
     }
 }
@@ -995,6 +1015,20 @@ __global__ void k_deconv(T *out, int64_t count, double w_over_n, double w, const
         const double kk = (double)k * w_over_n;
         for (int i = 0; i < q; ++i) s += wpsi[i] * cospi(kk * z[i]);
         out[k] = (T)(1.0 / (w * s));
+    }
+}
+
+template <typename T>
+__global__ void k_deconv_slot(T *out, const T *__restrict__ compact, int64_t count, Geometry g)
+{
+    const int logN1 = 31 - __clz(g.N1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = i >> logN1;
+        const int pos = (int)(i & (g.N1 - 1));
+        const int64_t k = d + (int64_t)g.N2 * slot_to_freq(pos, g.fb);
+        const int64_t m = k < g.n - k ? k : g.n - k;
+        out[i] = m < count ? compact[m] : T(0);
     }
 }
 
@@ -1146,7 +1180,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.shared = shared;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
     B.H = static_cast<const Cplx<T> *>(ws.H);
-    B.deconv = static_cast<const T *>(ws.deconv);
+    B.deconv = static_cast<const T *>(ws.deconv_slot);
     B.st = ws.stats;
     B.power = power;
     B.sums = sums;
@@ -1184,6 +1218,21 @@ template cudaError_t launch_pipeline<double>(const Geometry &, const Workspace &
                                              const Batch &, int64_t, const double *,
                                              const double *, const double *, double *, double *,
                                              int, cudaStream_t, cudaEvent_t *, int, int);
+template <typename T>
+cudaError_t launch_deconv_slot(const Geometry &g, void *out, const void *compact, int64_t count,
+                               cudaStream_t st)
+{
+    int64_t nb = (g.n + 255) / 256;
+    if (nb > 8192) nb = 8192;
+    k_deconv_slot<T><<<(int)nb, 256, 0, st>>>(static_cast<T *>(out),
+                                               static_cast<const T *>(compact), count, g);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_deconv_slot<float>(const Geometry &, void *, const void *, int64_t,
+                                               cudaStream_t);
+template cudaError_t launch_deconv_slot<double>(const Geometry &, void *, const void *, int64_t,
+                                                cudaStream_t);
 template cudaError_t launch_deconv_table<float>(const Geometry &, void *, int64_t, const double *,
                                                 const double *, int, cudaStream_t);
 template cudaError_t launch_deconv_table<double>(const Geometry &, void *, int64_t, const double *,

@@ -183,6 +183,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     const size_t o_tw4 = c.take(sizeof(V) * ((1u << kTw4Bits) + ((size_t)n >> kTw4Bits) + 1));
     const int64_t ndeconv = nf / 2 + 1;
     const size_t o_deconv = c.take(sizeof(T) * (size_t)ndeconv);
+    const size_t o_deconv_slot = c.take(sizeof(T) * (size_t)n);
     const size_t o_quad = c.take(sizeof(double) * 2 * kMaxQuad);
     if (c.off > kNoallocScratchBytes) return LS_ERR_UNSUPPORTED;
 
@@ -203,6 +204,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     ws.twB = base + o_twB;
     ws.tw4 = base + o_tw4;
     ws.deconv = base + o_deconv;
+    ws.deconv_slot = base + o_deconv_slot;
 
     // The last-block counters and the status word must start at zero.
     cudaError_t e = cudaMemsetAsync(base + o_counter, 0, 256, st);
@@ -218,6 +220,8 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     e = cudaMemcpyAsync(dquad, quad, sizeof(quad), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return LS_ERR_CUDA;
     e = launch_deconv_table<T>(g, ws.deconv, ndeconv, dquad, dquad + kMaxQuad, q, st);
+    if (e != cudaSuccess) return LS_ERR_CUDA;
+    e = launch_deconv_slot<T>(g, ws.deconv_slot, ws.deconv, ndeconv, st);
     if (e != cudaSuccess) return LS_ERR_CUDA;
 
     Batch bt;
