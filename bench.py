@@ -384,6 +384,29 @@ def run_ours(args):
         e2e = {"value": world * nsteps / dt, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * s.nd, "d2h_bytes_per_step": 8 * s.nf,
                "steps": nsteps, "host_buffers": "pinned"}
+
+    # -- small problems: launch-bound, so compare direct calls with a CUDA-graph
+    # replay of the same pipeline (back to back on resident buffers, no flush)
+    graph = None
+    if s.nf <= 1_000_000:
+        calls = 200
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            plan.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
+        torch.cuda.synchronize()
+        direct = calls / (time.perf_counter() - t0)
+        g = plan.graph(t, y, dy, s.f0, s.df, out=out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            g.replay()
+        torch.cuda.synchronize()
+        replay = calls / (time.perf_counter() - t0)
+        g.sync()
+        graph = {"direct": direct, "graph": replay, "unit": UNIT, "calls": calls,
+                 "note": "back to back on resident buffers, no L2 flush (launch-bound regime)"}
+        del g
     plan.close()
 
     # -- the plain single-series FP64 path on the same series (context)
@@ -448,6 +471,7 @@ def run_ours(args):
                        "frac_of_peak": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9 / peak},
         "stage_ms": avg, "stage_gbs": kern_gbs,
         "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
+        "graph_replay": graph,
         "gpu_launches": 6 * args.steps,
         "clocks": clk, "wall_s": wall,
     }

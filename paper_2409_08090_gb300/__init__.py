@@ -16,7 +16,7 @@ import threading
 
 from . import build as _build
 
-__all__ = ["LSError", "Plan", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
+__all__ = ["LSError", "Plan", "GraphedExecute", "lombscargle", "load_library", "LS_FP64", "LS_FP32",
            "LS_NORM_STANDARD", "LS_NORM_MODEL", "LS_NORM_LOG", "LS_NORM_PSD",
            "LS_NO_FIT_MEAN", "LS_NO_CENTER", "NORMALIZATIONS", "mode_word", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
            "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_execute_batch_shared", "ls_plan_describe", "ls_status_str",
@@ -267,9 +267,13 @@ class Plan:
     ``center_data`` (see ``mode_word``)."""
 
     def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
-                 device: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0):
+                 device: int = 0, upsampling: float | str = 0.0, batch_workspace_bytes: int = 0):
         self.prec = _prec_code(precision)
         self.device = int(device)
+        if upsampling == "tuned":        # measured per shape, cached (autotune.py)
+            from . import autotune
+            upsampling = autotune.tuned_upsampling(
+                nf, eps, "fp32" if self.prec == LS_FP32 else "fp64", max_nd, self.device)
         self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling,
                               batch_workspace_bytes)
         self.info = ls_plan_describe(self.handle)
@@ -314,6 +318,13 @@ class Plan:
         if sync:
             _check(ls_sync(self.handle), "ls_execute (device status)")
         return out
+
+    def graph(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None, out=None,
+              **model) -> "GraphedExecute":
+        """Record this execute (device buffers t, y, dy, out fixed) as a CUDA graph;
+        ``.replay()`` then re-runs it on whatever the buffers hold, with one
+        launch instead of one per kernel.  See ``GraphedExecute``."""
+        return GraphedExecute(self, t, y, dy, f0, df, nf, eps, out, model)
 
     def execute_batch(self, t, y, dy, offsets, f0, df, nf, eps=None, out=None,
                       sync: bool = True, **model):
@@ -383,6 +394,49 @@ class Plan:
                         eps, mode_word(**model), out.ctypes.data)
         _check(st, "ls_execute")
         return out
+
+
+class GraphedExecute:
+    """One ``ls_execute`` recorded by CUDA stream capture (torch.cuda.CUDAGraph).
+
+    With device buffers, ls_execute enqueues only kernels and a memset on the
+    plan's stream, so it can be captured; a replay re-runs the whole pipeline
+    on the current contents of ``t, y, dy`` (same N_d, grid and model) and
+    writes ``out``.  Device-side errors accumulate in the plan's status word:
+    ``sync()`` waits and raises them.  The plan must outlive the graph and must
+    not run other work concurrently with a replay (they share its workspace).
+    """
+
+    def __init__(self, plan: "Plan", t, y, dy, f0, df, nf, eps, out, model):
+        import torch
+        self.plan = plan
+        nf = int(plan.info.nf if nf is None else nf)
+        self.out = out if out is not None else torch.empty(nf, dtype=torch.float64,
+                                                            device=t.device)
+        self._args = (t, y, dy, f0, df, nf, eps)
+        dev = plan.device
+        # warm-up outside the capture (first-use set-up of the kernels), then record
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            plan.execute(t, y, dy, f0, df, nf, eps, out=self.out, sync=False, **model)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        _check(ls_sync(plan.handle), "graph warm-up (device status)")
+        self.graph = torch.cuda.CUDAGraph()
+        # "relaxed": the library queries pointer attributes while recording
+        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
+            plan.execute(t, y, dy, f0, df, nf, eps, out=self.out, sync=False, **model)
+        torch.cuda.synchronize(dev)
+
+    def replay(self):
+        """Enqueue the recorded pipeline on the current stream's device."""
+        self.graph.replay()
+        return self.out
+
+    def sync(self):
+        _check(ls_sync(self.plan.handle), "graph replay (device status)")
+        return self.out
 
 
 _plan_cache: dict = {}
