@@ -187,7 +187,9 @@ def algorithmic_bytes(info, nd: int, nf: int, precision: str) -> dict:
     pts = 3 * nd * (4 + rs + cx)          # cell, offset, strength per transform
     return {
         "pass_a_spread_fft": 3 * n * cx + pts,          # H written once
-        "pass_b_fft_deconv_power": 3 * n * cx + 8 * nf + rs * (nf // 2 + 1),
+        # H read once, P written, the deconvolution factor of each needed mode
+        # (pass-B order table: one entry per output frequency)
+        "pass_b_fft_deconv_power": 3 * n * cx + 8 * nf + rs * nf,
         "preprocess": 24 * nd + 3 * nd * (4 + rs + cx) + nd * (4 + rs + cx),
         "bin_sort": 2 * (3 * nd * (4 + rs + cx)) // 1,
     }
