@@ -165,15 +165,16 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, precision: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (same digest); else None."""
+def recorded_traffic(kernel: str, precision: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary of this kernel on this
+    workload, if it was taken on the current kernel sources (same digest);
+    else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
     except (OSError, ValueError):
         return None
-    ent = d.get(f"{kernel}:{precision}")
+    ent = d.get(f"{kernel}:{precision}:{workload}")
     if not ent or ent.get("source_digest") != source_digest():
         return None
     return ent.get("dram_bytes_per_launch")
@@ -362,7 +363,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": kname, "achieved": kern_gbs[dom], "peak": peak,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",
                 "frac": kern_gbs[dom] / peak,
-                "traffic": recorded_traffic(kname, args.precision),
+                "traffic": recorded_traffic(kname, args.precision, args.workload),
                 "algorithmic_bytes": alg[dom], "avg_ms": avg[dom]}
     spread_fft_ms = avg["pass_a_spread_fft"] + avg["pass_b_fft_deconv_power"]
     spread_fft_bytes = alg["pass_a_spread_fft"] + alg["pass_b_fft_deconv_power"]
