@@ -84,20 +84,22 @@ constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
 constexpr size_t kSmemOptin = 232448;             // opt-in shared memory per block (227 KB)
 
-bool build_fft(int L, FftPlan *fp);
+bool radix_schedule(int L, std::vector<int> &rad);
 
 // Shared memory of a one-column pass-A block (the smallest block a split can
 // use: padded column, per-column and root tables, slot table) plus 2 KB of
-// margin: a column length above the opt-in limit cannot launch.
+// margin: a column length above the opt-in limit cannot launch.  Called for
+// every candidate split of every series of a batch, so it only derives the
+// radix schedule (not the verified stage tables).
 bool passA_column_fits(int64_t N2, int prec)
 {
-    FftPlan fp;
-    if (N2 > (1 << 20) || !build_fft((int)N2, &fp)) return false;
+    std::vector<int> rad;
+    if (N2 > (1 << 20) || !radix_schedule((int)N2, rad)) return false;
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     const size_t nhi = (size_t)(N2 + 63) / 64;
     const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
     const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
-                         sizeof(int) * (size_t)(N2 / fp.Rlast) + 2048;
+                         sizeof(int) * (size_t)(N2 / rad.back()) + 2048;
     return bytes <= kSmemOptin;
 }
 

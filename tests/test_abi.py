@@ -131,3 +131,15 @@ def test_grid_sizes_are_minimal_admissible():
         # (a power of two) times an even N2, so k >= 6
         smaller = [c * 2 ** k for c in ODD for k in range(6, 40) if nmin <= c * 2 ** k < n]
         assert not smaller, (nf, n, smaller[:3])
+
+
+def test_choose_params_is_cheap_enough_for_per_series_calls():
+    # a ragged batch chooses parameters for every series on each call
+    import time
+
+    import paper_2409_08090_gb300 as nl
+    nl.load_library()
+    t0 = time.perf_counter()
+    for i in range(2000):
+        nl.ls_choose_params(1000 + 600 * i, 1e-6, nl.LS_FP32, 100 + 50 * i)
+    assert time.perf_counter() - t0 < 2.0
