@@ -843,8 +843,13 @@ struct PassBArgs {
     Geometry g;
     Batch bt;
     int shared;            // see PassAArgs
+    // 0: the three rows of each series.  Shared times: 1 transforms the two
+    // common rows (w^ at f and 2f, H slots 0 and 1) once and writes them back
+    // deconvolved, in slot order; 2 then transforms each series' own row and
+    // reads the common values from there.
+    int stage;
     const Cplx<T> *twB;    // two-level root table, length N1
-    const Cplx<T> *H;
+    Cplx<T> *H;
     const T *deconv;       // 1/phi_hat(|k'|) in pass-B order, [d * N1 + slot]
     const Stats *st;
     double *power;
@@ -932,8 +937,10 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     double *sums = B.sums ? B.sums + 6 * sd.out_off : nullptr;
     // rows of H straight into shared memory with asynchronous copies: every
     // element of the three rows is in flight at once, without registers.
+    const int stage = B.stage;
     for (int gi = 0; gi < 3; ++gi) {
         if (B.nofit && gi == 1) continue;
+        if ((stage == 1 && gi == 0) || (stage == 2 && gi != 0)) continue;
         const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
         const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
         V *dst = buf + (size_t)gi * Lp;
@@ -949,7 +956,26 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     cp_async_wait_all();
     __syncthreads();
 
-    if (B.nofit) {                          // rows 0 and 2
+    if (stage == 1) {                       // rows 1 and 2 (row 2 alone without a fitted mean)
+        if (B.nofit) fft_dif<1>(buf + 2 * (size_t)Lp, 1, Lp, g.fb, roots);
+        else if (sizeof(T) == 4) fft_dif<2>(buf + Lp, 2, Lp, g.fb, roots);
+        else fft_dif<1>(buf + Lp, 2, Lp, g.fb, roots);
+        // write both rows back deconvolved, in slot order, over the same row d of
+        // H slots 0 and 1 (this block read that row; no other block touches it)
+        V *o2 = B.H + (size_t)d * N1;
+        V *o3 = B.H + (size_t)g.n + (size_t)d * N1;
+        const T *dcr = B.deconv + (size_t)d * N1;
+        for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
+            const T dc = __ldg(dcr + pos);
+            const int sp = pad16(pos);
+            o2[pos] = B.nofit ? mk2(T(0), T(0)) : cscale(buf[Lp + sp], dc);
+            o3[pos] = cscale(buf[2 * Lp + sp], dc);
+        }
+        return;
+    }
+    if (stage == 2) {
+        fft_dif<1>(buf, 1, Lp, g.fb, roots);
+    } else if (B.nofit) {                   // rows 0 and 2
         if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
         else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
     } else {
@@ -986,9 +1012,17 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             const int64_t k = d + (int64_t)N2 * c;
             const int64_t kp = (c < c1) ? k : k - n;
             const int sp = pad16(pos);
-            const T dc = dcv[r];
-            const V g1 = buf[sp], g3 = buf[2 * Lp + sp];
-            const V g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
+            T dc = dcv[r];
+            V g1 = buf[sp], g2, g3;
+            if (stage == 2) {                   // common rows, already deconvolved
+                g1 = cscale(g1, dc);
+                g2 = B.H[(size_t)d * N1 + pos];
+                g3 = B.H[(size_t)g.n + (size_t)d * N1 + pos];
+                dc = T(1);
+            } else {
+                g3 = buf[2 * Lp + sp];
+                g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
+            }
             const int64_t out = kp + K0;
             if (power) {
                 const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, lam_tol_t);
@@ -1153,11 +1187,12 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     if ((err = allow_max_dynamic_smem((const void *)k_passA<T>)) != cudaSuccess) return err;
     // Pairs of adjacent column blocks write whole 32-byte sectors of each row
     // of H together (cluster store in k_passA).  Measured on the 1e6-point,
-    // 1.2e7-frequency FP32 workload: pass A 0.82 ms without clusters, 0.75 ms
-    // with pairs, 0.85 and 1.10 ms with clusters of 4 and 8 (larger clusters
-    // wait longer at their barriers and are harder to place).  nbins is a
-    // power of two, so cs divides it.
-    int cs = g.nbins < 2 ? g.nbins : 2;
+    // 1.2e7-frequency FP32 workload (2048 column blocks): pass A 0.82 ms
+    // without clusters, 0.75 ms with pairs, 0.85 and 1.10 ms with clusters of
+    // 4 and 8 (larger clusters wait longer at their barriers and are harder to
+    // place); the small grids of batches (tens to hundreds of column blocks)
+    // ran about 2% faster without.  nbins is a power of two, so cs divides it.
+    int cs = g.nbins >= 512 ? 2 : 1;
     while (cs > 1 && (cs * g.BA * (int)sizeof(Cplx<T>)) % 16) cs >>= 1;
     A.cs = cs;
     {
@@ -1183,7 +1218,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.bt = bt;
     B.shared = shared;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
-    B.H = static_cast<const Cplx<T> *>(ws.H);
+    B.H = static_cast<Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv_slot);
     B.st = ws.stats;
     B.power = power;
@@ -1197,7 +1232,15 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     if ((err = allow_max_dynamic_smem((const void *)k_passB<T>)) != cudaSuccess) return err;
-    k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
+    if (shared) {
+        B.stage = 1;
+        k_passB<T><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        B.stage = 2;
+        k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
+    } else {
+        B.stage = 0;
+        k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
+    }
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
