@@ -4,7 +4,7 @@
 // sign of the type-1 transform (Eq. 2), so Re g = C and Im g = S.
 //
 // Each transform runs in place as a decimation-in-frequency (Gentleman-Sande)
-// sequence of radix-R stages, R in {3, 5} first and then {16, 8, 4, 2}, each
+// sequence of radix-R stages, R in {9, 3, 5} first and then {16, 8, 4, 2}, each
 // butterfly an R-point DFT in registers.  Every butterfly reads and writes the
 // same R slots, so one buffer suffices and a stage needs only a barrier at its
 // end.  The output is left in digit-reversed order; slot_to_freq() gives the
@@ -104,6 +104,37 @@ template <> struct Dft<8> {
         for (int k = 0; k < 4; ++k) {
             v[k] = cadd(e[k], o[k]);
             v[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// 9 = 3 x 3: x index n = 3 n1 + n2, output k = k1 + 3 k2 (one stage where two
+// radix-3 stages would each read and write the whole transform).
+template <> struct Dft<9> {
+    template <typename V> __device__ __forceinline__ static void run(V *v) {
+        using T = decltype(v[0].x);
+        const V w1 = mk2(T(0.76604444311897803520), T(0.64278760968653932632));   // e^{2 pi i / 9}
+        const V w2 = mk2(T(0.17364817766693034885), T(0.98480775301220805936));   // e^{4 pi i / 9}
+        const V w4 = mk2(T(-0.93969262078590838405), T(0.34202014332566873304));  // e^{8 pi i / 9}
+        V y[3][3];
+#pragma unroll
+        for (int n2 = 0; n2 < 3; ++n2) {
+            V a[3] = {v[n2], v[n2 + 3], v[n2 + 6]};
+            Dft<3>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < 3; ++k1) y[n2][k1] = a[k1];
+        }
+        // y[n2][k1] *= exp(+2 pi i n2 k1 / 9)
+        y[1][1] = cmul(y[1][1], w1);
+        y[1][2] = cmul(y[1][2], w2);
+        y[2][1] = cmul(y[2][1], w2);
+        y[2][2] = cmul(y[2][2], w4);
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) {
+            V b[3] = {y[0][k1], y[1][k1], y[2][k1]};
+            Dft<3>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = b[k2];
         }
     }
 };
@@ -278,6 +309,7 @@ __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, cons
         const FftStage &st = fp.st[s];
         switch (st.R) {
         case 16: dif_stage_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 9: dif_stage_cols<9, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         case 8: dif_stage_cols<8, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         case 4: dif_stage_cols<4, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         case 5: dif_stage_cols<5, NC>(buf, ncol, colstride, st, roots, fp.L); break;

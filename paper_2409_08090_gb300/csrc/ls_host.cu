@@ -123,12 +123,13 @@ int ilog2_exact(int64_t x)
 }
 
 // Radix schedule of a sub-FFT of length L = c 2^k (c = 3^a 5^b, k >= 1): the
-// odd radices first, then one stage of 8, 4 or 2 for k mod 4, then 16s, so
-// the last stage is a power of two (16 whenever k >= 4).
+// odd radices first (3s paired into 9s), then one stage of 8, 4 or 2 for
+// k mod 4, then 16s, so the last stage is a power of two (16 whenever k >= 4).
 bool radix_schedule(int L, std::vector<int> &rad)
 {
     rad.clear();
     int x = L;
+    while (x % 9 == 0) { rad.push_back(9); x /= 9; }
     while (x % 3 == 0) { rad.push_back(3); x /= 3; }
     while (x % 5 == 0) { rad.push_back(5); x /= 5; }
     int k = 0;
