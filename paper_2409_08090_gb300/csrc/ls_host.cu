@@ -82,7 +82,6 @@ constexpr int kEvPerSet = LS_NUM_STAGES + 1;
 constexpr int kN1MaxF32 = 4096, kN2MaxF32 = 25600;
 constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
-constexpr size_t kSmemOptin = 232448;             // opt-in shared memory per block (227 KB)
 
 bool radix_schedule(int L, std::vector<int> &rad);
 
@@ -100,7 +99,7 @@ bool passA_column_fits(int64_t N2, int prec)
     const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
     const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
                          sizeof(int) * (size_t)(N2 / rad.back()) + 2048;
-    return bytes <= kSmemOptin;
+    return bytes <= kSmemOptinBytes;
 }
 
 struct DeviceGuard {

@@ -12,6 +12,7 @@ namespace nls {
 constexpr int kMaxStages = 8;     // stages of one sub-FFT
 constexpr int kTw4Bits = 12;      // four-step twiddle table split: W^p = lo[p % 4096] * hi[p / 4096]
 constexpr int kThreadsA = 256;
+constexpr size_t kSmemOptinBytes = 232448;   // opt-in shared memory per block (227 KB)
 constexpr int kThreadsB = 256;
 constexpr int kMinN1 = 32;        // keeps every kernel footprint (w <= 16) within two columns
 
@@ -163,7 +164,7 @@ size_t point_record_bytes();
 // Stage descriptors of a length-L sub-FFT (false if L has no schedule).
 bool fft_plan_for_length(int L, FftPlan *fp);
 
-size_t passA_smem_bytes(const Geometry &g, size_t cx_bytes);
+size_t passA_smem_bytes(const Geometry &g, size_t cx_bytes, int cs);
 size_t passB_smem_bytes(const Geometry &g, size_t cx_bytes);
 
 }  // namespace nls

@@ -482,10 +482,15 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     const int N1 = g.N1, N2 = g.N2, BA = g.BA;
     const int Lp = padded_len(N2);
     const int nhi = (N2 + 63) >> 6;
+    // The four-step twiddle tables cover the columns of the whole cluster
+    // (tc = cs * BA from column a_base): the cluster store twiddles the
+    // partner's columns as it writes them.
+    const int rank = (int)(blockIdx.x % (unsigned)A.cs);
+    const int tc = A.cs * BA;
     V *buf = reinterpret_cast<V *>(smem_raw);   // BA columns, padded layout
     V *alo = buf + (size_t)BA * Lp;             // W_n^{a dl}, dl < 64, per column
-    V *ahi = alo + BA * 64;                     // W_n^{64 a dh}, per column
-    V *roots = ahi + BA * nhi;                  // two-level root table of length N2
+    V *ahi = alo + tc * 64;                     // W_n^{64 a dh}, per column
+    V *roots = ahi + tc * nhi;                  // two-level root table of length N2
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
     // Instance -> (series, transform 0: s1, 1: s2, 2: s3) and its slot of H.
@@ -504,19 +509,20 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     if (A.nofit && grid == 1) return;    // whole block: before any barrier
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
+    const int a_base = (blk - rank) * BA;
     const int64_t pt_off = series_of(A.bt, ser).rec_off;
 
     for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
     load_roots(roots, A.twA, N2);
     fill_slot_table(dtab, g.fa);
-    for (int i = threadIdx.x; i < BA * 64; i += blockDim.x) {
+    for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
         const int col = i >> 6;
-        alo[i] = tw4_root(A.tw4, (int64_t)(a0 + col) * (i & 63));
+        alo[i] = tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63));
     }
-    for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
+    for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
         const int col = i / nhi;
         const int dh = i - col * nhi;
-        ahi[i] = tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * dh) % g.n);
+        ahi[i] = tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n);
     }
     __syncthreads();
 
@@ -597,25 +603,14 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     if (A.cs > 1) {
         // Cluster store.  A row of H receives only BA columns from one block,
         // so the cs blocks of a cluster (adjacent column blocks) write their
-        // rows together: each block first applies its twiddles in place, then
-        // takes every cs-th row and writes the cluster's cs * BA columns of it
-        // as 16-byte units, reading the other blocks' columns from their shared
-        // memory, so each row segment fills whole 32-byte sectors.
+        // rows together: each block takes every cs-th row and writes the
+        // cluster's cs * BA columns of it, twiddled, as 16-byte units, reading
+        // the other blocks' columns from their shared memory, so each row
+        // segment fills whole 32-byte sectors.
         namespace cg = cooperative_groups;
         cg::cluster_group cluster = cg::this_cluster();
-#pragma unroll 2
-        for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
-            const int d = slot_freq_tab(pos, dtab, g.fa);
-            const int sp = pad16(pos);
-            for (int col = 0; col < BA; ++col) {
-                const V tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
-                V *e = buf + (size_t)col * Lp + sp;
-                *e = cmul(*e, tw);
-            }
-        }
         cluster.sync();
         const int cs = A.cs;
-        const int rank = (int)cluster.block_rank();
         const int cc = cs * BA;                                  // columns of the cluster
         constexpr int kPerUnit = 16 / (int)sizeof(V);            // columns per 16-byte unit
         const int ur = cc / kPerUnit;                            // units per row
@@ -645,12 +640,16 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
                         const int pos = rank + cs * i;
                         dd[r] = slot_freq_tab(pos, dtab, g.fa);
                         const int sp = pad16(pos);
+                        const int dl = dd[r] & 63, dh = dd[r] >> 6;
                         if constexpr (sizeof(V) == 8) {
                             const int c0 = 2 * u, c1 = 2 * u + 1;
-                            va[r] = peer[c0 / BA][(size_t)(c0 % BA) * Lp + sp];
-                            vb[r] = peer[c1 / BA][(size_t)(c1 % BA) * Lp + sp];
+                            va[r] = cmul(peer[c0 / BA][(size_t)(c0 % BA) * Lp + sp],
+                                         cmul(alo[c0 * 64 + dl], ahi[c0 * nhi + dh]));
+                            vb[r] = cmul(peer[c1 / BA][(size_t)(c1 % BA) * Lp + sp],
+                                         cmul(alo[c1 * 64 + dl], ahi[c1 * nhi + dh]));
                         } else {
-                            va[r] = peer[u / BA][(size_t)(u % BA) * Lp + sp];
+                            va[r] = cmul(peer[u / BA][(size_t)(u % BA) * Lp + sp],
+                                         cmul(alo[u * 64 + dl], ahi[u * nhi + dh]));
                         }
                     }
                 }
@@ -1079,10 +1078,10 @@ size_t point_record_bytes()
     return sizeof(uint32_t) + sizeof(T) + 2 * sizeof(Cplx<T>);
 }
 
-size_t passA_smem_bytes(const Geometry &g, size_t cx)
+size_t passA_smem_bytes(const Geometry &g, size_t cx, int cs)
 {
     const size_t nhi = (size_t)(g.N2 + 63) / 64;
-    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)g.BA * (64 + nhi) + 64 + nhi) +
+    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)cs * g.BA * (64 + nhi) + 64 + nhi) +
            sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
 }
 
@@ -1183,7 +1182,6 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.twA = static_cast<const Cplx<T> *>(ws.twA);
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
-    const size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>));
     if ((err = allow_max_dynamic_smem((const void *)k_passA<T>)) != cudaSuccess) return err;
     // Pairs of adjacent column blocks write whole 32-byte sectors of each row
     // of H together (cluster store in k_passA).  Measured on the 1e6-point,
@@ -1194,6 +1192,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // ran about 2% faster without.  nbins is a power of two, so cs divides it.
     int cs = g.nbins >= 512 ? 2 : 1;
     while (cs > 1 && (cs * g.BA * (int)sizeof(Cplx<T>)) % 16) cs >>= 1;
+    size_t smA = passA_smem_bytes(g, sizeof(Cplx<T>), cs);
+    if (cs > 1 && smA + 1024 > kSmemOptinBytes) {    // the cluster's tables do not fit
+        cs = 1;
+        smA = passA_smem_bytes(g, sizeof(Cplx<T>), cs);
+    }
     A.cs = cs;
     {
         cudaLaunchConfig_t cfg = {};
