@@ -148,8 +148,9 @@ class _Slot:
         self.out_host = None
         self.plan = None
         self.keep = None        # device tensors alive until the batch completes
-        self.pin_in = None      # pinned staging reused across batches
-        self.pin_out = None
+        self.pin_in = None      # pinned input staging reused across batches
+        self.pin_out = None     # pinned output staging of small batches
+        self.views = False      # results of the batch in flight are views of its buffer
 
     def pinned(self, which: str, n: int):
         import torch
@@ -164,8 +165,9 @@ class PeriodogramServer:
     """Continuous-batching periodogram server on one GPU.
 
     submit() returns a Future resolved with the float64 power: a numpy array
-    (results="host"), or a view of the batch's CUDA tensor (results="device",
-    no host copy; the batch's device memory lives as long as any view).
+    (results="host": a view of the batch's pinned host buffer, which lives as
+    long as any of its views), or a view of the batch's CUDA tensor
+    (results="device", no host copy at all).
     `streams` batches can be on the GPU at once; requests arriving meanwhile
     are admitted (memory permitting) into the next batch.
     """
@@ -182,6 +184,7 @@ class PeriodogramServer:
         if results not in ("host", "device"):
             raise ValueError("results must be 'host' (numpy arrays) or 'device' (CUDA tensors)")
         self.results = results
+        self.copy_limit = 32 << 20     # bytes of output below which results are copied out
         self.sched = Scheduler(memory_budget, max_batch)
         self.slots = [_Slot(self.device) for _ in range(max(1, int(streams)))]
         self.cv = threading.Condition()
@@ -278,7 +281,16 @@ class PeriodogramServer:
                 fit_mean=not (word & nl.LS_NO_FIT_MEAN),
                 center_data=not (word & nl.LS_NO_CENTER))
             if self.results == "host":
-                out_host = slot.pinned("pin_out", out.numel())
+                if out.numel() * 8 <= self.copy_limit:
+                    # small batch: the slot's reused pinned buffer, copied out per request
+                    out_host = slot.pinned("pin_out", out.numel())
+                    slot.views = False
+                else:
+                    # large batch: a fresh pinned buffer (torch caches pinned
+                    # blocks) handed out as views, so no per-request host copy;
+                    # it returns to the cache when its last view is dropped
+                    out_host = torch.empty(out.numel(), dtype=torch.float64, pin_memory=True)
+                    slot.views = True
                 out_host.copy_(out, non_blocking=True)
             else:
                 out_host = out
@@ -302,7 +314,7 @@ class PeriodogramServer:
             if st != nl.LS_OK:
                 r.future.set_exception(nl.LSError(st, "batch"))
             elif self.results == "host":
-                r.future.set_result(res[o:o + r.nf].copy())
+                r.future.set_result(res[o:o + r.nf] if slot.views else res[o:o + r.nf].copy())
             else:
                 r.future.set_result(res[int(o):int(o) + r.nf])
         self.completed.extend(batch)
