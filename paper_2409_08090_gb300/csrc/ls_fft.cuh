@@ -21,6 +21,61 @@ namespace nls {
 __device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
 
+// Double-float numbers for the transforms of the FP64 path: a value is
+// hi + lo with two FP32 parts (about 48 significant bits), so the FFT runs on
+// the FP32 units (this part issues FP64 at 1/64 of the FP32 rate).  Sum:
+// Knuth's two-sum of the high parts with the low parts added in, an error
+// below 2^-47 (|a| + |b|), so transform errors stay bounded by the input norm
+// as with FP64; product: the fma two-product.  Spreading, deconvolution and
+// the power stay in FP64.
+struct dfl {
+    float hi, lo;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ explicit dfl(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+struct alignas(16) dfl2 {
+    dfl x, y;
+};
+__device__ __forceinline__ dfl operator+(dfl a, dfl b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return dfl(h, e - (h - s));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float h = p + e;
+    return dfl(h, e - (h - p));
+}
+__device__ __forceinline__ dfl2 mk2(dfl a, dfl b)
+{
+    dfl2 r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+
+// Complex type the transforms run in, per storage precision, and conversions.
+template <typename T> struct FftOf;
+template <> struct FftOf<float> { using type = float2; };
+template <> struct FftOf<double> { using type = dfl2; };
+__device__ __forceinline__ float2 to_fft(float2 v) { return v; }
+__device__ __forceinline__ dfl2 to_fft(double2 v) { return mk2(dfl(v.x), dfl(v.y)); }
+__device__ __forceinline__ float2 from_fft(float2 v) { return v; }
+__device__ __forceinline__ double2 from_fft(dfl2 v)
+{
+    return make_double2((double)v.x.hi + (double)v.x.lo, (double)v.y.hi + (double)v.y.lo);
+}
+
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk2(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk2(a.x - b.x, a.y - b.y); }
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
@@ -194,12 +249,13 @@ __device__ __forceinline__ V root_tw(const V *roots, int p)
     return cmul(roots[p & 63], roots[64 + (p >> 6)]);
 }
 
-// Load the two-level root table of length L into shared memory (no barrier).
-template <typename V>
-__device__ __forceinline__ void load_roots(V *dst, const V *__restrict__ src, int L)
+// Load the two-level root table of length L into shared memory in the
+// transform's type (no barrier).
+template <typename W, typename V>
+__device__ __forceinline__ void load_roots(W *dst, const V *__restrict__ src, int L)
 {
     const int cnt = 64 + ((L + 63) >> 6);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = to_fft(__ldg(src + i));
 }
 
 // Frequency index held by output slot pos of fft_dif: pos = sum_s d_s m_s

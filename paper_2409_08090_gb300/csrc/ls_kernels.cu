@@ -476,7 +476,9 @@ __device__ __forceinline__ T es_kernel(T z, T beta)
 template <typename T>
 __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 {
-    using V = Cplx<T>;
+    using V = Cplx<T>;               // storage: the spread's accumulators, H
+    using F = typename FftOf<T>::type;   // the transform's type (double-float for FP64)
+    static_assert(sizeof(F) == sizeof(V), "transform and storage types share the layout");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = A.g;
     const int N1 = g.N1, N2 = g.N2, BA = g.BA;
@@ -488,9 +490,10 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     const int rank = (int)(blockIdx.x % (unsigned)A.cs);
     const int tc = A.cs * BA;
     V *buf = reinterpret_cast<V *>(smem_raw);   // BA columns, padded layout
-    V *alo = buf + (size_t)BA * Lp;             // W_n^{a dl}, dl < 64, per column
-    V *ahi = alo + tc * 64;                     // W_n^{64 a dh}, per column
-    V *roots = ahi + tc * nhi;                  // two-level root table of length N2
+    F *bufF = reinterpret_cast<F *>(buf);       // the same columns once spread
+    F *alo = bufF + (size_t)BA * Lp;            // W_n^{a dl}, dl < 64, per column
+    F *ahi = alo + tc * 64;                     // W_n^{64 a dh}, per column
+    F *roots = ahi + tc * nhi;                  // two-level root table of length N2
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
     // Instance -> (series, transform 0: s1, 1: s2, 2: s3) and its slot of H.
@@ -517,12 +520,12 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     fill_slot_table(dtab, g.fa);
     for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
         const int col = i >> 6;
-        alo[i] = tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63));
+        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
     }
     for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
         const int col = i / nhi;
         const int dh = i - col * nhi;
-        ahi[i] = tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n);
+        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
     }
     __syncthreads();
 
@@ -596,8 +599,13 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     __syncthreads();
 
     // ---- column FFTs over b ----
-    if (sizeof(T) == 4 && (BA & 1) == 0) fft_dif<2>(buf, BA, Lp, g.fa, roots);
-    else fft_dif<1>(buf, BA, Lp, g.fa, roots);
+    if constexpr (sizeof(T) == 8) {
+        // FP64 accumulators -> double-float, in place (same 16 bytes per cell)
+        for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) bufF[i] = to_fft(buf[i]);
+        __syncthreads();
+    }
+    if (sizeof(T) == 4 && (BA & 1) == 0) fft_dif<2>(bufF, BA, Lp, g.fa, roots);
+    else fft_dif<1>(bufF, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     if (A.cs > 1) {
@@ -618,10 +626,10 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
         const int rpw = 32 / lr;                                 // rows per warp step
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int sub_row = lane / lr, u0 = lane - sub_row * lr;
-        V *Hc = A.H + (size_t)slot * (size_t)g.n + (size_t)(blk - rank) * BA;
-        const V *peer[8];
+        F *Hc = reinterpret_cast<F *>(A.H + (size_t)slot * (size_t)g.n + (size_t)(blk - rank) * BA);
+        const F *peer[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) peer[q] = q < cs ? cluster.map_shared_rank(buf, q) : buf;
+        for (int q = 0; q < 8; ++q) peer[q] = q < cs ? cluster.map_shared_rank(bufF, q) : bufF;
         const int nwarps = (int)(blockDim.x >> 5);
         const int rows = (N2 - rank + cs - 1) / cs;               // rows this block writes
         const int step = nwarps * rpw;
@@ -630,7 +638,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
         constexpr int kRows = 4;
         for (int i0 = warp * rpw + sub_row; i0 < rows; i0 += kRows * step) {
             for (int u = u0; u < ur; u += lr) {
-                V va[kRows], vb[kRows];
+                F va[kRows], vb[kRows];
                 int dd[kRows];
 #pragma unroll
                 for (int r = 0; r < kRows; ++r) {
@@ -656,7 +664,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 #pragma unroll
                 for (int r = 0; r < kRows; ++r) {
                     if (dd[r] < 0) continue;
-                    V *dst = Hc + (size_t)dd[r] * N1;
+                    F *dst = Hc + (size_t)dd[r] * N1;
                     if constexpr (sizeof(V) == 8)
                         reinterpret_cast<float4 *>(dst)[u] =
                             make_float4(va[r].x, va[r].y, vb[r].x, vb[r].y);
@@ -668,7 +676,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
         cluster.sync();      // peers may still read this block's columns
         return;
     }
-    V *H = A.H + (size_t)slot * (size_t)g.n + a0;
+    F *H = reinterpret_cast<F *>(A.H + (size_t)slot * (size_t)g.n + a0);
     if constexpr (sizeof(T) == 4) {
         if ((BA & 1) == 0) {
             // Column pairs as one 16-byte store: a0, N1 and n are even, so every
@@ -680,10 +688,10 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
                 const int sp = pad16(pos);
                 float4 *dst = reinterpret_cast<float4 *>(H + (size_t)d * N1);
                 for (int c0 = 0; c0 < BA; c0 += 2) {
-                    const V t0 = cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]);
-                    const V t1 = cmul(alo[(c0 + 1) * 64 + (d & 63)], ahi[(c0 + 1) * nhi + (d >> 6)]);
-                    const V v0 = cmul(buf[(size_t)c0 * Lp + sp], t0);
-                    const V v1 = cmul(buf[(size_t)(c0 + 1) * Lp + sp], t1);
+                    const F t0 = cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]);
+                    const F t1 = cmul(alo[(c0 + 1) * 64 + (d & 63)], ahi[(c0 + 1) * nhi + (d >> 6)]);
+                    const F v0 = cmul(bufF[(size_t)c0 * Lp + sp], t0);
+                    const F v1 = cmul(bufF[(size_t)(c0 + 1) * Lp + sp], t1);
                     dst[c0 >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
                 }
             }
@@ -693,10 +701,10 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
         const int d = slot_freq_tab(pos, dtab, g.fa);
         const int sp = pad16(pos);
-        V *dst = H + (size_t)d * N1;
+        F *dst = H + (size_t)d * N1;
         for (int col = 0; col < BA; ++col) {
-            const V tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
-            dst[col] = cmul(buf[(size_t)col * Lp + sp], tw);
+            const F tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
+            dst[col] = cmul(bufF[(size_t)col * Lp + sp], tw);
         }
     }
 }
@@ -920,12 +928,13 @@ template <typename T>
 __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
 {
     using V = Cplx<T>;
+    using F = typename FftOf<T>::type;   // the transform's type (double-float for FP64)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = B.g;
     const int N1 = g.N1, N2 = g.N2;
     const int Lp = padded_len(N1);
-    V *buf = reinterpret_cast<V *>(smem_raw);   // 3 rows, padded layout
-    V *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
+    F *buf = reinterpret_cast<F *>(smem_raw);   // 3 rows, padded layout
+    F *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
     int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
     const int ser = blockIdx.y;
@@ -942,7 +951,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         if ((stage == 1 && gi == 0) || (stage == 2 && gi != 0)) continue;
         const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
         const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
-        V *dst = buf + (size_t)gi * Lp;
+        V *dst = reinterpret_cast<V *>(buf + (size_t)gi * Lp);   // H holds F bits (pass A)
         for (int i = threadIdx.x; i < N1; i += blockDim.x) cp_async_elem(dst + pad16(i), src + i);
     }
     cp_async_commit();
@@ -967,8 +976,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
             const T dc = __ldg(dcr + pos);
             const int sp = pad16(pos);
-            o2[pos] = B.nofit ? mk2(T(0), T(0)) : cscale(buf[Lp + sp], dc);
-            o3[pos] = cscale(buf[2 * Lp + sp], dc);
+            o2[pos] = B.nofit ? mk2(T(0), T(0)) : cscale(from_fft(buf[Lp + sp]), dc);
+            o3[pos] = cscale(from_fft(buf[2 * Lp + sp]), dc);
         }
         return;
     }
@@ -1012,15 +1021,15 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             const int64_t kp = (c < c1) ? k : k - n;
             const int sp = pad16(pos);
             T dc = dcv[r];
-            V g1 = buf[sp], g2, g3;
+            V g1 = from_fft(buf[sp]), g2, g3;
             if (stage == 2) {                   // common rows, already deconvolved
                 g1 = cscale(g1, dc);
                 g2 = B.H[(size_t)d * N1 + pos];
                 g3 = B.H[(size_t)g.n + (size_t)d * N1 + pos];
                 dc = T(1);
             } else {
-                g3 = buf[2 * Lp + sp];
-                g2 = B.nofit ? mk2(T(0), T(0)) : buf[Lp + sp];
+                g3 = from_fft(buf[2 * Lp + sp]);
+                g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[Lp + sp]);
             }
             const int64_t out = kp + K0;
             if (power) {
