@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--no-fft-reference", action="store_true")
     ap.add_argument("--upsampling", type=float, default=0.0,
                     help="fine-grid upsampling: 0 (plan chooses), 2.0 or 1.5")
     ap.add_argument("--serving-results", default="host", choices=["host", "device"],
@@ -388,6 +389,34 @@ def run_ours(args):
                "h2d_bytes_per_step": 3 * 8 * s.nd, "d2h_bytes_per_step": 8 * s.nf,
                "steps": nsteps, "host_buffers": "pinned"}
 
+    # -- the library FFT as a reference for the FFT step: cuFFT (through
+    # torch.fft) on the same three fine grids, complex, in the plan's precision,
+    # out of place.  Our FFT is fused with spreading (pass A) and with
+    # deconvolution and power (pass B); cuFFT alone does none of that.
+    fft_ref = None
+    if info.n <= 64_000_000 and not args.no_fft_reference:
+        cdt = torch.complex64 if args.precision == "fp32" else torch.complex128
+        grids = torch.randn(3, info.n, dtype=cdt, device=device)
+        for _ in range(3):
+            torch.fft.fft(grids)
+        torch.cuda.synchronize()
+        fe0 = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        fe1 = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        for i in range(5):
+            flush.fill_(float(i))
+            fe0[i].record()
+            torch.fft.fft(grids)
+            fe1[i].record()
+        torch.cuda.synchronize()
+        fms = sorted(a.elapsed_time(b) for a, b in zip(fe0, fe1))
+        fft_ref = {"library": "cuFFT via torch.fft.fft (reference only, not on the path)",
+                   "grids": 3, "n": int(info.n), "dtype": str(cdt).replace("torch.", ""),
+                   "ms_median": fms[len(fms) // 2],
+                   "ours_passes_ms": spread_fft_ms,
+                   "note": "library: the three n-point FFTs alone; ours: pass A (spread + "
+                           "column FFTs + twiddle) plus pass B (row FFTs + deconvolution + power)"}
+        del grids
+
     # -- small problems: launch-bound, so compare direct calls with a CUDA-graph
     # replay of the same pipeline (back to back on resident buffers, no flush)
     graph = None
@@ -474,7 +503,7 @@ def run_ours(args):
                        "frac_of_peak": spread_fft_bytes / (spread_fft_ms * 1e-3) / 1e9 / peak},
         "stage_ms": avg, "stage_gbs": kern_gbs,
         "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
-        "graph_replay": graph,
+        "graph_replay": graph, "fft_reference": fft_ref,
         "gpu_launches": 6 * args.steps,
         "clocks": clk, "wall_s": wall,
     }
