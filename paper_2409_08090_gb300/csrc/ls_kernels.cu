@@ -515,21 +515,8 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     const int a_base = (blk - rank) * BA;
     const int64_t pt_off = series_of(A.bt, ser).rec_off;
 
-    for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
-    load_roots(roots, A.twA, N2);
-    fill_slot_table(dtab, g.fa);
-    for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
-        const int col = i >> 6;
-        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
-    }
-    for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
-        const int col = i / nhi;
-        const int dh = i - col * nhi;
-        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
-    }
-    __syncthreads();
-
-    // ---- spread ----
+    // ---- spread set-up: the record ranges and each thread's first records are
+    // requested before the prologue, so their latency overlaps it ----
     const PointSet<T> P = shifted((grid < 2) ? A.px : A.p2, pt_off);
     const V *str = (grid == 1) ? P.s[1] : P.s[0];
     const int *bs = A.binstart + (size_t)ser * 2 * (g.nbins + 1) + ((grid < 2) ? 0 : (g.nbins + 1));
@@ -549,16 +536,13 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     }
     const int cnt0 = r0e - r0s;
     const int total = cnt0 + (r1e - r1s);
-    const T halfw = T(0.5) * T(g.w);
-    const T zscale = T(2) / T(g.w);
-    const T beta = T(g.beta);
     // kPre records per thread are loaded before any is used, so their global
     // loads overlap instead of forming one dependent chain per record.
     constexpr int kPre = 4;
-    for (int e0 = threadIdx.x; e0 < total; e0 += kPre * blockDim.x) {
-        uint32_t abv[kPre];
-        T rv[kPre];
-        V sv[kPre];
+    uint32_t abv[kPre];
+    T rv[kPre];
+    V sv[kPre];
+    auto load_chunk = [&](int e0) {
 #pragma unroll
         for (int q = 0; q < kPre; ++q) {
             const int e = e0 + q * (int)blockDim.x;
@@ -569,6 +553,29 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
                 sv[q] = __ldg(str + j);
             }
         }
+    };
+    load_chunk((int)threadIdx.x);
+
+    for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
+    load_roots(roots, A.twA, N2);
+    fill_slot_table(dtab, g.fa);
+    for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
+        const int col = i >> 6;
+        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
+    }
+    for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
+        const int col = i / nhi;
+        const int dh = i - col * nhi;
+        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
+    }
+    __syncthreads();
+
+    // ---- spread ----
+    const T halfw = T(0.5) * T(g.w);
+    const T zscale = T(2) / T(g.w);
+    const T beta = T(g.beta);
+    for (int e0 = threadIdx.x; e0 < total; e0 += kPre * blockDim.x) {
+        if (e0 != (int)threadIdx.x) load_chunk(e0);
 #pragma unroll
         for (int q = 0; q < kPre; ++q) {
             if (e0 + q * (int)blockDim.x >= total) break;
