@@ -250,6 +250,18 @@ ls_status ls_choose_params(int64_t nf, double eps, int prec, int64_t max_nd, dou
 double ls_kernel_ft(double k, int64_t n, int32_t width, double beta);
 
 /*
+ * ls_selftest_kernel_eval: runs, on `device`, the double-float evaluation of
+ * the ES kernel psi(z) = exp(beta (sqrt(1 - z^2) - 1)) that the FP64 path's
+ * spreading uses and the plain FP64 one, at n points evenly spaced on [-1, 1]
+ * (2 <= n <= 2^24, 0 < beta < 100), and writes the largest absolute
+ * difference to *max_abs_err (psi <= 1, so this is the error relative to the
+ * kernel's peak, the scale the spreading error is measured on; near z = +-1
+ * the relative error of either evaluation grows with 1/sqrt(1 - z^2)).
+ * Synchronous; allocates 16 n bytes.
+ */
+ls_status ls_selftest_kernel_eval(double beta, int n, int device, double *max_abs_err);
+
+/*
  * ls_execute_noalloc: the periodogram of one small series without allocating
  * any memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- code running while a CUDA

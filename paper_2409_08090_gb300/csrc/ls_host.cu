@@ -1028,6 +1028,30 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     return LS_OK;
 }
 
+ls_status ls_selftest_kernel_eval(double beta, int n, int device, double *max_abs_err)
+{
+    if (!max_abs_err || n < 2 || n > (1 << 24) || !(beta > 0.0) || !(beta < 100.0))
+        return LS_ERR_ARG;
+    DeviceGuard guard(device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    double *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(double) * (size_t)n);
+    if (e != cudaSuccess) return LS_ERR_NOMEM;
+    e = launch_kernel_eval_pair(n, beta, d, d + n, 0);
+    std::vector<double> h(2 * (size_t)n);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h.data(), d, 2 * sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e);
+    double worst = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double d = fabs(h[(size_t)i] - h[(size_t)n + i]);
+        if (!(d <= worst)) worst = d;
+    }
+    *max_abs_err = worst;
+    return LS_OK;
+}
+
 ls_status ls_set_stream(ls_plan_t p, void *stream)
 {
     if (!p) return LS_ERR_ARG;

@@ -158,6 +158,11 @@ template <typename T>
 cudaError_t launch_deconv_slot(const Geometry &g, void *out, const void *compact, int64_t count,
                                cudaStream_t st);
 
+// Self-test: the FP64 path's double-float kernel evaluation and the FP64 one
+// at n points of [-1, 1] (device buffers of n doubles each).
+cudaError_t launch_kernel_eval_pair(int n, double beta, double *dfl_out, double *fp64_out,
+                                    cudaStream_t st);
+
 template <typename T>
 size_t point_record_bytes();
 

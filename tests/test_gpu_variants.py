@@ -149,3 +149,16 @@ def test_unknown_model_bits_are_rejected(nl):
                            s.nf, 1e-9, word, out.data_ptr())
         assert st == nl.LS_ERR_UNSUPPORTED
     plan.close()
+
+
+@pytest.mark.parametrize("beta", [2.3 * 7, 2.3 * 10, 2.3 * 13, 0.976 * 3.14159 * (1 - 1 / 3) * 12])
+def test_double_float_kernel_evaluation_matches_fp64(nl, beta):
+    # the FP64 path spreads with a double-float evaluation of psi (exp and sqrt
+    # on the FP32 units) for tolerances down to 1e-11; on the kernel's peak
+    # scale it must agree with the FP64 exp/sqrt evaluation to a small fraction
+    # of that (x = beta (s - 1) carries about beta 2^-48)
+    import ctypes
+    err = ctypes.c_double()
+    st = nl._lib.ls_selftest_kernel_eval(beta, 200_001, 0, ctypes.byref(err))
+    assert st == nl.LS_OK
+    assert err.value <= beta * 2.0 ** -48 * 1.5, err.value
