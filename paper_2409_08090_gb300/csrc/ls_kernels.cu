@@ -464,6 +464,7 @@ struct PassAArgs {
     const Cplx<T> *tw4;    // four-step table (lo 4096, hi)
     Cplx<T> *H;
     int cs;                // blocks per thread-block cluster along the columns (1: none)
+    int ny;                // instances (transforms of series) along the grid's y
 };
 
 template <typename T>
@@ -527,8 +528,11 @@ __global__ void k_kernel_eval_pair(int n, double beta, double *dfl_out, double *
     }
 }
 
+// One instance (a transform of a series) of one column block; the tables are
+// built when build_tables is set (the first instance a block takes).
 template <typename T>
-__global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
+__device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int y,
+                                               const bool build_tables)
 {
     using V = Cplx<T>;               // storage: the spread's accumulators, H
     using F = typename FftOf<T>::type;   // the transform's type (double-float for FP64)
@@ -555,15 +559,15 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     // of series 0, slot 2 + s the s1 of series s.
     int ser, grid, slot;
     if (A.shared) {
-        slot = blockIdx.y;
+        slot = y;
         ser = slot < 2 ? 0 : slot - 2;
         grid = slot < 2 ? slot + 1 : 0;
     } else {
-        ser = blockIdx.y / 3;
-        grid = blockIdx.y - 3 * ser;
-        slot = blockIdx.y;
+        ser = y / 3;
+        grid = y - 3 * ser;
+        slot = y;
     }
-    if (A.nofit && grid == 1) return;    // whole block: before any barrier
+    if (A.nofit && grid == 1) return;    // whole block: before any barrier (y is uniform)
     const int blk = blockIdx.x;
     const int a0 = blk * BA;
     const int a_base = (blk - rank) * BA;
@@ -611,16 +615,18 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
     load_chunk((int)threadIdx.x);
 
     for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
-    load_roots(roots, A.twA, N2);
-    fill_slot_table(dtab, g.fa);
-    for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
-        const int col = i >> 6;
-        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
-    }
-    for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
-        const int col = i / nhi;
-        const int dh = i - col * nhi;
-        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
+    if (build_tables) {
+        load_roots(roots, A.twA, N2);
+        fill_slot_table(dtab, g.fa);
+        for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
+            const int col = i >> 6;
+            alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
+        }
+        for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
+            const int col = i / nhi;
+            const int dh = i - col * nhi;
+            ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
+        }
     }
     __syncthreads();
 
@@ -774,6 +780,34 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
             const F tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
             dst[col] = cmul(bufF[(size_t)col * Lp + sp], tw);
         }
+    }
+}
+
+
+// One instance per block (blockIdx.y), the usual launch.
+template <typename T>
+__global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
+{
+    passA_instance<T>(A, (int)blockIdx.y, true);
+}
+
+// Many instances per block: y = blockIdx.y, + gridDim.y, ... of the block's
+// column block (a persistent loop when a batch has more instances than the
+// launch has rows of blocks); the tables depend only on the columns and are
+// built once.  An instance skipped without a fitted mean is skipped by the
+// whole block (and cluster), so the barriers stay uniform.
+template <typename T>
+__global__ void __launch_bounds__(kThreadsA, 2) k_passA_loop(PassAArgs<T> A)
+{
+    bool first = true;
+    for (int y = blockIdx.y; y < A.ny; y += gridDim.y) {
+        if (A.nofit) {
+            const int grid = A.shared ? (y < 2 ? y + 1 : 0) : y % 3;
+            if (grid == 1) continue;
+        }
+        if (!first) __syncthreads();      // the previous instance is done with the buffer
+        passA_instance<T>(A, y, first);
+        first = false;
     }
 }
 
@@ -932,6 +966,7 @@ struct PassBArgs {
     double lam_tol;        // eigenvalues of M at or below this count as zero
     int nofit;             // 1: no offset in the model: C = S = 0, grid s2 absent
     int norm;              // 0 standard, 1 model, 2 log, 3 psd
+    int nser;              // series of the launch (stages 0 and 2)
 };
 
 // Normalisation of the standard power P = p / YY (p the explained weighted
@@ -1005,15 +1040,33 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     F *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
     int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
-    const int ser = blockIdx.y;
+    const int stage = B.stage;
+    load_roots(roots, B.twB, N1);
+    fill_slot_table(dtab, g.fb);
+    V *bufV = reinterpret_cast<V *>(buf);
+    if (stage == 2) {
+        // the common rows of a shared-times batch (deconvolved, slot order) are the
+        // same for every series of this row: keep them in rows 1 and 2 for all
+        for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
+            const int sp = pad16(pos);
+            bufV[Lp + sp] = B.H[(size_t)d * N1 + pos];
+            bufV[2 * Lp + sp] = B.H[(size_t)g.n + (size_t)d * N1 + pos];
+        }
+    }
+    const int nser = stage == 1 ? 1 : B.nser;
+
+    // The block takes the series s = blockIdx.y, + gridDim.y, ... of its row d
+    // (a persistent loop when the batch has more series than the launch has
+    // rows of blocks): the tables are built once.
+    for (int ser = blockIdx.y; ser < nser; ser += gridDim.y) {
     const SeriesDesc sd = series_of(B.bt, ser);
     const int64_t nf = sd.nf, K0 = sd.ph.K0;
     const Stats *stat = B.st + ser;
     double *power = B.power ? B.power + sd.out_off : nullptr;
     double *sums = B.sums ? B.sums + 6 * sd.out_off : nullptr;
+    __syncthreads();                      // the previous series is done with buf
     // rows of H straight into shared memory with asynchronous copies: every
     // element of the three rows is in flight at once, without registers.
-    const int stage = B.stage;
     for (int gi = 0; gi < 3; ++gi) {
         if (B.nofit && gi == 1) continue;
         if ((stage == 1 && gi == 0) || (stage == 2 && gi != 0)) continue;
@@ -1027,8 +1080,6 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     const double YY = stat->YY;
     const double psd_factor = 0.5 * stat->W * YY / (stat->scale * stat->scale);
     const double unscale = 1.0 / stat->scale;
-    load_roots(roots, B.twB, N1);
-    fill_slot_table(dtab, g.fb);
     cp_async_wait_all();
     __syncthreads();
 
@@ -1047,7 +1098,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             o2[pos] = B.nofit ? mk2(T(0), T(0)) : cscale(from_fft(buf[Lp + sp]), dc);
             o3[pos] = cscale(from_fft(buf[2 * Lp + sp]), dc);
         }
-        return;
+        continue;
     }
     if (stage == 2) {
         fft_dif<1>(buf, 1, Lp, g.fb, roots);
@@ -1092,8 +1143,8 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             V g1 = from_fft(buf[sp]), g2, g3;
             if (stage == 2) {                   // common rows, already deconvolved
                 g1 = cscale(g1, dc);
-                g2 = B.H[(size_t)d * N1 + pos];
-                g3 = B.H[(size_t)g.n + (size_t)d * N1 + pos];
+                g2 = bufV[Lp + sp];
+                g3 = bufV[2 * Lp + sp];
                 dc = T(1);
             } else {
                 g3 = from_fft(buf[2 * Lp + sp]);
@@ -1113,6 +1164,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             }
         }
     }
+    }   // series
 }
 
 // ---------------------------------------------------------------------------
@@ -1260,6 +1312,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     if ((err = allow_max_dynamic_smem((const void *)k_passA<T>)) != cudaSuccess) return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passA_loop<T>)) != cudaSuccess) return err;
     // Pairs of adjacent column blocks write whole 32-byte sectors of each row
     // of H together (cluster store in k_passA).  Measured on the 1e6-point,
     // 1.2e7-frequency FP32 workload (2048 column blocks): pass A 0.82 ms
@@ -1275,9 +1328,21 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         smA = passA_smem_bytes(g, sizeof(Cplx<T>), cs);
     }
     A.cs = cs;
+    // Rows of blocks: every instance gets its own row of blocks while that
+    // keeps the launch within about eight blocks per SM; beyond that the blocks
+    // loop over instances (tables built once per block).
+    int nsm = 0, dev_id = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+    if (nsm <= 0) nsm = 152;
+    const int target = 8 * nsm;
+    A.ny = shared ? S + 2 : 3 * S;
+    int gyA = (target + g.nbins - 1) / g.nbins;
+    if (gyA < 3) gyA = 3;
+    if (gyA > A.ny) gyA = A.ny;
     {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(g.nbins, shared ? S + 2 : 3 * S);
+        cfg.gridDim = dim3(g.nbins, gyA);
         cfg.blockDim = dim3(kThreadsA);
         cfg.dynamicSmemBytes = smA;
         cfg.stream = st;
@@ -1288,7 +1353,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        err = cudaLaunchKernelEx(&cfg, k_passA<T>, A);
+        err = (gyA < A.ny) ? cudaLaunchKernelEx(&cfg, k_passA_loop<T>, A)
+                           : cudaLaunchKernelEx(&cfg, k_passA<T>, A);
         if (err != cudaSuccess) return err;
     }
 
@@ -1312,14 +1378,18 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     if ((err = allow_max_dynamic_smem((const void *)k_passB<T>)) != cudaSuccess) return err;
+    B.nser = S;
+    int gyB = (target + g.N2 - 1) / g.N2;
+    if (gyB < 1) gyB = 1;
+    if (gyB > S) gyB = S;
     if (shared) {
         B.stage = 1;
         k_passB<T><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
         B.stage = 2;
-        k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
+        k_passB<T><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
     } else {
         B.stage = 0;
-        k_passB<T><<<dim3(g.N2, S), kThreadsB, smB, st>>>(B);
+        k_passB<T><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
     }
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
