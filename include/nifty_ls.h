@@ -170,7 +170,10 @@ ls_status ls_execute_sums(ls_plan_t plan, const double *t, const double *y, cons
  * "Performance").  Series whose frequency counts map to the same fine grid
  * run together: one launch per pipeline stage, the series on the grid's second
  * dimension, within the plan's batch workspace (ls_plan_opts); larger groups
- * are cut into several launches.  The plan supplies precision, tolerance,
+ * are cut into several launches.  The launches are spread over four internal
+ * streams (each with a quarter of the workspace) so that small groups overlap
+ * on the device; the plan's stream waits for all of them before the call
+ * returns, so the call is ordered on it like any other.  The plan supplies precision, tolerance,
  * upsampling, device and stream; its nf and max_nd do not limit the batch.
  *   offsets      host int64[nseries + 1]: series s owns points
  *                offsets[s] .. offsets[s+1]-1 of t, y and dy (>= 2 points).

@@ -30,6 +30,11 @@ struct BatchClass {
 };
 
 // Workspace of ls_execute_batch, grown on demand.
+// Batch launches are spread over kBatchLanes streams, each with its own
+// workspace, so the many small launches of a ragged batch (one per grid class)
+// overlap on the device; the plan's stream waits for all of them.
+constexpr int kBatchLanes = 4;
+
 struct BatchWorkspace {
     Workspace ws;
     int64_t cap_points = 0;   // point records
@@ -70,8 +75,11 @@ struct ls_plan_s {
     int64_t t_count;
     // ls_execute_batch
     std::vector<BatchClass> classes;
-    BatchWorkspace bws;
-    int64_t batch_budget = 0;   // bytes for the batch workspace (0: chosen on first use)
+    BatchWorkspace bws[kBatchLanes];
+    cudaStream_t lane_stream[kBatchLanes] = {};
+    cudaEvent_t lane_done[kBatchLanes] = {};
+    cudaEvent_t lane_start = nullptr;
+    int64_t batch_budget = 0;   // bytes for the batch workspaces (0: chosen on first use)
 };
 
 namespace {
@@ -600,13 +608,14 @@ void batch_free(ls_plan_s *p);
 // of H, `bins` histogram entries per array and nred reduction blocks per
 // series (the buffers grow by a quarter beyond the request).
 template <typename T>
-ls_status batch_reserve(ls_plan_s *p, int S, int64_t points, int64_t cells, int64_t bins, int nred)
+ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t cells, int64_t bins,
+                        int nred)
 {
-    BatchWorkspace &b = p->bws;
+    BatchWorkspace &b = p->bws[lane];
     if (S <= b.cap_S && points <= b.cap_points && cells <= b.cap_cells && nred <= b.cap_nred &&
         bins <= b.ws_bins)
         return LS_OK;
-    cudaStreamSynchronize(p->stream);
+    cudaStreamSynchronize(p->lane_stream[lane]);
     for (void *a : b.allocs) cudaFree(a);
     b.allocs.clear();
     b.bytes = 0;
@@ -722,13 +731,64 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
 
 void batch_free(ls_plan_s *p)
 {
+    for (int l = 0; l < kBatchLanes; ++l)
+        if (p->lane_stream[l]) cudaStreamSynchronize(p->lane_stream[l]);
     for (BatchClass &c : p->classes) {
         plan_free(c.sub);
         delete c.sub;
     }
     p->classes.clear();
-    for (void *a : p->bws.allocs) cudaFree(a);
-    p->bws = BatchWorkspace();
+    for (int l = 0; l < kBatchLanes; ++l) {
+        for (void *a : p->bws[l].allocs) cudaFree(a);
+        p->bws[l] = BatchWorkspace();
+        if (p->lane_stream[l]) cudaStreamDestroy(p->lane_stream[l]);
+        if (p->lane_done[l]) cudaEventDestroy(p->lane_done[l]);
+        p->lane_stream[l] = nullptr;
+        p->lane_done[l] = nullptr;
+    }
+    if (p->lane_start) cudaEventDestroy(p->lane_start);
+    p->lane_start = nullptr;
+}
+
+// Start a batch call: the lanes wait for the work already queued on the
+// plan's stream (their streams and events are created on first use).
+ls_status lanes_begin(ls_plan_s *p)
+{
+    cudaError_t e;
+    for (int l = 0; l < kBatchLanes; ++l) {
+        if (!p->lane_stream[l]) {
+            if ((e = cudaStreamCreateWithFlags(&p->lane_stream[l], cudaStreamNonBlocking)))
+                return cuda_status(e);
+            if ((e = cudaEventCreateWithFlags(&p->lane_done[l], cudaEventDisableTiming)))
+                return cuda_status(e);
+        }
+    }
+    if (!p->lane_start && (e = cudaEventCreateWithFlags(&p->lane_start, cudaEventDisableTiming)))
+        return cuda_status(e);
+    if ((e = cudaEventRecord(p->lane_start, p->stream))) return cuda_status(e);
+    for (int l = 0; l < kBatchLanes; ++l)
+        if ((e = cudaStreamWaitEvent(p->lane_stream[l], p->lane_start, 0))) return cuda_status(e);
+    return LS_OK;
+}
+
+// End a batch call (also on error paths): the plan's stream waits for every lane.
+struct LanesJoin {
+    ls_plan_s *p;
+    ~LanesJoin()
+    {
+        for (int l = 0; l < kBatchLanes; ++l) {
+            if (!p->lane_stream[l]) continue;
+            cudaEventRecord(p->lane_done[l], p->lane_stream[l]);
+            cudaStreamWaitEvent(p->stream, p->lane_done[l], 0);
+        }
+    }
+};
+
+// Wait until no lane is using the class tables (before a class is rebuilt).
+void lanes_sync(ls_plan_s *p)
+{
+    for (int l = 0; l < kBatchLanes; ++l)
+        if (p->lane_stream[l]) cudaStreamSynchronize(p->lane_stream[l]);
 }
 
 // Tables-only sub-plan for the grid class of pp covering nf frequencies.
@@ -742,6 +802,7 @@ ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s 
             }
             // the deconvolution table must reach nf/2: rebuild with the larger nf
             cudaStreamSynchronize(p->stream);
+            lanes_sync(p);
             plan_free(c.sub);
             delete c.sub;
             ls_plan_t np;
@@ -761,7 +822,7 @@ ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s 
 }
 
 template <typename T>
-ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
+ls_status batch_launch(ls_plan_s *p, int lane, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
                        int64_t points, int64_t max_nd, const double *t, const double *y,
                        const double *dy, double *power, int shared, int mode)
 {
@@ -772,12 +833,13 @@ ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDes
     const int cap_red = (8 * p->nsm + S - 1) / S;
     if (nred > cap_red) nred = cap_red;
     if (nred < 1) nred = 1;
-    ls_status s = batch_reserve<T>(p, S, points, g.n * grids, 2 * ((int64_t)g.nbins + 1) * S,
-                                   nred);
+    ls_status s = batch_reserve<T>(p, lane, S, points, g.n * grids,
+                                   2 * ((int64_t)g.nbins + 1) * S, nred);
     if (s != LS_OK) return s;
-    BatchWorkspace &b = p->bws;
+    BatchWorkspace &b = p->bws[lane];
+    cudaStream_t st = p->lane_stream[lane];
     cudaError_t e = cudaMemcpyAsync(b.desc, descs.data(), sizeof(SeriesDesc) * descs.size(),
-                                    cudaMemcpyHostToDevice, p->stream);
+                                    cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
     Workspace ws = b.ws;
     ws.twA = sub->ws.twA;
@@ -790,7 +852,7 @@ ls_status batch_launch(ls_plan_s *p, ls_plan_s *sub, const std::vector<SeriesDes
     bt.many = b.desc;
     bt.one = descs[0];
     e = launch_pipeline<T>(g, ws, b.cap_points, bt, max_nd, t, y, dy, power, nullptr, nred,
-                           p->stream, nullptr, shared, mode);
+                           st, nullptr, shared, mode);
     return cuda_status(e);
 }
 
@@ -935,6 +997,11 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
     const size_t cx = p->prec == LS_FP32 ? 8 : 16;
     const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
     constexpr int kMaxBatchS = 16384;
+    const int64_t lane_budget = p->batch_budget / kBatchLanes;
+    ls_status lst = lanes_begin(p);
+    if (lst != LS_OK) return lst;
+    LanesJoin join{p};
+    int lane = 0;
     size_t i = 0;
     while (i < items.size()) {
         // one class
@@ -958,16 +1025,17 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
                 const int64_t nd = offsets[s + 1] - offsets[s];
                 const int64_t bytes = (int64_t)(3 * (size_t)items[k].pp.n * cx * (descs.size() + 1) +
                                                 4 * recb * (size_t)(points + nd));
-                if (!descs.empty() && bytes > p->batch_budget) break;
+                if (!descs.empty() && bytes > lane_budget) break;
                 descs.push_back(make_series(offsets[s], points, nd, out_offsets[s], nf[s], f0[s], df[s]));
                 points += nd;
                 max_nd = std::max(max_nd, nd);
                 ++k;
             }
             st = (p->prec == LS_FP32)
-                     ? batch_launch<float>(p, sub, descs, points, max_nd, t, y, dy, power, 0, norm)
-                     : batch_launch<double>(p, sub, descs, points, max_nd, t, y, dy, power, 0, norm);
+                     ? batch_launch<float>(p, lane, sub, descs, points, max_nd, t, y, dy, power, 0, norm)
+                     : batch_launch<double>(p, lane, sub, descs, points, max_nd, t, y, dy, power, 0, norm);
             if (st != LS_OK) return st;
+            lane = (lane + 1) % kBatchLanes;
         }
         i = j;
     }
@@ -1004,13 +1072,18 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     const size_t cx = p->prec == LS_FP32 ? 8 : 16;
     const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
     constexpr int kMaxBatchS = 16384;
+    const int64_t lane_budget = p->batch_budget / kBatchLanes;
+    ls_status lst = lanes_begin(p);
+    if (lst != LS_OK) return lst;
+    LanesJoin join{p};
+    int lane = 0;
     int64_t s0 = 0;
     while (s0 < nseries) {
         // series per launch within the budget: H holds S + 2 grids
         int64_t S = 1;
         while (S < kMaxBatchS && s0 + S < nseries &&
                (int64_t)((size_t)pp.n * cx * (S + 3) + 4 * recb * (size_t)nd * (S + 1)) <=
-                   p->batch_budget)
+                   lane_budget)
             ++S;
         std::vector<SeriesDesc> descs;
         descs.reserve((size_t)S);
@@ -1020,9 +1093,10 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
             descs.push_back(d);
         }
         st = (p->prec == LS_FP32)
-                 ? batch_launch<float>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm)
-                 : batch_launch<double>(p, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm);
+                 ? batch_launch<float>(p, lane, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm)
+                 : batch_launch<double>(p, lane, sub, descs, S * nd, nd, t, Y, dy, power, 1, norm);
         if (st != LS_OK) return st;
+        lane = (lane + 1) % kBatchLanes;
         s0 += S;
     }
     return LS_OK;
