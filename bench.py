@@ -378,16 +378,49 @@ def run_ours(args):
         yh = torch.from_numpy(s.y).pin_memory().numpy()
         dyh = torch.from_numpy(s.dy).pin_memory().numpy()
         ph = torch.empty(s.nf, dtype=torch.float64).pin_memory().numpy()
-        nsteps = max(3, min(args.steps, 10))
+        nsteps = max(4, min(args.steps, 10))
         plan.execute_host(th, yh, dyh, s.f0, s.df, out=ph)
         barrier(pg)
         t0 = time.perf_counter()
         for _ in range(nsteps):
             plan.execute_host(th, yh, dyh, s.f0, s.df, out=ph)
+        dt_serial = allreduce_max(time.perf_counter() - t0, pg, device)
+        # Two host threads, each with its own plan, CUDA stream and pinned
+        # buffers, calling the same host-buffer entry point: one periodogram's
+        # copies overlap the other's kernels (the way a service would call it).
+        import threading
+        plan2 = nl.Plan(s.nd, s.nf, eps, args.precision, device=local,
+                        upsampling=args.upsampling)
+        bufs = [(th, yh, dyh, ph)]
+        bufs.append(tuple(torch.from_numpy(a.copy()).pin_memory().numpy()
+                          for a in (s.t, s.y, s.dy)) +
+                    (torch.empty(s.nf, dtype=torch.float64).pin_memory().numpy(),))
+        streams = [torch.cuda.Stream(device=device) for _ in range(2)]
+        per = nsteps // 2
+
+        def worker(i):
+            pl = plan if i == 0 else plan2
+            with torch.cuda.stream(streams[i]):
+                for _ in range(per):
+                    a, b_, c_, o = bufs[i]
+                    pl.execute_host(a, b_, c_, s.f0, s.df, out=o)
+
+        worker(1)                      # warm the second plan
+        barrier(pg)
+        t0 = time.perf_counter()
+        th2 = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+        for x in th2:
+            x.start()
+        for x in th2:
+            x.join()
         dt = allreduce_max(time.perf_counter() - t0, pg, device)
-        e2e = {"value": world * nsteps / dt, "unit": UNIT,
+        plan2.close()
+        e2e = {"value": world * 2 * per / dt, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * s.nd, "d2h_bytes_per_step": 8 * s.nf,
-               "steps": nsteps, "host_buffers": "pinned"}
+               "steps": 2 * per, "host_buffers": "pinned", "api": "Plan.execute_host",
+               "concurrency": "2 host threads, a plan and a CUDA stream each",
+               "serial": {"value": world * nsteps / dt_serial, "steps": nsteps,
+                          "concurrency": "1 host thread"}}
 
     # -- the library FFT as a reference for the FFT step: cuFFT (through
     # torch.fft) on the same three fine grids, complex, in the plan's precision,
