@@ -1027,7 +1027,9 @@ template <> struct PowerOut<float> {
     }
 };
 
-template <typename T>
+// kStage is PassBArgs::stage as a template parameter: each launch carries only
+// its own code (fewer instruction-fetch stalls than one kernel for all stages).
+template <typename T, int kStage>
 __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
 {
     using V = Cplx<T>;
@@ -1040,11 +1042,11 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     F *roots = buf + 3 * (size_t)Lp;            // two-level root table of length N1
     int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
-    const int stage = B.stage;
+    constexpr int stage = kStage;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
     V *bufV = reinterpret_cast<V *>(buf);
-    if (stage == 2) {
+    if constexpr (stage == 2) {
         // the common rows of a shared-times batch (deconvolved, slot order) are the
         // same for every series of this row: keep them in rows 1 and 2 for all
         for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
@@ -1083,7 +1085,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     cp_async_wait_all();
     __syncthreads();
 
-    if (stage == 1) {                       // rows 1 and 2 (row 2 alone without a fitted mean)
+    if constexpr (stage == 1) {             // rows 1 and 2 (row 2 alone without a fitted mean)
         if (B.nofit) fft_dif<1>(buf + 2 * (size_t)Lp, 1, Lp, g.fb, roots);
         else if (sizeof(T) == 4) fft_dif<2>(buf + Lp, 2, Lp, g.fb, roots);
         else fft_dif<1>(buf + Lp, 2, Lp, g.fb, roots);
@@ -1100,14 +1102,16 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         }
         continue;
     }
-    if (stage == 2) {
+    if constexpr (stage == 2) {
         fft_dif<1>(buf, 1, Lp, g.fb, roots);
-    } else if (B.nofit) {                   // rows 0 and 2
-        if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
-        else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
     } else {
-        if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
-        else fft_dif<1>(buf, 3, Lp, g.fb, roots);
+        if (B.nofit) {                      // rows 0 and 2
+            if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
+            else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
+        } else {
+            if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
+            else fft_dif<1>(buf, 3, Lp, g.fb, roots);
+        }
     }
 
     const T lam_tol_t = (T)B.lam_tol;
@@ -1141,7 +1145,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             const int sp = pad16(pos);
             T dc = dcv[r];
             V g1 = from_fft(buf[sp]), g2, g3;
-            if (stage == 2) {                   // common rows, already deconvolved
+            if constexpr (stage == 2) {         // common rows, already deconvolved
                 g1 = cscale(g1, dc);
                 g2 = bufV[Lp + sp];
                 g3 = bufV[2 * Lp + sp];
@@ -1377,19 +1381,21 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // arithmetic uses 1e-15).
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
-    if ((err = allow_max_dynamic_smem((const void *)k_passB<T>)) != cudaSuccess) return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 0>)) != cudaSuccess) return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 1>)) != cudaSuccess) return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 2>)) != cudaSuccess) return err;
     B.nser = S;
     int gyB = (target + g.N2 - 1) / g.N2;
     if (gyB < 1) gyB = 1;
     if (gyB > S) gyB = S;
     if (shared) {
         B.stage = 1;
-        k_passB<T><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        k_passB<T, 1><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
         B.stage = 2;
-        k_passB<T><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+        k_passB<T, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
     } else {
         B.stage = 0;
-        k_passB<T><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+        k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
     }
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
