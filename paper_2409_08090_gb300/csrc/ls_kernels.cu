@@ -529,8 +529,9 @@ __global__ void k_kernel_eval_pair(int n, double beta, double *dfl_out, double *
 }
 
 // One instance (a transform of a series) of one column block; the tables are
-// built when build_tables is set (the first instance a block takes).
-template <typename T>
+// built when build_tables is set (the first instance a block takes).  kCluster:
+// the launch pairs column blocks in clusters (A.cs > 1), the store path then.
+template <typename T, bool kCluster>
 __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int y,
                                                const bool build_tables)
 {
@@ -682,7 +683,7 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     else fft_dif<1>(bufF, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
-    if (A.cs > 1) {
+    if constexpr (kCluster) {
         // Cluster store.  A row of H receives only BA columns from one block,
         // so the cs blocks of a cluster (adjacent column blocks) write their
         // rows together: each block takes every cs-th row and writes the
@@ -785,10 +786,10 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
 
 
 // One instance per block (blockIdx.y), the usual launch.
-template <typename T>
+template <typename T, bool kCluster>
 __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 {
-    passA_instance<T>(A, (int)blockIdx.y, true);
+    passA_instance<T, kCluster>(A, (int)blockIdx.y, true);
 }
 
 // Many instances per block: y = blockIdx.y, + gridDim.y, ... of the block's
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 // launch has rows of blocks); the tables depend only on the columns and are
 // built once.  An instance skipped without a fitted mean is skipped by the
 // whole block (and cluster), so the barriers stay uniform.
-template <typename T>
+template <typename T, bool kCluster>
 __global__ void __launch_bounds__(kThreadsA, 2) k_passA_loop(PassAArgs<T> A)
 {
     bool first = true;
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_loop(PassAArgs<T> A)
             if (grid == 1) continue;
         }
         if (!first) __syncthreads();      // the previous instance is done with the buffer
-        passA_instance<T>(A, y, first);
+        passA_instance<T, kCluster>(A, y, first);
         first = false;
     }
 }
@@ -1315,8 +1316,13 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.twA = static_cast<const Cplx<T> *>(ws.twA);
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
-    if ((err = allow_max_dynamic_smem((const void *)k_passA<T>)) != cudaSuccess) return err;
-    if ((err = allow_max_dynamic_smem((const void *)k_passA_loop<T>)) != cudaSuccess) return err;
+    {
+        const void *fns[4] = {(const void *)k_passA<T, false>, (const void *)k_passA<T, true>,
+                              (const void *)k_passA_loop<T, false>,
+                              (const void *)k_passA_loop<T, true>};
+        for (const void *f : fns)
+            if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
+    }
     // Pairs of adjacent column blocks write whole 32-byte sectors of each row
     // of H together (cluster store in k_passA).  Measured on the 1e6-point,
     // 1.2e7-frequency FP32 workload (2048 column blocks): pass A 0.82 ms
@@ -1357,8 +1363,13 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        err = (gyA < A.ny) ? cudaLaunchKernelEx(&cfg, k_passA_loop<T>, A)
-                           : cudaLaunchKernelEx(&cfg, k_passA<T>, A);
+        const bool loop = gyA < A.ny;
+        if (cs > 1)
+            err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true>, A)
+                       : cudaLaunchKernelEx(&cfg, k_passA<T, true>, A);
+        else
+            err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, false>, A)
+                       : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
         if (err != cudaSuccess) return err;
     }
 
