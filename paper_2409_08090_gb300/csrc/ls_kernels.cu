@@ -955,8 +955,8 @@ struct PassBArgs {
     int shared;            // see PassAArgs
     // 0: the three rows of each series.  Shared times: 1 transforms the two
     // common rows (w^ at f and 2f, H slots 0 and 1) once and writes them back
-    // deconvolved, in slot order; 2 then transforms each series' own row and
-    // reads the common values from there.
+    // deconvolved, in slot order; 2 (k_passB_series) then transforms the
+    // series' own rows and reads the common values from there.
     int stage;
     const Cplx<T> *twB;    // two-level root table, length N1
     Cplx<T> *H;
@@ -968,6 +968,7 @@ struct PassBArgs {
     int nofit;             // 1: no offset in the model: C = S = 0, grid s2 absent
     int norm;              // 0 standard, 1 model, 2 log, 3 psd
     int nser;              // series of the launch (stages 0 and 2)
+    int group;             // series rows per block of k_passB_series
 };
 
 // Normalisation of the standard power P = p / YY (p the explained weighted
@@ -1046,16 +1047,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     constexpr int stage = kStage;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
-    V *bufV = reinterpret_cast<V *>(buf);
-    if constexpr (stage == 2) {
-        // the common rows of a shared-times batch (deconvolved, slot order) are the
-        // same for every series of this row: keep them in rows 1 and 2 for all
-        for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
-            const int sp = pad16(pos);
-            bufV[Lp + sp] = B.H[(size_t)d * N1 + pos];
-            bufV[2 * Lp + sp] = B.H[(size_t)g.n + (size_t)d * N1 + pos];
-        }
-    }
+    static_assert(stage == 0 || stage == 1, "stage 2 runs in k_passB_series");
     const int nser = stage == 1 ? 1 : B.nser;
 
     // The block takes the series s = blockIdx.y, + gridDim.y, ... of its row d
@@ -1072,7 +1064,7 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
     // element of the three rows is in flight at once, without registers.
     for (int gi = 0; gi < 3; ++gi) {
         if (B.nofit && gi == 1) continue;
-        if ((stage == 1 && gi == 0) || (stage == 2 && gi != 0)) continue;
+        if (stage == 1 && gi == 0) continue;
         const size_t slot = B.shared ? (gi == 0 ? 2 + ser : gi - 1) : 3 * ser + gi;
         const V *src = B.H + slot * (size_t)g.n + (size_t)d * N1;
         V *dst = reinterpret_cast<V *>(buf + (size_t)gi * Lp);   // H holds F bits (pass A)
@@ -1103,16 +1095,12 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         }
         continue;
     }
-    if constexpr (stage == 2) {
-        fft_dif<1>(buf, 1, Lp, g.fb, roots);
+    if (B.nofit) {                          // rows 0 and 2
+        if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
+        else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
     } else {
-        if (B.nofit) {                      // rows 0 and 2
-            if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
-            else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
-        } else {
-            if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
-            else fft_dif<1>(buf, 3, Lp, g.fb, roots);
-        }
+        if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
+        else fft_dif<1>(buf, 3, Lp, g.fb, roots);
     }
 
     const T lam_tol_t = (T)B.lam_tol;
@@ -1144,17 +1132,9 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
             const int64_t k = d + (int64_t)N2 * c;
             const int64_t kp = (c < c1) ? k : k - n;
             const int sp = pad16(pos);
-            T dc = dcv[r];
-            V g1 = from_fft(buf[sp]), g2, g3;
-            if constexpr (stage == 2) {         // common rows, already deconvolved
-                g1 = cscale(g1, dc);
-                g2 = bufV[Lp + sp];
-                g3 = bufV[2 * Lp + sp];
-                dc = T(1);
-            } else {
-                g3 = from_fft(buf[2 * Lp + sp]);
-                g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[Lp + sp]);
-            }
+            const T dc = dcv[r];
+            const V g1 = from_fft(buf[sp]), g3 = from_fft(buf[2 * Lp + sp]);
+            const V g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[Lp + sp]);
             const int64_t out = kp + K0;
             if (power) {
                 const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, lam_tol_t);
@@ -1170,6 +1150,90 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
         }
     }
     }   // series
+}
+
+// ---------------------------------------------------------------------------
+// Pass B for the series of a shared-times batch (after stage 1 wrote the common
+// rows back deconvolved): a block takes row d of `group` series at a time, their
+// rows side by side in shared memory next to the two common rows, so the row
+// copies, the transforms' barriers, the common values and the deconvolution
+// factor of each mode are shared by the group.  All series have the same grid.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreadsB, 2) k_passB_series(PassBArgs<T> B)
+{
+    using V = Cplx<T>;
+    using F = typename FftOf<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geometry &g = B.g;
+    const int N1 = g.N1, N2 = g.N2;
+    const int Lp = padded_len(N1);
+    const int G = B.group;
+    F *buf = reinterpret_cast<F *>(smem_raw);   // rows 0, 1: common values; 2 .. 1+G: series
+    V *bufV = reinterpret_cast<V *>(buf);
+    F *roots = buf + (size_t)(2 + G) * Lp;
+    double *sc = reinterpret_cast<double *>(roots + 64 + ((N1 + 63) >> 6));   // 4 per series
+    int64_t *soff = reinterpret_cast<int64_t *>(sc + 4 * G);                   // output offsets
+    int *dtab = reinterpret_cast<int *>(soff + G);
+    const int d = blockIdx.x;
+    load_roots(roots, B.twB, N1);
+    fill_slot_table(dtab, g.fb);
+    for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
+        const int sp = pad16(pos);
+        bufV[sp] = B.H[(size_t)d * N1 + pos];
+        bufV[Lp + sp] = B.H[(size_t)g.n + (size_t)d * N1 + pos];
+    }
+    const SeriesDesc sd0 = series_of(B.bt, 0);
+    const int64_t nf = sd0.nf, K0 = sd0.ph.K0;
+    const int64_t n = g.n;
+    const int c1 = (nf - K0 > d) ? (int)((nf - K0 - d + N2 - 1) / N2) : 0;
+    const int c2 = (int)((n - K0 - d + N2 - 1) / N2);
+    const T lam_tol_t = (T)B.lam_tol;
+    const T *dcrow = B.deconv + (size_t)d * N1;
+
+    for (int s0 = blockIdx.y * G; s0 < B.nser; s0 += gridDim.y * G) {
+        const int gact = min(G, B.nser - s0);
+        __syncthreads();                  // the previous group is done with its rows
+        for (int r = 0; r < gact; ++r) {
+            const V *src = B.H + (size_t)(2 + s0 + r) * (size_t)n + (size_t)d * N1;
+            V *dst = bufV + (size_t)(2 + r) * Lp;
+            for (int i = threadIdx.x; i < N1; i += blockDim.x) cp_async_elem(dst + pad16(i), src + i);
+        }
+        cp_async_commit();
+        if ((int)threadIdx.x < gact) {
+            const int r = threadIdx.x;
+            const Stats *stat = B.st + s0 + r;
+            const double YY = stat->YY;
+            sc[4 * r] = YY;
+            sc[4 * r + 1] = 0.5 * stat->W * YY / (stat->scale * stat->scale);
+            const float hi = (float)YY;
+            sc[4 * r + 2] = hi;
+            sc[4 * r + 3] = (float)(YY - (double)hi);
+            soff[r] = series_of(B.bt, s0 + r).out_off;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (sizeof(T) == 4) fft_dif<2>(buf + 2 * (size_t)Lp, gact, Lp, g.fb, roots);
+        else fft_dif<1>(buf + 2 * (size_t)Lp, gact, Lp, g.fb, roots);
+
+        for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
+            const int c = slot_freq_tab(pos, dtab, g.fb);
+            if (c >= c1 && c < c2) continue;            // mode not requested
+            const int64_t k = d + (int64_t)N2 * c;
+            const int64_t out = ((c < c1) ? k : k - n) + K0;
+            const int sp = pad16(pos);
+            const T dc = __ldg(dcrow + pos);
+            const V g2 = bufV[sp], g3 = bufV[Lp + sp];
+            for (int r = 0; r < gact; ++r) {
+                const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
+                ff YYf;
+                YYf.hi = (float)sc[4 * r + 2];
+                YYf.lo = (float)sc[4 * r + 3];
+                const double P = PowerOut<T>::eval(g1, g2, g3, T(1), sc[4 * r], YYf, lam_tol_t);
+                B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1222,6 +1286,23 @@ size_t passA_smem_bytes(const Geometry &g, size_t cx, int cs)
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
 {
     return cx * (3 * (size_t)padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64) +
+           sizeof(int) * (size_t)(g.N1 / g.fb.Rlast);
+}
+
+// Series rows per block of k_passB_series: as many as fit (with the two common
+// rows) in the shared memory two blocks per SM can have, at most 8.
+static int passB_group(const Geometry &g, size_t cx)
+{
+    const size_t row = cx * (size_t)padded_len(g.N1);
+    const size_t budget = 100 * 1024;
+    int G = (int)(budget / row) - 2;
+    return G < 1 ? 1 : (G > 8 ? 8 : G);
+}
+
+static size_t passB_series_smem_bytes(const Geometry &g, size_t cx, int G)
+{
+    return cx * ((size_t)(2 + G) * padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64) +
+           (4 * sizeof(double) + sizeof(int64_t)) * (size_t)G +
            sizeof(int) * (size_t)(g.N1 / g.fb.Rlast);
 }
 
@@ -1394,7 +1475,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 0>)) != cudaSuccess) return err;
     if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 1>)) != cudaSuccess) return err;
-    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 2>)) != cudaSuccess) return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passB_series<T>)) != cudaSuccess) return err;
     B.nser = S;
     int gyB = (target + g.N2 - 1) / g.N2;
     if (gyB < 1) gyB = 1;
@@ -1403,7 +1484,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         B.stage = 1;
         k_passB<T, 1><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
         B.stage = 2;
-        k_passB<T, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+        B.group = passB_group(g, sizeof(Cplx<T>));
+        int gy2 = (S + B.group - 1) / B.group;
+        if (gy2 > gyB) gy2 = gyB;
+        k_passB_series<T><<<dim3(g.N2, gy2), kThreadsB,
+                            passB_series_smem_bytes(g, sizeof(Cplx<T>), B.group), st>>>(B);
     } else {
         B.stage = 0;
         k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
