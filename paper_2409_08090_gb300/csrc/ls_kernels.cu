@@ -465,6 +465,7 @@ struct PassAArgs {
     Cplx<T> *H;
     int cs;                // blocks per thread-block cluster along the columns (1: none)
     int ny;                // instances (transforms of series) along the grid's y
+    int group;             // series per block iteration of k_passA_series
 };
 
 template <typename T>
@@ -784,6 +785,176 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     }
 }
 
+
+// Pass A for the series grids (w^ (y - ybar) at f) of a shared-times batch:
+// a block takes column block blk of `group` series at a time, their columns
+// side by side in shared memory (series r owns columns r BA .. r BA + BA - 1),
+// so the transforms' barriers, the tables and the stores are shared by the
+// group.  No cluster pairs (used for small grids only).
+constexpr int kMaxGroup = 8;   // series per block iteration of the grouped kernels
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
+{
+    __shared__ int grp[4 * kMaxGroup + 1];
+    __shared__ int64_t grp_off[kMaxGroup];
+    using V = Cplx<T>;
+    using F = typename FftOf<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geometry &g = A.g;
+    const int N1 = g.N1, N2 = g.N2, BA = g.BA;
+    const int Lp = padded_len(N2);
+    const int nhi = (N2 + 63) >> 6;
+    const int G = A.group;
+    V *buf = reinterpret_cast<V *>(smem_raw);
+    F *bufF = reinterpret_cast<F *>(buf);
+    F *alo = bufF + (size_t)G * BA * Lp;
+    F *ahi = alo + BA * 64;
+    F *roots = ahi + BA * nhi;
+    int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);
+    const int blk = blockIdx.x;
+    const int a0 = blk * BA;
+    load_roots(roots, A.twA, N2);
+    fill_slot_table(dtab, g.fa);
+    for (int i = threadIdx.x; i < BA * 64; i += blockDim.x)
+        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a0 + (i >> 6)) * (i & 63)));
+    for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
+        const int col = i / nhi;
+        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * (i - col * nhi)) % g.n));
+    }
+    const T halfw = T(0.5) * T(g.w);
+    const T zscale = T(2) / T(g.w);
+    const T beta = T(g.beta);
+    const dfl beta_dfl(g.beta);
+    const bool dfl_ok = g.eps >= 1e-11;
+    const int nbb = (g.w - 1 + BA - 1) >> g.logBA;
+    const int nser = A.ny - 2;
+
+    for (int s0 = blockIdx.y * G; s0 < nser; s0 += gridDim.y * G) {
+        const int gact = min(G, nser - s0);
+        __syncthreads();                  // tables ready / the previous group is stored
+        for (int i = threadIdx.x; i < gact * BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
+        __syncthreads();
+        // record ranges of the group's series (rows of grp: first range start,
+        // its length, second range start, exclusive prefix of the totals)
+        if ((int)threadIdx.x < gact) {
+            const int r = threadIdx.x;
+            const int *bs = A.binstart + (size_t)(s0 + r) * 2 * (g.nbins + 1);
+            int r0s, r0e, r1s = 0, r1e = 0;
+            if (nbb + 1 >= g.nbins) {
+                r0s = bs[0];
+                r0e = bs[g.nbins];
+            } else if (blk - nbb >= 0) {
+                r0s = bs[blk - nbb];
+                r0e = bs[blk + 1];
+            } else {
+                r0s = bs[blk - nbb + g.nbins];
+                r0e = bs[g.nbins];
+                r1s = bs[0];
+                r1e = bs[blk + 1];
+            }
+            grp[4 * r] = r0s;
+            grp[4 * r + 1] = r0e - r0s;
+            grp[4 * r + 2] = r1s;
+            grp[4 * r + 3] = (r0e - r0s) + (r1e - r1s);
+            grp_off[r] = series_of(A.bt, s0 + r).rec_off;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {           // prefix of the totals
+            int acc = 0;
+            for (int r = 0; r < gact; ++r) {
+                const int tot = grp[4 * r + 3];
+                grp[4 * r + 3] = acc;
+                acc += tot;
+            }
+            grp[4 * kMaxGroup] = acc;
+        }
+        __syncthreads();
+        const int all = grp[4 * kMaxGroup];
+        // kPre records per thread in flight, over the group's records in turn
+        constexpr int kPre = 4;
+        for (int e0 = threadIdx.x; e0 < all; e0 += kPre * blockDim.x) {
+            uint32_t abv[kPre];
+            T rv[kPre];
+            V sv[kPre];
+            int rr[kPre];
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int e = e0 + q * (int)blockDim.x;
+                rr[q] = -1;
+                if (e < all) {
+                    int r = 0;
+                    while (r + 1 < gact && grp[4 * (r + 1) + 3] <= e) ++r;
+                    const int el = e - grp[4 * r + 3];
+                    const int j = (el < grp[4 * r + 1]) ? grp[4 * r] + el
+                                                        : grp[4 * r + 2] + el - grp[4 * r + 1];
+                    const PointSet<T> P = shifted(A.px, grp_off[r]);
+                    abv[q] = __ldg(P.ab + j);
+                    rv[q] = __ldg(P.roff + j);
+                    sv[q] = __ldg(P.s[0] + j);
+                    rr[q] = r;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                if (rr[q] < 0) break;
+                const uint32_t ab = abv[q];
+                const int aj = (int)(ab & 0xFFFFu);
+                const int bj = (int)(ab >> 16);
+                int o = aj - a0;
+                if (o < 0) o += N1;
+                int i0, cs;
+                if (o < BA) { i0 = 0; cs = o; }
+                else { i0 = N1 - o; cs = 0; }
+                const int cnt = min(BA - cs, g.w - i0);
+                V *cols = buf + (size_t)rr[q] * BA * Lp;
+                for (int u = 0; u < cnt; ++u) {
+                    const int i = i0 + u;
+                    int b = bj + ((aj + i >= N1) ? 1 : 0);
+                    if (b >= N2) b -= N2;
+                    const T z = (rv[q] - halfw + T(i)) * zscale;
+                    T v;
+                    if constexpr (sizeof(T) == 8) v = dfl_ok ? es_kernel_dfl(z, beta_dfl) : es_kernel(z, beta);
+                    else v = es_kernel(z, beta);
+                    V *dst = cols + (size_t)(cs + u) * Lp + pad16(b);
+                    atomicAdd(&dst->x, sv[q].x * v);
+                    atomicAdd(&dst->y, sv[q].y * v);
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 8) {
+            for (int i = threadIdx.x; i < gact * BA * Lp; i += blockDim.x) bufF[i] = to_fft(buf[i]);
+            __syncthreads();
+        }
+        if (sizeof(T) == 4) fft_dif<2>(bufF, gact * BA, Lp, g.fa, roots);
+        else fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
+        // twiddle exp(2 pi i a d / n) and store H[2 + s][d][a], slot order; the
+        // BA columns of a row go out as 16-byte units
+        for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
+            const int d = slot_freq_tab(pos, dtab, g.fa);
+            const int sp = pad16(pos);
+            for (int r = 0; r < gact; ++r) {
+                F *dst = reinterpret_cast<F *>(A.H + (size_t)(2 + s0 + r) * (size_t)g.n +
+                                               (size_t)d * N1 + a0);
+                if constexpr (sizeof(F) == 8) {
+                    for (int c0 = 0; c0 < BA; c0 += 2) {       // BA >= 2 (group launches)
+                        const F v0 = cmul(bufF[(size_t)(r * BA + c0) * Lp + sp],
+                                          cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]));
+                        const F v1 = cmul(bufF[(size_t)(r * BA + c0 + 1) * Lp + sp],
+                                          cmul(alo[(c0 + 1) * 64 + (d & 63)],
+                                               ahi[(c0 + 1) * nhi + (d >> 6)]));
+                        reinterpret_cast<float4 *>(dst)[c0 >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
+                    }
+                } else {
+                    for (int col = 0; col < BA; ++col)
+                        dst[col] = cmul(bufF[(size_t)(r * BA + col) * Lp + sp],
+                                        cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]));
+                }
+            }
+        }
+    }
+}
 
 // One instance per block (blockIdx.y), the usual launch.
 template <typename T, bool kCluster>
@@ -1428,6 +1599,17 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     if (nsm <= 0) nsm = 152;
     const int target = 8 * nsm;
     A.ny = shared ? S + 2 : 3 * S;
+    // Shared times with small grids: the series grids go through
+    // k_passA_series, `group` series per block iteration (the common grids
+    // through the usual kernel first).
+    const size_t cxA = sizeof(Cplx<T>);
+    const size_t colA = (size_t)g.BA * padded_len(g.N2) * cxA;
+    const size_t tabA = cxA * ((size_t)g.BA * (64 + (g.N2 + 63) / 64) + 64 + (g.N2 + 63) / 64) +
+                        sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
+    int groupA = (int)((100 * 1024 - tabA) / colA);
+    groupA = groupA > 8 ? 8 : groupA;
+    const bool grouped = shared && cs == 1 && g.BA >= 2 && groupA >= 2 && S >= 2;
+    if (grouped) A.ny = 2;
     int gyA = (target + g.nbins - 1) / g.nbins;
     if (gyA < 3) gyA = 3;
     if (gyA > A.ny) gyA = A.ny;
@@ -1452,6 +1634,17 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, false>, A)
                        : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
         if (err != cudaSuccess) return err;
+    }
+    if (grouped) {
+        A.ny = S + 2;
+        A.group = groupA;
+        const size_t smS = (size_t)groupA * colA + tabA;
+        if ((err = allow_max_dynamic_smem((const void *)k_passA_series<T>)) != cudaSuccess)
+            return err;
+        int gyS = (S + groupA - 1) / groupA;
+        const int gcap = (target + g.nbins - 1) / g.nbins;
+        if (gyS > gcap) gyS = gcap;
+        k_passA_series<T><<<dim3(g.nbins, gyS), kThreadsA, smS, st>>>(A);
     }
 
     if (ev) cudaEventRecord(ev[3], st);
