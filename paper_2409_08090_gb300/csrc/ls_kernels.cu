@@ -465,7 +465,7 @@ struct PassAArgs {
     Cplx<T> *H;
     int cs;                // blocks per thread-block cluster along the columns (1: none)
     int ny;                // instances (transforms of series) along the grid's y
-    int group;             // series per block iteration of k_passA_series
+    int group;             // instances per block iteration of k_passA_group
 };
 
 template <typename T>
@@ -786,18 +786,23 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
 }
 
 
-// Pass A for the series grids (w^ (y - ybar) at f) of a shared-times batch:
-// a block takes column block blk of `group` series at a time, their columns
-// side by side in shared memory (series r owns columns r BA .. r BA + BA - 1),
-// so the transforms' barriers, the tables and the stores are shared by the
-// group.  No cluster pairs (used for small grids only).
-constexpr int kMaxGroup = 8;   // series per block iteration of the grouped kernels
+// Pass A for many small grids of one batch launch: a block takes column block
+// blk of `group` instances at a time (instances: the transforms of the series;
+// in a shared-times batch only the series grids, the common grids go through
+// the usual kernel first), their columns side by side in shared memory
+// (member r owns columns r BA .. r BA + BA - 1), so the tables, the
+// transforms' barriers and the stores are shared by the group.  No cluster
+// pairs (small grids only).
+constexpr int kMaxGroup = 8;   // instances per block iteration of the grouped kernels
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
+__global__ void __launch_bounds__(kThreadsA, 2) k_passA_group(PassAArgs<T> A)
 {
     __shared__ int grp[4 * kMaxGroup + 1];
-    __shared__ int64_t grp_off[kMaxGroup];
+    __shared__ const uint32_t *g_ab[kMaxGroup];
+    __shared__ const T *g_roff[kMaxGroup];
+    __shared__ const Cplx<T> *g_str[kMaxGroup];
+    __shared__ int g_slot[kMaxGroup];
     using V = Cplx<T>;
     using F = typename FftOf<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -828,10 +833,14 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
     const dfl beta_dfl(g.beta);
     const bool dfl_ok = g.eps >= 1e-11;
     const int nbb = (g.w - 1 + BA - 1) >> g.logBA;
-    const int nser = A.ny - 2;
+    // instances taken here: shared times -> the series grids (H slot 2 + s);
+    // otherwise every transform of every series, without the w^ grid when the
+    // model has no offset
+    const int S = A.shared ? A.ny - 2 : A.ny / 3;
+    const int ni = A.shared ? S : (A.nofit ? 2 * S : 3 * S);
 
-    for (int s0 = blockIdx.y * G; s0 < nser; s0 += gridDim.y * G) {
-        const int gact = min(G, nser - s0);
+    for (int s0 = blockIdx.y * G; s0 < ni; s0 += gridDim.y * G) {
+        const int gact = min(G, ni - s0);
         __syncthreads();                  // tables ready / the previous group is stored
         for (int i = threadIdx.x; i < gact * BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
         __syncthreads();
@@ -839,7 +848,28 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
         // its length, second range start, exclusive prefix of the totals)
         if ((int)threadIdx.x < gact) {
             const int r = threadIdx.x;
-            const int *bs = A.binstart + (size_t)(s0 + r) * 2 * (g.nbins + 1);
+            const int idx = s0 + r;
+            int ser, grid, slot;
+            if (A.shared) {
+                ser = idx;
+                grid = 0;
+                slot = 2 + idx;
+            } else if (A.nofit) {
+                ser = idx >> 1;
+                grid = (idx & 1) ? 2 : 0;
+                slot = 3 * ser + grid;
+            } else {
+                ser = idx / 3;
+                grid = idx - 3 * ser;
+                slot = idx;
+            }
+            const PointSet<T> P = shifted(grid < 2 ? A.px : A.p2, series_of(A.bt, ser).rec_off);
+            g_ab[r] = P.ab;
+            g_roff[r] = P.roff;
+            g_str[r] = grid == 1 ? P.s[1] : P.s[0];
+            g_slot[r] = slot;
+            const int *bs = A.binstart + (size_t)ser * 2 * (g.nbins + 1) +
+                            (grid < 2 ? 0 : (g.nbins + 1));
             int r0s, r0e, r1s = 0, r1e = 0;
             if (nbb + 1 >= g.nbins) {
                 r0s = bs[0];
@@ -857,7 +887,6 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
             grp[4 * r + 1] = r0e - r0s;
             grp[4 * r + 2] = r1s;
             grp[4 * r + 3] = (r0e - r0s) + (r1e - r1s);
-            grp_off[r] = series_of(A.bt, s0 + r).rec_off;
         }
         __syncthreads();
         if (threadIdx.x == 0) {           // prefix of the totals
@@ -888,10 +917,9 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
                     const int el = e - grp[4 * r + 3];
                     const int j = (el < grp[4 * r + 1]) ? grp[4 * r] + el
                                                         : grp[4 * r + 2] + el - grp[4 * r + 1];
-                    const PointSet<T> P = shifted(A.px, grp_off[r]);
-                    abv[q] = __ldg(P.ab + j);
-                    rv[q] = __ldg(P.roff + j);
-                    sv[q] = __ldg(P.s[0] + j);
+                    abv[q] = __ldg(g_ab[r] + j);
+                    rv[q] = __ldg(g_roff[r] + j);
+                    sv[q] = __ldg(g_str[r] + j);
                     rr[q] = r;
                 }
             }
@@ -935,7 +963,7 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA_series(PassAArgs<T> A)
             const int d = slot_freq_tab(pos, dtab, g.fa);
             const int sp = pad16(pos);
             for (int r = 0; r < gact; ++r) {
-                F *dst = reinterpret_cast<F *>(A.H + (size_t)(2 + s0 + r) * (size_t)g.n +
+                F *dst = reinterpret_cast<F *>(A.H + (size_t)g_slot[r] * (size_t)g.n +
                                                (size_t)d * N1 + a0);
                 if constexpr (sizeof(F) == 8) {
                     for (int c0 = 0; c0 < BA; c0 += 2) {       // BA >= 2 (group launches)
@@ -1139,7 +1167,7 @@ struct PassBArgs {
     int nofit;             // 1: no offset in the model: C = S = 0, grid s2 absent
     int norm;              // 0 standard, 1 model, 2 log, 3 psd
     int nser;              // series of the launch (stages 0 and 2)
-    int group;             // series rows per block of k_passB_series
+    int group;             // series per block of k_passB_series / k_passB_group
 };
 
 // Normalisation of the standard power P = p / YY (p the explained weighted
@@ -1408,6 +1436,94 @@ __global__ void __launch_bounds__(kThreadsB, 2) k_passB_series(PassBArgs<T> B)
 }
 
 // ---------------------------------------------------------------------------
+// Pass B for many small grids of independent series (stage 0 of a batch whose
+// series all have this grid): a block takes row d of `group` series at a time,
+// their rows (s1, s2, s3 each; s1, s3 without a fitted mean) side by side in
+// shared memory, so the tables, the copies' wait, the transforms' barriers and
+// the deconvolution factors are shared by the group.  The series share the
+// grid but not N_f or the first mode K0.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreadsB, 2) k_passB_group(PassBArgs<T> B)
+{
+    using V = Cplx<T>;
+    using F = typename FftOf<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geometry &g = B.g;
+    const int N1 = g.N1, N2 = g.N2;
+    const int logN1 = 31 - __clz(N1);
+    const int Lp = padded_len(N1);
+    const int G = B.group;
+    const int nr = B.nofit ? 2 : 3;              // rows per series; s3 is the last
+    F *buf = reinterpret_cast<F *>(smem_raw);    // series r: rows nr r .. nr r + nr - 1
+    V *bufV = reinterpret_cast<V *>(buf);
+    F *roots = buf + (size_t)nr * G * Lp;
+    double *sc = reinterpret_cast<double *>(roots + 64 + ((N1 + 63) >> 6));   // 4 per series
+    int64_t *obase = reinterpret_cast<int64_t *>(sc + 4 * G);   // out_off + K0 per series
+    int *cr = reinterpret_cast<int *>(obase + G);               // c1, c2 per series
+    int *dtab = cr + 2 * G;
+    const int d = blockIdx.x;
+    const int64_t n = g.n;
+    load_roots(roots, B.twB, N1);
+    fill_slot_table(dtab, g.fb);
+    const T lam_tol_t = (T)B.lam_tol;
+    const T *dcrow = B.deconv + (size_t)d * N1;
+
+    for (int s0 = blockIdx.y * G; s0 < B.nser; s0 += gridDim.y * G) {
+        const int gact = min(G, B.nser - s0);
+        __syncthreads();                  // tables ready / the previous group is done
+        // row d of every grid of the group, flattened over (row, element)
+        for (int e = threadIdx.x; e < gact * nr * N1; e += blockDim.x) {
+            const int row = e >> logN1, i = e & (N1 - 1);
+            const int r = row / nr, j = row - nr * r;
+            const int gi = (B.nofit && j == 1) ? 2 : j;
+            const V *src = B.H + (size_t)(3 * (s0 + r) + gi) * (size_t)n + (size_t)d * N1;
+            cp_async_elem(bufV + (size_t)row * Lp + pad16(i), src + i);
+        }
+        cp_async_commit();
+        if ((int)threadIdx.x < gact) {
+            const int r = threadIdx.x;
+            const SeriesDesc sd = series_of(B.bt, s0 + r);
+            const Stats *stat = B.st + s0 + r;
+            const double YY = stat->YY;
+            sc[4 * r] = YY;
+            sc[4 * r + 1] = 0.5 * stat->W * YY / (stat->scale * stat->scale);
+            const float hi = (float)YY;
+            sc[4 * r + 2] = hi;
+            sc[4 * r + 3] = (float)(YY - (double)hi);
+            const int64_t nf = sd.nf, K0 = sd.ph.K0;
+            cr[2 * r] = (nf - K0 > d) ? (int)((nf - K0 - d + N2 - 1) / N2) : 0;
+            cr[2 * r + 1] = (int)((n - K0 - d + N2 - 1) / N2);
+            obase[r] = sd.out_off + K0;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (sizeof(T) == 4) fft_dif<2>(buf, gact * nr, Lp, g.fb, roots);
+        else fft_dif<1>(buf, gact * nr, Lp, g.fb, roots);
+
+        for (int e = threadIdx.x; e < gact * N1; e += blockDim.x) {
+            const int r = e >> logN1, pos = e & (N1 - 1);
+            const int c = slot_freq_tab(pos, dtab, g.fb);
+            const int c1 = cr[2 * r], c2 = cr[2 * r + 1];
+            if (c >= c1 && c < c2) continue;            // mode not requested
+            const int64_t k = d + (int64_t)N2 * c;
+            const int64_t kp = (c < c1) ? k : k - n;
+            const int sp = pad16(pos);
+            const T dc = __ldg(dcrow + pos);
+            const size_t base = (size_t)nr * r * Lp + sp;
+            const V g1 = from_fft(buf[base]);
+            const V g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[base + Lp]);
+            const V g3 = from_fft(buf[base + (size_t)(nr - 1) * Lp]);
+            ff YYf;
+            YYf.hi = (float)sc[4 * r + 2];
+            YYf.lo = (float)sc[4 * r + 3];
+            const double P = PowerOut<T>::eval(g1, g2, g3, dc, sc[4 * r], YYf, lam_tol_t);
+            B.power[obase[r] + kp] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Deconvolution table: 1/phi_hat(k), phi_hat(k) = w int_0^1 psi(z) cos(pi k w z / n) dz
 // by the plan's quadrature rule (nodes z, weights already times psi(z)).
 // ---------------------------------------------------------------------------
@@ -1468,6 +1584,22 @@ static int passB_group(const Geometry &g, size_t cx)
     const size_t budget = 100 * 1024;
     int G = (int)(budget / row) - 2;
     return G < 1 ? 1 : (G > 8 ? 8 : G);
+}
+
+// Series per block of k_passB_group: as many as fit (nr rows each) in the
+// shared memory two blocks per SM can have, at most 8.
+static int passB_group_indep(const Geometry &g, size_t cx, int nr)
+{
+    const size_t row = cx * (size_t)padded_len(g.N1);
+    const int G = (int)(100 * 1024 / (row * nr));
+    return G > 8 ? 8 : G;
+}
+
+static size_t passB_group_smem_bytes(const Geometry &g, size_t cx, int G, int nr)
+{
+    return cx * ((size_t)nr * G * padded_len(g.N1) + 64 + (size_t)(g.N1 + 63) / 64) +
+           (4 * sizeof(double) + sizeof(int64_t) + 2 * sizeof(int)) * (size_t)G +
+           sizeof(int) * (size_t)(g.N1 / g.fb.Rlast);
 }
 
 static size_t passB_series_smem_bytes(const Geometry &g, size_t cx, int G)
@@ -1599,21 +1731,22 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     if (nsm <= 0) nsm = 152;
     const int target = 8 * nsm;
     A.ny = shared ? S + 2 : 3 * S;
-    // Shared times with small grids: the series grids go through
-    // k_passA_series, `group` series per block iteration (the common grids
-    // through the usual kernel first).
+    // Small grids: the instances go through k_passA_group, `group` per block
+    // iteration (in a shared-times batch only the series grids; the common
+    // grids through the usual kernel first).
     const size_t cxA = sizeof(Cplx<T>);
     const size_t colA = (size_t)g.BA * padded_len(g.N2) * cxA;
     const size_t tabA = cxA * ((size_t)g.BA * (64 + (g.N2 + 63) / 64) + 64 + (g.N2 + 63) / 64) +
                         sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
     int groupA = (int)((100 * 1024 - tabA) / colA);
     groupA = groupA > 8 ? 8 : groupA;
-    const bool grouped = shared && cs == 1 && g.BA >= 2 && groupA >= 2 && S >= 2;
-    if (grouped) A.ny = 2;
+    const int ninst = shared ? S : (nofit ? 2 * S : 3 * S);
+    const bool grouped = cs == 1 && g.BA >= 2 && groupA >= 2 && ninst >= 2;
+    if (grouped) A.ny = shared ? 2 : 0;
     int gyA = (target + g.nbins - 1) / g.nbins;
     if (gyA < 3) gyA = 3;
     if (gyA > A.ny) gyA = A.ny;
-    {
+    if (A.ny > 0) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g.nbins, gyA);
         cfg.blockDim = dim3(kThreadsA);
@@ -1636,15 +1769,15 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         if (err != cudaSuccess) return err;
     }
     if (grouped) {
-        A.ny = S + 2;
+        A.ny = shared ? S + 2 : 3 * S;
         A.group = groupA;
         const size_t smS = (size_t)groupA * colA + tabA;
-        if ((err = allow_max_dynamic_smem((const void *)k_passA_series<T>)) != cudaSuccess)
+        if ((err = allow_max_dynamic_smem((const void *)k_passA_group<T>)) != cudaSuccess)
             return err;
-        int gyS = (S + groupA - 1) / groupA;
+        int gyS = (ninst + groupA - 1) / groupA;
         const int gcap = (target + g.nbins - 1) / g.nbins;
         if (gyS > gcap) gyS = gcap;
-        k_passA_series<T><<<dim3(g.nbins, gyS), kThreadsA, smS, st>>>(A);
+        k_passA_group<T><<<dim3(g.nbins, gyS), kThreadsA, smS, st>>>(A);
     }
 
     if (ev) cudaEventRecord(ev[3], st);
@@ -1684,7 +1817,20 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
                             passB_series_smem_bytes(g, sizeof(Cplx<T>), B.group), st>>>(B);
     } else {
         B.stage = 0;
-        k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+        // Small rows: `group` series per block iteration (power output only).
+        const int nr = nofit ? 2 : 3;
+        const int GB = passB_group_indep(g, sizeof(Cplx<T>), nr);
+        if (GB >= 2 && S >= 2 && power && !sums) {
+            if ((err = allow_max_dynamic_smem((const void *)k_passB_group<T>)) != cudaSuccess)
+                return err;
+            B.group = GB;
+            int gy2 = (S + GB - 1) / GB;
+            if (gy2 > gyB) gy2 = gyB;
+            k_passB_group<T><<<dim3(g.N2, gy2), kThreadsB,
+                               passB_group_smem_bytes(g, sizeof(Cplx<T>), GB, nr), st>>>(B);
+        } else {
+            k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+        }
     }
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();

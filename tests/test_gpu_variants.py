@@ -120,6 +120,46 @@ def test_batch_variants_match_single_series(nl, prec, eps):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_grouped_class_variants_match_single_series(nl, oracle_mod, prec, eps):
+    # many series of one grid class (different N_d, N_f, f0, df): the launches
+    # that take several series per block iteration, every model variant
+    import torch
+    cases = [(300 + 60 * i, (280, 300, 310)[i % 3]) for i in range(9)]
+    series = [W.random_case(400 + i, nd, nf, unit_dy=(i % 2 == 0), f0_bins=1.0 + 2.5 * i,
+                            df_t=(0.2, 0.7)[i % 2]) for i, (nd, nf) in enumerate(cases)]
+    pcode = nl.LS_FP64 if prec == "fp64" else nl.LS_FP32
+    keys = [tuple(nl.ls_choose_params(s.nf, eps, pcode, max_nd=s.nd)[k] for k in ("n", "n1", "width"))
+            for s in series]
+    assert max(keys.count(k) for k in set(keys)) >= 6
+    offsets = np.zeros(len(series) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum([s.nd for s in series])
+    t = _dev(np.concatenate([s.t for s in series]))
+    y = _dev(np.concatenate([s.y - 0.3 for s in series]))
+    dy = _dev(np.concatenate([np.ones(s.nd) if s.dy is None else s.dy for s in series]))
+    bplan = nl.Plan(2, 1, eps, prec)
+    for (fit_mean, center), norm in itertools.product(MODELS, ("standard", "log")):
+        model = dict(normalization=norm, fit_mean=fit_mean, center_data=center)
+        P, off = bplan.execute_batch(t, y, dy, offsets, [s.f0 for s in series],
+                                     [s.df for s in series], [s.nf for s in series], **model)
+        P = P.cpu().numpy()
+        for i, (s, o, a) in enumerate(zip(series, off, offsets[:-1])):
+            plan = nl.Plan(s.nd, s.nf, eps, prec)
+            P1 = plan.execute(t[a:a + s.nd].contiguous(), y[a:a + s.nd].contiguous(),
+                              dy[a:a + s.nd].contiguous(), s.f0, s.df, **model).cpu().numpy()
+            plan.close()
+            scale = max(1.0, float(np.max(np.abs(P1))))
+            assert_rerun_close(P[o:o + s.nf], P1, prec, scale, (i, fit_mean, center, norm))
+        if (fit_mean, center, norm) == (False, False, "standard"):
+            s, o = series[4], off[4]
+            ref = oracle_mod.periodogram(s.t, s.y - 0.3, s.dy, s.f0, s.df, np.arange(s.nf),
+                                         fit_mean=False, center_data=False)
+            tol = 1e-9 if prec == "fp64" else 1e-4
+            assert np.max(np.abs(P[o:o + s.nf] - ref)) <= tol
+    bplan.close()
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("fit_mean,center", MODELS)
 def test_shared_times_variants_match_oracle(nl, oracle_mod, fit_mean, center):
     import torch
