@@ -87,6 +87,9 @@ typedef struct {
     double eps;            /* tolerance the plan was made for                 */
     double sigma;          /* upsampling factor chosen (n >= sigma nf)        */
     int64_t workspace_bytes;
+    int32_t cols_per_block; /* fine-grid columns per pass-A block (bin width)  */
+    int32_t fft_max_radix;  /* largest power-of-two radix among the stages of
+                               the two sub-FFT schedules (N2 and N1)           */
 } ls_plan_info;
 
 /*
@@ -123,6 +126,22 @@ typedef struct {
      * memory at the first batch call, at most 8 GiB.  Larger batches are cut
      * into launches that fit. */
     uint64_t batch_workspace_bytes;
+    /* Fine-grid columns per pass-A block: the spreader's tile is this many
+     * columns of n2 cells, and the bin sort's bins are this many columns wide.
+     * 0 lets the plan choose (the widest of 8, 4, 2 whose two blocks fit an
+     * SM); 1, 2, 4 or 8 request a width.  A grid that cannot use the request
+     * (fewer than two bins, or a block beyond the opt-in shared memory) takes
+     * the automatic width; ls_plan_describe reports the width taken.  Batch
+     * classes apply the same rule to their own grids. */
+    int32_t cols_per_block;
+    /* Largest radix of the fine-grid FFT stages (each sub-FFT runs the odd
+     * radices 9, 3, 5 first, then powers of two): 16 for radix-16 stages, 8
+     * for radix-8 stages (more stages, lighter butterflies), for both
+     * sub-FFTs; a pass-A column that would not fit with radix 8 keeps 16.
+     * 0 lets the plan choose: radix 8 on the FP64 path; on the FP32 path
+     * radix 16 for the columns (N2) and, for the rows (N1), radix 8 where it
+     * adds no stage. */
+    int32_t fft_max_radix;
 } ls_plan_opts;
 
 /* ls_plan with options (opts may be NULL: the defaults). */

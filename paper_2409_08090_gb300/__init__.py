@@ -39,7 +39,8 @@ _dbl = ctypes.c_double
 class PlanInfo(ctypes.Structure):
     _fields_ = [("nf", _i64), ("max_nd", _i64), ("n", _i64), ("n1", _i32), ("n2", _i32),
                 ("width", _i32), ("prec", _i32), ("beta", _dbl), ("eps", _dbl),
-                ("sigma", _dbl), ("workspace_bytes", _i64)]
+                ("sigma", _dbl), ("workspace_bytes", _i64), ("cols_per_block", _i32),
+                ("fft_max_radix", _i32)]
 
 
 class LSError(RuntimeError):
@@ -121,17 +122,21 @@ def ls_status_str(status: int) -> str:
 
 
 class PlanOpts(ctypes.Structure):
-    _fields_ = [("upsampling", _dbl), ("batch_workspace_bytes", ctypes.c_uint64)]
+    _fields_ = [("upsampling", _dbl), ("batch_workspace_bytes", ctypes.c_uint64),
+                ("cols_per_block", _i32), ("fft_max_radix", _i32)]
 
 
 def ls_plan(max_nd: int, nf: int, eps: float, prec: int = LS_FP64, device: int = 0,
-            stream: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0) -> int:
-    """Plan handle; ``upsampling`` 0 (automatic), 2.0 or 1.5, and the batch
-    workspace budget in bytes (0: automatic), both through ls_plan_ex."""
+            stream: int = 0, upsampling: float = 0.0, batch_workspace_bytes: int = 0,
+            cols_per_block: int = 0, fft_max_radix: int = 0) -> int:
+    """Plan handle; ``upsampling`` 0 (automatic), 2.0 or 1.5, the batch
+    workspace budget in bytes (0: automatic), the pass-A tile width in columns
+    and the largest FFT radix (0: automatic), all through ls_plan_ex."""
     h = _c_void_p()
     lib = load_library()
-    if upsampling or batch_workspace_bytes:
-        opts = PlanOpts(float(upsampling), int(batch_workspace_bytes))
+    if upsampling or batch_workspace_bytes or cols_per_block or fft_max_radix:
+        opts = PlanOpts(float(upsampling), int(batch_workspace_bytes), int(cols_per_block),
+                        int(fft_max_radix))
         st = lib.ls_plan_ex(ctypes.byref(h), int(max_nd), int(nf), float(eps), int(prec),
                             int(device), _c_void_p(stream or None), ctypes.byref(opts))
     else:
@@ -269,15 +274,23 @@ class Plan:
     ``center_data`` (see ``mode_word``)."""
 
     def __init__(self, max_nd: int, nf: int, eps: float = 1e-9, precision="fp64",
-                 device: int = 0, upsampling: float | str = 0.0, batch_workspace_bytes: int = 0):
+                 device: int = 0, upsampling: float | str = 0.0, batch_workspace_bytes: int = 0,
+                 cols_per_block: int = 0, fft_max_radix: int = 0):
+        """``upsampling`` 0 (the plan's cost model), 2.0 or 1.5, or "tuned":
+        upsampling, tile width and FFT schedule measured per shape and cached
+        (``autotune``; explicit ``cols_per_block`` / ``fft_max_radix`` are then
+        ignored)."""
         self.prec = _prec_code(precision)
         self.device = int(device)
         if upsampling == "tuned":        # measured per shape, cached (autotune.py)
             from . import autotune
-            upsampling = autotune.tuned_upsampling(
+            opts = autotune.tuned_options(
                 nf, eps, "fp32" if self.prec == LS_FP32 else "fp64", max_nd, self.device)
+            upsampling = opts["upsampling"]
+            cols_per_block = opts["cols_per_block"]
+            fft_max_radix = opts["fft_max_radix"]
         self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling,
-                              batch_workspace_bytes)
+                              batch_workspace_bytes, cols_per_block, fft_max_radix)
         self.info = ls_plan_describe(self.handle)
 
     def close(self):

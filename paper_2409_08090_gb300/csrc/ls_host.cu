@@ -18,6 +18,8 @@ struct PlanParams {
     int32_t w, n1, n2;
     double beta, sigma, upsampling;
     int64_t n;
+    int32_t cols = 0;     // requested columns per pass-A block (0: automatic)
+    int32_t maxr = 0;     // requested largest FFT radix (0: 16)
 };
 
 struct ls_plan_s;
@@ -56,6 +58,9 @@ struct ls_plan_s {
     double eps;
     double sigma;         // upsampling factor the plan chose
     double upsampling;    // requested upsampling (0: automatic)
+    int32_t cols_req;     // requested columns per pass-A block (0: automatic)
+    int32_t maxr_req;     // requested largest FFT radix (0: 16)
+    int maxrA, maxrB;     // largest radix of the pass-A (N2) / pass-B (N1) FFT stages
     int nsm;
     Geometry g;
     Workspace ws;
@@ -91,7 +96,7 @@ constexpr int kN1MaxF32 = 4096, kN2MaxF32 = 25600;
 constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
 
-bool radix_schedule(int L, std::vector<int> &rad);
+bool radix_schedule(int L, std::vector<int> &rad, int maxr = 16);
 
 // Shared memory of a one-column pass-A block (the smallest block a split can
 // use: padded column, per-column and root tables, slot table) plus 2 KB of
@@ -132,7 +137,9 @@ int ilog2_exact(int64_t x)
 // Radix schedule of a sub-FFT of length L = c 2^k (c = 3^a 5^b, k >= 1): the
 // odd radices first (3s paired into 9s), then one stage of 8, 4 or 2 for
 // k mod 4, then 16s, so the last stage is a power of two (16 whenever k >= 4).
-bool radix_schedule(int L, std::vector<int> &rad)
+// With maxr = 8 the power-of-two part is one stage of 4 or 2 for k mod 3 and
+// then 8s (more stages, fewer registers per butterfly).
+bool radix_schedule(int L, std::vector<int> &rad, int maxr)
 {
     rad.clear();
     int x = L;
@@ -142,8 +149,9 @@ bool radix_schedule(int L, std::vector<int> &rad)
     int k = 0;
     while ((x >> k) > 1) ++k;
     if ((1 << k) != x || k == 0) return false;
-    if (k % 4) rad.push_back(1 << (k % 4));
-    for (int i = 0; i < k / 4; ++i) rad.push_back(16);
+    const int lr = maxr == 8 ? 3 : 4;
+    if (k % lr) rad.push_back(1 << (k % lr));
+    for (int i = 0; i < k / lr; ++i) rad.push_back(1 << lr);
     return (int)rad.size() <= kMaxStages;
 }
 
@@ -336,10 +344,10 @@ void plan_free(ls_plan_s *p)
 
 // Stage descriptors of a length-L DIF FFT (radix schedule, sub-lengths and
 // the constants for exact small divisions).
-bool build_fft(int L, FftPlan *fp)
+bool build_fft(int L, FftPlan *fp, int maxr = 16)
 {
     std::vector<int> rad;
-    if (!radix_schedule(L, rad)) return false;
+    if (!radix_schedule(L, rad, maxr)) return false;
     fp->L = L;
     fp->nstages = (int)rad.size();
     int Ls = L;
@@ -384,7 +392,8 @@ ls_status upload_tables(ls_plan_s *p)
 {
     Geometry &g = p->g;
     std::vector<T> tA, tB, t4;
-    if (!build_fft(g.N2, &g.fa) || !build_fft(g.N1, &g.fb)) return LS_ERR_UNSUPPORTED;
+    if (!build_fft(g.N2, &g.fa, p->maxrA) || !build_fft(g.N1, &g.fb, p->maxrB))
+        return LS_ERR_UNSUPPORTED;
     fill_root_table(tA, g.N2, 6);
     fill_root_table(tB, g.N1, 6);
     fill_root_table(t4, g.n, kTw4Bits);
@@ -688,6 +697,8 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
     p->eps = eps;
     p->sigma = pp.sigma;
     p->upsampling = pp.upsampling;
+    p->cols_req = pp.cols;
+    p->maxr_req = pp.maxr;
     p->bytes = 0;
     p->stage_in = p->stage_out = p->stage_sums = nullptr;
     p->timing = false;
@@ -702,14 +713,58 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
     g.beta = pp.beta;
     g.eps = eps;
     const size_t cx = prec == LS_FP32 ? 8 : 16;
+    // FFT schedules (largest power-of-two radix of each sub-FFT).  A request
+    // applies to both.  Automatic, from measurements on GB300: the
+    // double-float transforms of the FP64 path run faster with radix-8
+    // butterflies (fewer live registers) even where that adds a stage (pass A
+    // 5.2 -> 4.9 ms on a 1.9e7-cell grid, pass B 1.55x faster on 3.7e5 cells);
+    // on the FP32 path pass A keeps radix 16, and pass B takes radix 8 where
+    // that adds no stage (N1 = 512: 8, 8, 8 instead of 2, 16, 16; 8% faster).
+    auto nstages = [](int L, int r) {
+        std::vector<int> rad;
+        return radix_schedule(L, rad, r) ? (int)rad.size() : 1 << 20;
+    };
+    if (pp.maxr == 8 || pp.maxr == 16) {
+        p->maxrA = p->maxrB = pp.maxr;
+    } else if (prec == LS_FP64) {
+        p->maxrA = p->maxrB = 8;
+    } else {
+        p->maxrA = 16;
+        p->maxrB = nstages(pp.n1, 8) <= nstages(pp.n1, 16) ? 8 : 16;
+    }
+    // Tile width: the widest candidate whose two blocks fit an SM.  FP64 takes
+    // at most 2 columns (measured: 2 columns ran pass A 1.8x faster than 8 on
+    // a 3.7e5-cell grid, and the ragged FP64 batch 13% faster than the widest).
+    static const int kColsF32[3] = {8, 4, 2}, kColsF64[1] = {2};
+    const int *cands = prec == LS_FP64 ? kColsF64 : kColsF32;
+    const int ncand = prec == LS_FP64 ? 1 : 3;
     int BA = 1;
-    for (int cand : {8, 4, 2}) {
+    for (int i = 0; i < ncand; ++i) {
+        const int cand = cands[i];
         if (pp.n1 % cand == 0 && (size_t)cand * pp.n2 * cx <= kSmemPairBudget &&
             pp.n1 / cand >= 2) {
             BA = cand;
             break;
         }
     }
+    // Shared memory of a pass-A block of ba columns without cluster tables
+    // (padded columns, root tables, slot table) plus 1 KB of margin.
+    auto tile_bytes = [&](int ba) {
+        std::vector<int> rad;
+        if (!radix_schedule(pp.n2, rad, p->maxrA)) return (size_t)-1;
+        const size_t nhi = (size_t)(pp.n2 + 63) / 64;
+        const size_t padded = (size_t)pp.n2 + pp.n2 / 16 + 1;
+        return cx * ((size_t)ba * padded + (size_t)ba * (64 + nhi) + 64 + nhi) +
+               sizeof(int) * (size_t)(pp.n2 / rad.back()) + 1024;
+    };
+    // radix-8 stages need a larger slot table: keep 16 where it would not fit
+    if (p->maxrA == 8 && tile_bytes(BA) > kSmemOptinBytes) p->maxrA = 16;
+    // A requested tile width is taken where the grid can use it: at least two
+    // bins, and the block within the opt-in shared memory (one block per SM
+    // at the widest).
+    if (pp.cols > 0 && pp.n1 % pp.cols == 0 && pp.n1 / pp.cols >= 2 &&
+        tile_bytes(pp.cols) <= kSmemOptinBytes)
+        BA = pp.cols;
     g.BA = BA;
     g.logBA = ilog2_exact(BA);
     g.nbins = pp.n1 / BA;
@@ -940,6 +995,13 @@ ls_status ls_plan_ex(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int
     if (max_nd < 2 || max_nd > ((int64_t)1 << 30)) return LS_ERR_ARG;
     PlanParams pp;
     pp.upsampling = opts ? opts->upsampling : 0.0;
+    if (opts) {
+        const int c = opts->cols_per_block, r = opts->fft_max_radix;
+        if (!(c == 0 || c == 1 || c == 2 || c == 4 || c == 8)) return LS_ERR_ARG;
+        if (!(r == 0 || r == 8 || r == 16)) return LS_ERR_ARG;
+        pp.cols = c;
+        pp.maxr = r;
+    }
     ls_status s = ls_choose_params(nf, eps, prec, max_nd, pp.upsampling, &pp.w, &pp.beta, &pp.n,
                                    &pp.n1, &pp.n2, &pp.sigma);
     if (s != LS_OK) return s;
@@ -978,6 +1040,8 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
         Item it;
         it.s = s;
         it.pp.upsampling = p->upsampling;
+        it.pp.cols = p->cols_req;
+        it.pp.maxr = p->maxr_req;
         ls_status st = ls_choose_params(nf[s], eps, p->prec, nd, p->upsampling, &it.pp.w,
                                         &it.pp.beta, &it.pp.n, &it.pp.n1, &it.pp.n2, &it.pp.sigma);
         if (st != LS_OK) return st;
@@ -1059,6 +1123,8 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
         return LS_ERR_ARG;
     PlanParams pp;
     pp.upsampling = p->upsampling;
+    pp.cols = p->cols_req;
+    pp.maxr = p->maxr_req;
     ls_status st = ls_choose_params(nf, eps, p->prec, nd, p->upsampling, &pp.w, &pp.beta, &pp.n,
                                     &pp.n1, &pp.n2, &pp.sigma);
     if (st != LS_OK) return st;
@@ -1184,6 +1250,14 @@ ls_status ls_plan_describe(ls_plan_t p, ls_plan_info *info)
     info->eps = p->eps;
     info->sigma = p->sigma;
     info->workspace_bytes = p->bytes;
+    info->cols_per_block = p->g.BA;
+    int r = 0;
+    for (const FftPlan *f : {&p->g.fa, &p->g.fb})
+        for (int k = 0; k < f->nstages; ++k) {
+            const int R = f->st[k].R;
+            if ((R & (R - 1)) == 0 && R > r) r = R;
+        }
+    info->fft_max_radix = r;
     return LS_OK;
 }
 

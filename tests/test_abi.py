@@ -143,3 +143,31 @@ def test_choose_params_is_cheap_enough_for_per_series_calls():
     for i in range(2000):
         nl.ls_choose_params(1000 + 600 * i, 1e-6, nl.LS_FP32, 100 + 50 * i)
     assert time.perf_counter() - t0 < 2.0
+
+
+def _struct_fields(name):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            out += [v.strip() for v in decl.split(None, 1)[1].split(",")]
+    return out
+
+
+def test_option_and_info_structs_match_the_header():
+    import paper_2409_08090_gb300 as nl
+    assert [f[0] for f in nl.PlanOpts._fields_] == _struct_fields("ls_plan_opts")
+    assert [f[0] for f in nl.PlanInfo._fields_] == _struct_fields("ls_plan_info")
+
+
+@pytest.mark.parametrize("opt", [dict(cols_per_block=3), dict(cols_per_block=16),
+                                 dict(fft_max_radix=4), dict(fft_max_radix=32),
+                                 dict(upsampling=1.25)])
+def test_plan_options_are_validated_before_any_device_work(opt):
+    # argument checks run on the host, ahead of the device query
+    import paper_2409_08090_gb300 as nl
+    with pytest.raises(nl.LSError) as e:
+        nl.ls_plan(1000, 12_000, 1e-6, nl.LS_FP32, **opt)
+    assert e.value.status == 1
