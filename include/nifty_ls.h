@@ -227,6 +227,52 @@ ls_status ls_execute_batch_shared(ls_plan_t plan, int64_t nseries, int64_t nd, c
                                   const double *Y, const double *dy, double f0, double df,
                                   int64_t nf, double eps, int norm, double *power);
 
+/*
+ * Prepared batches: the host work of a batch call done once for a fixed
+ * layout, so repeated batches of new values pay only the kernels and a run can
+ * be recorded by CUDA stream capture (a graph) and replayed.
+ *
+ * ls_batch_prepare takes the arguments of ls_execute_batch that fix the
+ * layout (offsets, f0, df, nf, out_offsets, eps, norm; host arrays, read
+ * during the call only), and ls_batch_prepare_shared those of
+ * ls_execute_batch_shared (nseries, nd, f0, df, nf, eps, norm).  Preparation
+ * validates the series, groups them by fine grid, builds each grid's tables,
+ * splits the groups into launches within the plan's batch workspace budget,
+ * allocates the workspaces of those launches and uploads the per-series
+ * descriptors; the batch owns all of it (ls_batch_describe reports the
+ * bytes).  Synchronous (table construction).
+ *
+ * ls_batch_run: the periodograms of the prepared layout for the values at t,
+ * y, dy (device arrays laid out as for the matching execute call) into power
+ * (device).  It enqueues kernels and memsets only (on the plan's stream and
+ * its four batch streams, joined back into the plan's stream before it
+ * returns): no allocation, no host-device copy, no host synchronisation.
+ * Errors and the device status word behave as for ls_execute_batch.  Runs of
+ * one batch, and runs and other calls on its plan, must not overlap on the
+ * device (they share streams, the status word and, for one batch, its
+ * workspaces); the plan must outlive the batch.
+ *
+ * ls_batch_destroy waits for the plan's streams and frees the batch.  A graph
+ * recorded from ls_batch_run must not be replayed after that.  ls_destroy of
+ * the plan releases the device memory of batches still prepared on it and
+ * leaves their handles inert: ls_batch_run and ls_batch_describe then return
+ * LS_ERR_ARG and ls_batch_destroy only frees the handle.
+ */
+typedef struct ls_batch_s *ls_batch_t;
+
+ls_status ls_batch_prepare(ls_plan_t plan, ls_batch_t *out, int64_t nseries,
+                           const int64_t *offsets, const double *f0, const double *df,
+                           const int64_t *nf, const int64_t *out_offsets, double eps, int norm);
+ls_status ls_batch_prepare_shared(ls_plan_t plan, ls_batch_t *out, int64_t nseries, int64_t nd,
+                                  double f0, double df, int64_t nf, double eps, int norm);
+ls_status ls_batch_run(ls_batch_t batch, const double *t, const double *y, const double *dy,
+                       double *power);
+/* Launches and grid classes of the batch, and the device bytes it owns (any
+ * output pointer may be NULL). */
+ls_status ls_batch_describe(ls_batch_t batch, int64_t *launches, int64_t *classes,
+                            int64_t *bytes);
+ls_status ls_batch_destroy(ls_batch_t batch);
+
 /* Wait for the plan's stream; return and clear the device-side status of every
  * execute since the previous ls_sync (LS_ERR_ARG for invalid values,
  * LS_ERR_DEGENERATE for a constant series, else LS_OK). */

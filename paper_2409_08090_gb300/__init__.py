@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 from . import build as _build
 
@@ -21,7 +22,8 @@ __all__ = ["LSError", "Plan", "GraphedExecute", "lombscargle", "load_library", "
            "LS_NO_FIT_MEAN", "LS_NO_CENTER", "NORMALIZATIONS", "mode_word", "ls_plan", "ls_execute", "ls_execute_sums", "ls_sync",
            "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_execute_batch_shared", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
-           "ls_timing_report", "STAGE_NAMES"]
+           "ls_timing_report", "STAGE_NAMES", "PreparedBatch", "GraphedBatch", "ls_batch_prepare",
+           "ls_batch_prepare_shared", "ls_batch_run", "ls_batch_describe", "ls_batch_destroy"]
 
 LS_FP64, LS_FP32 = 0, 1
 LS_NORM_STANDARD, LS_NORM_MODEL, LS_NORM_LOG, LS_NORM_PSD = range(4)
@@ -82,6 +84,15 @@ _SIGS = {
                                                _c_void_p]),
     "ls_execute_noalloc": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _i64, _dbl, _dbl,
                                           _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
+    "ls_batch_prepare": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_c_void_p), _i64, _c_void_p,
+                                        _c_void_p, _c_void_p, _c_void_p, _c_void_p, _dbl,
+                                        ctypes.c_int]),
+    "ls_batch_prepare_shared": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_c_void_p), _i64, _i64,
+                                               _dbl, _dbl, _i64, _dbl, ctypes.c_int]),
+    "ls_batch_run": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p]),
+    "ls_batch_describe": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                         ctypes.POINTER(_i64)]),
+    "ls_batch_destroy": (ctypes.c_int, [_c_void_p]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "ls_timing_report": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
 }
@@ -224,6 +235,43 @@ def ls_choose_params(nf: int, eps: float, prec: int = LS_FP64, max_nd: int | Non
             "sigma": sg.value}
 
 
+def ls_batch_prepare(plan: int, nseries: int, offsets: int, f0: int, df: int, nf: int,
+                     out_offsets: int, eps: float, norm: int) -> int:
+    """Prepared-batch handle; offsets, f0, df, nf, out_offsets are host addresses."""
+    h = _c_void_p()
+    _check(load_library().ls_batch_prepare(_c_void_p(plan), ctypes.byref(h), int(nseries),
+                                           _c_void_p(offsets), _c_void_p(f0), _c_void_p(df),
+                                           _c_void_p(nf), _c_void_p(out_offsets), float(eps),
+                                           int(norm)), "ls_batch_prepare")
+    return h.value
+
+
+def ls_batch_prepare_shared(plan: int, nseries: int, nd: int, f0: float, df: float, nf: int,
+                            eps: float, norm: int) -> int:
+    h = _c_void_p()
+    _check(load_library().ls_batch_prepare_shared(_c_void_p(plan), ctypes.byref(h), int(nseries),
+                                                  int(nd), float(f0), float(df), int(nf),
+                                                  float(eps), int(norm)),
+           "ls_batch_prepare_shared")
+    return h.value
+
+
+def ls_batch_run(batch: int, t: int, y: int, dy: int | None, power: int) -> int:
+    return load_library().ls_batch_run(_c_void_p(batch), _c_void_p(t), _c_void_p(y),
+                                       _c_void_p(dy or None), _c_void_p(power))
+
+
+def ls_batch_describe(batch: int) -> dict:
+    a, b, c = _i64(), _i64(), _i64()
+    _check(load_library().ls_batch_describe(_c_void_p(batch), ctypes.byref(a), ctypes.byref(b),
+                                            ctypes.byref(c)), "ls_batch_describe")
+    return {"launches": a.value, "classes": b.value, "bytes": c.value}
+
+
+def ls_batch_destroy(batch: int) -> int:
+    return load_library().ls_batch_destroy(_c_void_p(batch))
+
+
 def ls_timing_enable(plan: int, enable: bool = True) -> None:
     _check(load_library().ls_timing_enable(_c_void_p(plan), int(bool(enable))),
            "ls_timing_enable")
@@ -292,8 +340,13 @@ class Plan:
         self.handle = ls_plan(max_nd, nf, eps, self.prec, self.device, 0, upsampling,
                               batch_workspace_bytes, cols_per_block, fft_max_radix)
         self.info = ls_plan_describe(self.handle)
+        self._batches = weakref.WeakSet()
 
     def close(self):
+        """Destroy the plan (its prepared batches first: finalizers of objects
+        in a reference cycle run in no particular order)."""
+        for b in list(getattr(self, "_batches", ())):
+            b.close()
         if getattr(self, "handle", None):
             ls_destroy(self.handle)
             self.handle = None
@@ -333,6 +386,37 @@ class Plan:
         if sync:
             _check(ls_sync(self.handle), "ls_execute (device status)")
         return out
+
+    def prepare_batch(self, offsets, f0, df, nf, eps=None, **model) -> "PreparedBatch":
+        """Prepare the layout of a ragged batch (arguments as for
+        ``execute_batch``, without the data): ``PreparedBatch.run`` then
+        computes it for new values with kernels only."""
+        import numpy as np
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        ns = offsets.shape[0] - 1
+        f0 = np.ascontiguousarray(np.broadcast_to(np.asarray(f0, dtype=np.float64), (ns,)))
+        df = np.ascontiguousarray(np.broadcast_to(np.asarray(df, dtype=np.float64), (ns,)))
+        nf = np.ascontiguousarray(np.broadcast_to(np.asarray(nf, dtype=np.int64), (ns,)))
+        out_off = np.zeros(ns, dtype=np.int64)
+        if ns > 1:
+            out_off[1:] = np.cumsum(nf)[:-1]
+        eps = float(self.info.eps if eps is None else eps)
+        ls_set_stream(self.handle, self._stream())
+        h = ls_batch_prepare(self.handle, ns, offsets.ctypes.data, f0.ctypes.data, df.ctypes.data,
+                             nf.ctypes.data, out_off.ctypes.data, eps, mode_word(**model))
+        pb = PreparedBatch(self, h, (int(nf.sum()),), out_off)
+        self._batches.add(pb)
+        return pb
+
+    def prepare_shared(self, nseries: int, nd: int, f0: float, df: float, nf: int, eps=None,
+                       **model) -> "PreparedBatch":
+        """Prepare a uniform batch (arguments as for ``execute_shared``)."""
+        eps = float(self.info.eps if eps is None else eps)
+        ls_set_stream(self.handle, self._stream())
+        h = ls_batch_prepare_shared(self.handle, nseries, nd, f0, df, nf, eps, mode_word(**model))
+        pb = PreparedBatch(self, h, (int(nseries), int(nf)), None)
+        self._batches.add(pb)
+        return pb
 
     def graph(self, t, y, dy, f0: float, df: float, nf: int | None = None, eps=None, out=None,
               **model) -> "GraphedExecute":
@@ -411,6 +495,25 @@ class Plan:
         return out
 
 
+def _record(plan: "Plan", run, device: int):
+    """Warm a run up outside capture (first-use set-up of the kernels), then
+    record one run as a CUDA graph.  "relaxed": the library queries pointer
+    attributes while recording."""
+    import torch
+    side = torch.cuda.Stream(device=device)
+    side.wait_stream(torch.cuda.current_stream(device))
+    with torch.cuda.stream(side):
+        run()
+    torch.cuda.current_stream(device).wait_stream(side)
+    torch.cuda.synchronize(device)
+    _check(ls_sync(plan.handle), "graph warm-up (device status)")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="relaxed"):
+        run()
+    torch.cuda.synchronize(device)
+    return graph
+
+
 class GraphedExecute:
     """One ``ls_execute`` recorded by CUDA stream capture (torch.cuda.CUDAGraph).
 
@@ -429,28 +532,98 @@ class GraphedExecute:
         self.out = out if out is not None else torch.empty(nf, dtype=torch.float64,
                                                             device=t.device)
         self._args = (t, y, dy, f0, df, nf, eps)
-        dev = plan.device
-        # warm-up outside the capture (first-use set-up of the kernels), then record
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(torch.cuda.current_stream(dev))
-        with torch.cuda.stream(side):
-            plan.execute(t, y, dy, f0, df, nf, eps, out=self.out, sync=False, **model)
-        torch.cuda.current_stream(dev).wait_stream(side)
-        torch.cuda.synchronize(dev)
-        _check(ls_sync(plan.handle), "graph warm-up (device status)")
-        self.graph = torch.cuda.CUDAGraph()
-        # "relaxed": the library queries pointer attributes while recording
-        with torch.cuda.graph(self.graph, capture_error_mode="relaxed"):
-            plan.execute(t, y, dy, f0, df, nf, eps, out=self.out, sync=False, **model)
-        torch.cuda.synchronize(dev)
+        self.graph = _record(plan, lambda: plan.execute(t, y, dy, f0, df, nf, eps, out=self.out,
+                                                         sync=False, **model), plan.device)
 
     def replay(self):
         """Enqueue the recorded pipeline on the current stream's device."""
+        if not self.plan.handle:
+            raise RuntimeError("the plan of this graph was closed: its memory is gone")
         self.graph.replay()
         return self.out
 
     def sync(self):
         _check(ls_sync(self.plan.handle), "graph replay (device status)")
+        return self.out
+
+
+class PreparedBatch:
+    """A batch layout prepared once (``ls_batch_prepare`` / ``_shared``).
+
+    ``run(t, y, dy)`` computes the periodograms of new values in that layout
+    (ragged: concatenated t, y, dy as for ``Plan.execute_batch``; shared: t, dy
+    of nd values and Y of nseries x nd) with kernels only, and ``graph``
+    records a run as a CUDA graph.  Output: ragged, a flat tensor with series
+    s at ``out_offsets[s]``; shared, (nseries, nf).  The plan must outlive
+    the batch; runs on one plan must not overlap."""
+
+    def __init__(self, plan: "Plan", handle: int, shape: tuple, out_offsets):
+        self.plan = plan
+        self.handle = handle
+        self.shape = shape
+        self.out_offsets = out_offsets
+
+    def describe(self) -> dict:
+        return ls_batch_describe(self.handle)
+
+    def _out(self, like, out):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=like.device)
+        return out
+
+    def run(self, t, y, dy, out=None, sync: bool = True):
+        import torch
+        if not self.handle:
+            raise RuntimeError("this prepared batch was closed")
+        for a in (t, y) + ((dy,) if dy is not None else ()):
+            if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+                raise ValueError("t, y, dy must be contiguous float64 CUDA tensors")
+        out = self._out(t, out)
+        ls_set_stream(self.plan.handle, self.plan._stream())
+        _check(ls_batch_run(self.handle, t.data_ptr(), y.data_ptr(),
+                            dy.data_ptr() if dy is not None else None, out.data_ptr()),
+               "ls_batch_run")
+        if sync:
+            _check(ls_sync(self.plan.handle), "ls_batch_run (device status)")
+        return out
+
+    def graph(self, t, y, dy, out=None) -> "GraphedBatch":
+        return GraphedBatch(self, t, y, dy, self._out(t, out))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ls_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GraphedBatch:
+    """One ``PreparedBatch.run`` recorded as a CUDA graph: a replay re-runs
+    every launch of the batch (over the plan's batch streams) on the current
+    contents of t, y, dy.  ``sync()`` raises device-side errors.  The batch
+    must outlive the graph."""
+
+    def __init__(self, batch: PreparedBatch, t, y, dy, out):
+        self.batch = batch
+        self.out = out
+        self._args = (t, y, dy)
+        self.graph = _record(batch.plan, lambda: batch.run(t, y, dy, out=out, sync=False),
+                             batch.plan.device)
+
+    def replay(self):
+        if not self.batch.handle:
+            raise RuntimeError("the batch of this graph was closed: its memory is gone")
+        self.graph.replay()
+        return self.out
+
+    def sync(self):
+        _check(ls_sync(self.batch.plan.handle), "graph replay (device status)")
         return self.out
 
 

@@ -23,6 +23,7 @@ struct PlanParams {
 };
 
 struct ls_plan_s;
+struct ls_batch_s;
 
 // One grid class of a ragged batch: series whose frequency count maps to the
 // same fine grid share these tables (sub-plan without workspace).
@@ -85,6 +86,32 @@ struct ls_plan_s {
     cudaEvent_t lane_done[kBatchLanes] = {};
     cudaEvent_t lane_start = nullptr;
     int64_t batch_budget = 0;   // bytes for the batch workspaces (0: chosen on first use)
+    std::vector<ls_batch_s *> batches;   // prepared batches not yet destroyed
+};
+
+// One launch of a prepared batch (ls_batch_prepare): everything but the
+// data pointers, fixed at preparation.
+struct PreparedLaunch {
+    int lane;
+    size_t cls;           // index into ls_batch_s::subs
+    int S;
+    int64_t points, max_nd;
+    size_t desc_off;      // first descriptor in ls_batch_s::desc_all
+    SeriesDesc one;
+    int shared;
+};
+
+// A prepared batch owns its class tables, its per-lane workspaces and its
+// device descriptors, so nothing a later call does to the plan's own batch
+// state (class rebuilds, workspace growth) moves memory a recorded run uses.
+struct ls_batch_s {
+    ls_plan_s *plan = nullptr;   // null once the plan is destroyed (the handle is then inert)
+    int norm = 0;
+    std::vector<ls_plan_s *> subs;
+    std::vector<PreparedLaunch> launches;
+    BatchWorkspace bws[kBatchLanes];
+    SeriesDesc *desc_all = nullptr;
+    int64_t bytes = 0;
 };
 
 namespace {
@@ -613,22 +640,25 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
 // ---------------------------------------------------------------------------
 void batch_free(ls_plan_s *p);
 
-// Make the batch workspace hold S series, `points` records, `cells` elements
-// of H, `bins` histogram entries per array and nred reduction blocks per
-// series (the buffers grow by a quarter beyond the request).
+// Make the batch workspace b hold S series, `points` records, `cells`
+// elements of H, `bins` histogram entries per array and nred reduction blocks
+// per series (the buffers grow by a quarter beyond the request).  st is the
+// stream that last used b (synchronised before a reallocation); device errors
+// of its launches go to the status word `status`.
 template <typename T>
-ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t cells, int64_t bins,
-                        int nred)
+ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int64_t points,
+                     int64_t cells, int64_t bins, int nred, bool exact = false)
 {
-    BatchWorkspace &b = p->bws[lane];
     if (S <= b.cap_S && points <= b.cap_points && cells <= b.cap_cells && nred <= b.cap_nred &&
         bins <= b.ws_bins)
         return LS_OK;
-    cudaStreamSynchronize(p->lane_stream[lane]);
+    if (st) cudaStreamSynchronize(st);
     for (void *a : b.allocs) cudaFree(a);
     b.allocs.clear();
     b.bytes = 0;
-    auto grow = [](int64_t need, int64_t have) { return need > have ? need + need / 4 : have; };
+    auto grow = [exact](int64_t need, int64_t have) {
+        return need > have ? need + (exact ? 0 : need / 4) : have;
+    };
     b.cap_S = (int)grow(S, b.cap_S);
     b.cap_points = grow(points, b.cap_points);
     b.cap_cells = grow(cells, b.cap_cells);
@@ -670,8 +700,16 @@ ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t c
     ws.stats = static_cast<Stats *>(v);
     if ((s = alloc(&v, sizeof(SeriesDesc) * (size_t)b.cap_S)) != LS_OK) return s;
     b.desc = static_cast<SeriesDesc *>(v);
-    ws.status = p->ws.status;   // errors of batch launches reach ls_sync too
+    ws.status = status;   // errors of batch launches reach ls_sync too
     return LS_OK;
+}
+
+template <typename T>
+ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t cells, int64_t bins,
+                        int nred)
+{
+    return reserve_ws<T>(p->bws[lane], p->lane_stream[lane], p->ws.status, S, points, cells, bins,
+                         nred);
 }
 
 // Plan (geometry, tables and, unless tables_only, the single-series workspace)
@@ -876,18 +914,43 @@ ls_status batch_class(ls_plan_s *p, const PlanParams &pp, int64_t nf, ls_plan_s 
     return LS_OK;
 }
 
+// Reduction blocks per series of a batch launch: one per 256 points, at most
+// about eight blocks per SM over the launch.
+int batch_nred(const ls_plan_s *p, int S, int64_t max_nd)
+{
+    int nred = (int)((max_nd + 255) / 256);
+    const int cap_red = (8 * p->nsm + S - 1) / S;
+    if (nred > cap_red) nred = cap_red;
+    return nred < 1 ? 1 : nred;
+}
+
+// Enqueue the pipeline of one batch launch on stream st: workspace b (sized
+// for it), tables of the class plan `sub`, descriptors already on the device.
+// Kernels and memsets only, so the launch can be recorded by stream capture.
 template <typename T>
-ls_status batch_launch(ls_plan_s *p, int lane, ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
+ls_status enqueue_batch(const BatchWorkspace &b, cudaStream_t st, const ls_plan_s *sub,
+                        const Batch &bt, int64_t max_nd, int nred, const double *t,
+                        const double *y, const double *dy, double *power, int shared, int mode)
+{
+    Workspace ws = b.ws;
+    ws.twA = sub->ws.twA;
+    ws.twB = sub->ws.twB;
+    ws.tw4 = sub->ws.tw4;
+    ws.deconv = sub->ws.deconv;
+    ws.deconv_slot = sub->ws.deconv_slot;
+    return cuda_status(launch_pipeline<T>(sub->g, ws, b.cap_points, bt, max_nd, t, y, dy, power,
+                                          nullptr, nred, st, nullptr, shared, mode));
+}
+
+template <typename T>
+ls_status batch_launch(ls_plan_s *p, int lane, const ls_plan_s *sub, const std::vector<SeriesDesc> &descs,
                        int64_t points, int64_t max_nd, const double *t, const double *y,
                        const double *dy, double *power, int shared, int mode)
 {
     const Geometry &g = sub->g;
     const int S = (int)descs.size();
     const int64_t grids = shared ? S + 2 : 3 * (int64_t)S;
-    int nred = (int)((max_nd + 255) / 256);
-    const int cap_red = (8 * p->nsm + S - 1) / S;
-    if (nred > cap_red) nred = cap_red;
-    if (nred < 1) nred = 1;
+    const int nred = batch_nred(p, S, max_nd);
     ls_status s = batch_reserve<T>(p, lane, S, points, g.n * grids,
                                    2 * ((int64_t)g.nbins + 1) * S, nred);
     if (s != LS_OK) return s;
@@ -896,19 +959,208 @@ ls_status batch_launch(ls_plan_s *p, int lane, ls_plan_s *sub, const std::vector
     cudaError_t e = cudaMemcpyAsync(b.desc, descs.data(), sizeof(SeriesDesc) * descs.size(),
                                     cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_status(e);
-    Workspace ws = b.ws;
-    ws.twA = sub->ws.twA;
-    ws.twB = sub->ws.twB;
-    ws.tw4 = sub->ws.tw4;
-    ws.deconv = sub->ws.deconv;
-    ws.deconv_slot = sub->ws.deconv_slot;
     Batch bt;
     bt.S = S;
     bt.many = b.desc;
     bt.one = descs[0];
-    e = launch_pipeline<T>(g, ws, b.cap_points, bt, max_nd, t, y, dy, power, nullptr, nred,
-                           st, nullptr, shared, mode);
-    return cuda_status(e);
+    return enqueue_batch<T>(b, st, sub, bt, max_nd, nred, t, y, dy, power, shared, mode);
+}
+
+// Default batch budget: half of the free device memory, at most 8 GiB.
+void init_batch_budget(ls_plan_s *p)
+{
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    p->batch_budget = (int64_t)std::min<size_t>(fr / 2, (size_t)8 << 30);
+}
+
+// A grid class of a ragged batch call and the largest N_f among its series.
+struct ClassSpec {
+    PlanParams pp;
+    int64_t nf_max;
+};
+
+// One launch of a ragged batch: series of one class (index cls) whose fine
+// grids and point records fit the lane budget.
+struct LaunchSpec {
+    size_t cls;
+    std::vector<SeriesDesc> descs;
+    int64_t points = 0, max_nd = 0;
+};
+
+// Validate every series of a ragged batch, find its grid class (n, N1, w,
+// beta of ls_choose_params), group the series by class (stable: series keep
+// their order inside a class) and cut each class into launches of at most
+// lane_budget bytes of grids and records.
+ls_status split_batch(const ls_plan_s *p, int64_t nseries, const int64_t *offsets,
+                      const double *f0, const double *df, const int64_t *nf,
+                      const int64_t *out_offsets, double eps, int64_t lane_budget,
+                      std::vector<ClassSpec> &classes, std::vector<LaunchSpec> &launches)
+{
+    struct Item {
+        int64_t s;
+        PlanParams pp;
+    };
+    std::vector<Item> items;
+    items.reserve((size_t)nseries);
+    for (int64_t s = 0; s < nseries; ++s) {
+        const int64_t nd = offsets[s + 1] - offsets[s];
+        if (offsets[s] < 0 || nd < 2 || nf[s] < 1 || out_offsets[s] < 0) return LS_ERR_ARG;
+        if (!(df[s] > 0.0) || !isfinite(df[s]) || !isfinite(f0[s])) return LS_ERR_ARG;
+        Item it;
+        it.s = s;
+        it.pp.upsampling = p->upsampling;
+        it.pp.cols = p->cols_req;
+        it.pp.maxr = p->maxr_req;
+        ls_status st = ls_choose_params(nf[s], eps, p->prec, nd, p->upsampling, &it.pp.w,
+                                        &it.pp.beta, &it.pp.n, &it.pp.n1, &it.pp.n2, &it.pp.sigma);
+        if (st != LS_OK) return st;
+        items.push_back(it);
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.pp.n != b.pp.n) return a.pp.n > b.pp.n;
+        if (a.pp.n1 != b.pp.n1) return a.pp.n1 < b.pp.n1;
+        return a.pp.w < b.pp.w;
+    });
+    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
+    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    constexpr int kMaxBatchS = 16384;
+    size_t i = 0;
+    while (i < items.size()) {
+        size_t j = i;
+        int64_t nf_max = 0;
+        while (j < items.size() && items[j].pp.n == items[i].pp.n && items[j].pp.n1 == items[i].pp.n1 &&
+               items[j].pp.w == items[i].pp.w && items[j].pp.beta == items[i].pp.beta) {
+            nf_max = std::max(nf_max, nf[items[j].s]);
+            ++j;
+        }
+        classes.push_back(ClassSpec{items[i].pp, nf_max});
+        size_t k = i;
+        while (k < j) {
+            LaunchSpec L;
+            L.cls = classes.size() - 1;
+            while (k < j && (int)L.descs.size() < kMaxBatchS) {
+                const int64_t s = items[k].s;
+                const int64_t nd = offsets[s + 1] - offsets[s];
+                const int64_t bytes = (int64_t)(3 * (size_t)items[k].pp.n * cx * (L.descs.size() + 1) +
+                                                4 * recb * (size_t)(L.points + nd));
+                if (!L.descs.empty() && bytes > lane_budget) break;
+                L.descs.push_back(make_series(offsets[s], L.points, nd, out_offsets[s], nf[s], f0[s],
+                                              df[s]));
+                L.points += nd;
+                L.max_nd = std::max(L.max_nd, nd);
+                ++k;
+            }
+            launches.push_back(std::move(L));
+        }
+        i = j;
+    }
+    return LS_OK;
+}
+
+// Build the prepared batch b from its classes and launches: class tables,
+// per-lane workspaces sized for the launches each lane takes (round robin, as
+// ls_execute_batch), and all descriptors in one device array.
+template <typename T>
+ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec> &classes,
+                        const std::vector<LaunchSpec> &launches, int shared)
+{
+    for (const ClassSpec &c : classes) {
+        ls_plan_t np = nullptr;
+        ls_status s = create_plan(&np, 2, c.nf_max, p->eps, p->prec, p->device, p->stream, c.pp,
+                                  true);
+        if (s != LS_OK) return s;
+        b->subs.push_back(np);
+        b->bytes += np->bytes;
+    }
+    struct Need {
+        bool used = false;
+        int S = 0, nred = 0;
+        int64_t points = 0, cells = 0, bins = 0;
+    } need[kBatchLanes];
+    std::vector<SeriesDesc> all;
+    int lane = 0;
+    for (const LaunchSpec &L : launches) {
+        const ls_plan_s *sub = b->subs[L.cls];
+        PreparedLaunch pl;
+        pl.lane = lane;
+        pl.cls = L.cls;
+        pl.S = (int)L.descs.size();
+        pl.points = L.points;
+        pl.max_nd = L.max_nd;
+        pl.desc_off = all.size();
+        pl.one = L.descs[0];
+        pl.shared = shared;
+        all.insert(all.end(), L.descs.begin(), L.descs.end());
+        const int64_t grids = shared ? pl.S + 2 : 3 * (int64_t)pl.S;
+        Need &n = need[lane];
+        n.used = true;
+        n.S = std::max(n.S, pl.S);
+        n.nred = std::max(n.nred, batch_nred(p, pl.S, pl.max_nd));
+        n.points = std::max(n.points, pl.points);
+        n.cells = std::max(n.cells, sub->g.n * grids);
+        n.bins = std::max(n.bins, 2 * ((int64_t)sub->g.nbins + 1) * pl.S);
+        b->launches.push_back(pl);
+        lane = (lane + 1) % kBatchLanes;
+    }
+    for (int l = 0; l < kBatchLanes; ++l) {
+        if (!need[l].used) continue;
+        ls_status s = reserve_ws<T>(b->bws[l], nullptr, p->ws.status, need[l].S, need[l].points,
+                                    need[l].cells, need[l].bins, need[l].nred, true);
+        if (s != LS_OK) return s;
+        b->bytes += b->bws[l].bytes;
+    }
+    void *v = nullptr;
+    const size_t db = sizeof(SeriesDesc) * all.size();
+    cudaError_t e = cudaMalloc(&v, db);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->desc_all = static_cast<SeriesDesc *>(v);
+    b->bytes += (int64_t)db;
+    return cuda_status(cudaMemcpy(b->desc_all, all.data(), db, cudaMemcpyHostToDevice));
+}
+
+void batch_release(ls_batch_s *b)
+{
+    for (ls_plan_s *sp : b->subs) {
+        plan_free(sp);
+        delete sp;
+    }
+    b->subs.clear();
+    for (BatchWorkspace &w : b->bws) {
+        for (void *a : w.allocs) cudaFree(a);
+        w = BatchWorkspace();
+    }
+    if (b->desc_all) cudaFree(b->desc_all);
+    b->desc_all = nullptr;
+}
+
+// Validation shared by the batch entry points (series-independent arguments).
+ls_status check_batch_call(const ls_plan_s *p, double eps, int norm)
+{
+    if (!mode_supported(norm)) return LS_ERR_UNSUPPORTED;
+    if (!(eps >= p->eps * (1.0 - 1e-12)) || !isfinite(eps)) return LS_ERR_ARG;
+    return LS_OK;
+}
+
+ls_status finish_prepare(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec> &classes,
+                         const std::vector<LaunchSpec> &launches, int shared, ls_batch_t *out)
+{
+    ls_status st = (p->prec == LS_FP32) ? prepare_batch<float>(p, b, classes, launches, shared)
+                                        : prepare_batch<double>(p, b, classes, launches, shared);
+    if (st == LS_OK) {
+        // the lanes' streams and events exist before any run (none is created
+        // while a run is being recorded)
+        st = lanes_begin(p);
+        LanesJoin join{p};
+    }
+    if (st != LS_OK) {
+        batch_release(b);
+        delete b;
+        return st;
+    }
+    p->batches.push_back(b);
+    *out = b;
+    return LS_OK;
 }
 
 }  // namespace
@@ -1026,82 +1278,26 @@ ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets,
     if (!is_device_pointer(t) || !is_device_pointer(y) || !is_device_pointer(power) ||
         (dy && !is_device_pointer(dy)))
         return LS_ERR_ARG;
-    // Validate every series and find its grid class.
-    struct Item {
-        int64_t s;
-        PlanParams pp;
-    };
-    std::vector<Item> items;
-    items.reserve((size_t)nseries);
-    for (int64_t s = 0; s < nseries; ++s) {
-        const int64_t nd = offsets[s + 1] - offsets[s];
-        if (offsets[s] < 0 || nd < 2 || nf[s] < 1 || out_offsets[s] < 0) return LS_ERR_ARG;
-        if (!(df[s] > 0.0) || !isfinite(df[s]) || !isfinite(f0[s])) return LS_ERR_ARG;
-        Item it;
-        it.s = s;
-        it.pp.upsampling = p->upsampling;
-        it.pp.cols = p->cols_req;
-        it.pp.maxr = p->maxr_req;
-        ls_status st = ls_choose_params(nf[s], eps, p->prec, nd, p->upsampling, &it.pp.w,
-                                        &it.pp.beta, &it.pp.n, &it.pp.n1, &it.pp.n2, &it.pp.sigma);
-        if (st != LS_OK) return st;
-        items.push_back(it);
-    }
-    // Group by class (stable: series keep their order inside a class).
-    std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
-        if (a.pp.n != b.pp.n) return a.pp.n > b.pp.n;
-        if (a.pp.n1 != b.pp.n1) return a.pp.n1 < b.pp.n1;
-        return a.pp.w < b.pp.w;
-    });
-    if (p->batch_budget <= 0) {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
-        p->batch_budget = (int64_t)std::min<size_t>(fr / 2, (size_t)8 << 30);
-    }
-    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
-    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
-    constexpr int kMaxBatchS = 16384;
-    const int64_t lane_budget = p->batch_budget / kBatchLanes;
-    ls_status lst = lanes_begin(p);
-    if (lst != LS_OK) return lst;
+    if (p->batch_budget <= 0) init_batch_budget(p);
+    std::vector<ClassSpec> classes;
+    std::vector<LaunchSpec> launches;
+    ls_status st = split_batch(p, nseries, offsets, f0, df, nf, out_offsets, eps,
+                               p->batch_budget / kBatchLanes, classes, launches);
+    if (st != LS_OK) return st;
+    std::vector<ls_plan_s *> subs(classes.size(), nullptr);
+    for (size_t c = 0; c < classes.size(); ++c)
+        if ((st = batch_class(p, classes[c].pp, classes[c].nf_max, &subs[c])) != LS_OK) return st;
+    if ((st = lanes_begin(p)) != LS_OK) return st;
     LanesJoin join{p};
     int lane = 0;
-    size_t i = 0;
-    while (i < items.size()) {
-        // one class
-        size_t j = i;
-        int64_t nf_max = 0;
-        while (j < items.size() && items[j].pp.n == items[i].pp.n && items[j].pp.n1 == items[i].pp.n1 &&
-               items[j].pp.w == items[i].pp.w && items[j].pp.beta == items[i].pp.beta) {
-            nf_max = std::max(nf_max, nf[items[j].s]);
-            ++j;
-        }
-        ls_plan_s *sub = nullptr;
-        ls_status st = batch_class(p, items[i].pp, nf_max, &sub);
+    for (const LaunchSpec &L : launches) {
+        st = (p->prec == LS_FP32)
+                 ? batch_launch<float>(p, lane, subs[L.cls], L.descs, L.points, L.max_nd, t, y, dy,
+                                       power, 0, norm)
+                 : batch_launch<double>(p, lane, subs[L.cls], L.descs, L.points, L.max_nd, t, y, dy,
+                                        power, 0, norm);
         if (st != LS_OK) return st;
-        // launches within the budget
-        size_t k = i;
-        while (k < j) {
-            std::vector<SeriesDesc> descs;
-            int64_t points = 0, max_nd = 0;
-            while (k < j && (int)descs.size() < kMaxBatchS) {
-                const int64_t s = items[k].s;
-                const int64_t nd = offsets[s + 1] - offsets[s];
-                const int64_t bytes = (int64_t)(3 * (size_t)items[k].pp.n * cx * (descs.size() + 1) +
-                                                4 * recb * (size_t)(points + nd));
-                if (!descs.empty() && bytes > lane_budget) break;
-                descs.push_back(make_series(offsets[s], points, nd, out_offsets[s], nf[s], f0[s], df[s]));
-                points += nd;
-                max_nd = std::max(max_nd, nd);
-                ++k;
-            }
-            st = (p->prec == LS_FP32)
-                     ? batch_launch<float>(p, lane, sub, descs, points, max_nd, t, y, dy, power, 0, norm)
-                     : batch_launch<double>(p, lane, sub, descs, points, max_nd, t, y, dy, power, 0, norm);
-            if (st != LS_OK) return st;
-            lane = (lane + 1) % kBatchLanes;
-        }
-        i = j;
+        lane = (lane + 1) % kBatchLanes;
     }
     return LS_OK;
 }
@@ -1130,11 +1326,7 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     if (st != LS_OK) return st;
     ls_plan_s *sub = nullptr;
     if ((st = batch_class(p, pp, nf, &sub)) != LS_OK) return st;
-    if (p->batch_budget <= 0) {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
-        p->batch_budget = (int64_t)std::min<size_t>(fr / 2, (size_t)8 << 30);
-    }
+    if (p->batch_budget <= 0) init_batch_budget(p);
     const size_t cx = p->prec == LS_FP32 ? 8 : 16;
     const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
     constexpr int kMaxBatchS = 16384;
@@ -1165,6 +1357,133 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
         lane = (lane + 1) % kBatchLanes;
         s0 += S;
     }
+    return LS_OK;
+}
+
+ls_status ls_batch_prepare(ls_plan_t p, ls_batch_t *out, int64_t nseries, const int64_t *offsets,
+                           const double *f0, const double *df, const int64_t *nf,
+                           const int64_t *out_offsets, double eps, int norm)
+{
+    if (!out) return LS_ERR_ARG;
+    *out = nullptr;
+    if (!p || nseries < 1 || !offsets || !f0 || !df || !nf || !out_offsets) return LS_ERR_ARG;
+    ls_status st = check_batch_call(p, eps, norm);
+    if (st != LS_OK) return st;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (p->batch_budget <= 0) init_batch_budget(p);
+    std::vector<ClassSpec> classes;
+    std::vector<LaunchSpec> launches;
+    st = split_batch(p, nseries, offsets, f0, df, nf, out_offsets, eps,
+                     p->batch_budget / kBatchLanes, classes, launches);
+    if (st != LS_OK) return st;
+    ls_batch_s *b = new (std::nothrow) ls_batch_s();
+    if (!b) return LS_ERR_NOMEM;
+    b->plan = p;
+    b->norm = norm;
+    return finish_prepare(p, b, classes, launches, 0, out);
+}
+
+ls_status ls_batch_prepare_shared(ls_plan_t p, ls_batch_t *out, int64_t nseries, int64_t nd,
+                                  double f0, double df, int64_t nf, double eps, int norm)
+{
+    if (!out) return LS_ERR_ARG;
+    *out = nullptr;
+    if (!p || nseries < 1 || nd < 2 || nf < 1) return LS_ERR_ARG;
+    if (!(df > 0.0) || !isfinite(df) || !isfinite(f0)) return LS_ERR_ARG;
+    ls_status st = check_batch_call(p, eps, norm);
+    if (st != LS_OK) return st;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    PlanParams pp;
+    pp.upsampling = p->upsampling;
+    pp.cols = p->cols_req;
+    pp.maxr = p->maxr_req;
+    st = ls_choose_params(nf, eps, p->prec, nd, p->upsampling, &pp.w, &pp.beta, &pp.n, &pp.n1,
+                          &pp.n2, &pp.sigma);
+    if (st != LS_OK) return st;
+    if (p->batch_budget <= 0) init_batch_budget(p);
+    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
+    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    const int64_t lane_budget = p->batch_budget / kBatchLanes;
+    std::vector<ClassSpec> classes{ClassSpec{pp, nf}};
+    std::vector<LaunchSpec> launches;
+    for (int64_t s0 = 0; s0 < nseries;) {
+        int64_t S = 1;     // series per launch within the lane budget (as ls_execute_batch_shared)
+        while (S < 16384 && s0 + S < nseries &&
+               (int64_t)((size_t)pp.n * cx * (S + 3) + 4 * recb * (size_t)nd * (S + 1)) <=
+                   lane_budget)
+            ++S;
+        LaunchSpec L;
+        L.cls = 0;
+        L.points = S * nd;
+        L.max_nd = nd;
+        for (int64_t k = 0; k < S; ++k) {
+            SeriesDesc d = make_series(0, k * nd, nd, (s0 + k) * nf, nf, f0, df);
+            d.y_off = (s0 + k) * nd;
+            L.descs.push_back(d);
+        }
+        launches.push_back(std::move(L));
+        s0 += S;
+    }
+    ls_batch_s *b = new (std::nothrow) ls_batch_s();
+    if (!b) return LS_ERR_NOMEM;
+    b->plan = p;
+    b->norm = norm;
+    return finish_prepare(p, b, classes, launches, 1, out);
+}
+
+ls_status ls_batch_run(ls_batch_t b, const double *t, const double *y, const double *dy,
+                       double *power)
+{
+    if (!b || !b->plan || !t || !y || !power) return LS_ERR_ARG;
+    ls_plan_s *p = b->plan;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (!is_device_pointer(t) || !is_device_pointer(y) || !is_device_pointer(power) ||
+        (dy && !is_device_pointer(dy)))
+        return LS_ERR_ARG;
+    ls_status st = lanes_begin(p);
+    if (st != LS_OK) return st;
+    LanesJoin join{p};
+    for (const PreparedLaunch &L : b->launches) {
+        Batch bt;
+        bt.S = L.S;
+        bt.many = b->desc_all + L.desc_off;
+        bt.one = L.one;
+        const int nred = batch_nred(p, L.S, L.max_nd);
+        const ls_plan_s *sub = b->subs[L.cls];
+        cudaStream_t ls = p->lane_stream[L.lane];
+        st = (p->prec == LS_FP32)
+                 ? enqueue_batch<float>(b->bws[L.lane], ls, sub, bt, L.max_nd, nred, t, y, dy, power,
+                                        L.shared, b->norm)
+                 : enqueue_batch<double>(b->bws[L.lane], ls, sub, bt, L.max_nd, nred, t, y, dy,
+                                         power, L.shared, b->norm);
+        if (st != LS_OK) return st;
+    }
+    return LS_OK;
+}
+
+ls_status ls_batch_describe(ls_batch_t b, int64_t *launches, int64_t *classes, int64_t *bytes)
+{
+    if (!b || !b->plan) return LS_ERR_ARG;
+    if (launches) *launches = (int64_t)b->launches.size();
+    if (classes) *classes = (int64_t)b->subs.size();
+    if (bytes) *bytes = b->bytes;
+    return LS_OK;
+}
+
+ls_status ls_batch_destroy(ls_batch_t b)
+{
+    if (!b) return LS_ERR_ARG;
+    if (ls_plan_s *p = b->plan) {
+        DeviceGuard guard(p->device);
+        cudaStreamSynchronize(p->stream);
+        lanes_sync(p);
+        batch_release(b);
+        p->batches.erase(std::remove(p->batches.begin(), p->batches.end(), b), p->batches.end());
+    }
+    delete b;
     return LS_OK;
 }
 
@@ -1311,6 +1630,15 @@ ls_status ls_destroy(ls_plan_t p)
     {
         DeviceGuard guard(p->device);
         cudaStreamSynchronize(p->stream);
+        // batches still prepared on this plan lose their device memory and
+        // become inert handles (ls_batch_run refuses them; ls_batch_destroy
+        // only frees the handle)
+        lanes_sync(p);
+        for (ls_batch_s *b : p->batches) {
+            batch_release(b);
+            b->plan = nullptr;
+        }
+        p->batches.clear();
         destroy_timing(p);
         batch_free(p);
         plan_free(p);

@@ -171,3 +171,20 @@ def test_plan_options_are_validated_before_any_device_work(opt):
     with pytest.raises(nl.LSError) as e:
         nl.ls_plan(1000, 12_000, 1e-6, nl.LS_FP32, **opt)
     assert e.value.status == 1
+
+
+def test_prepared_batch_entry_points_reject_null_handles():
+    # argument checks only: no device is touched
+    import paper_2409_08090_gb300 as nl
+    lib = nl.load_library()
+    assert lib.ls_batch_run(None, None, None, None, None) == 1
+    assert lib.ls_batch_destroy(None) == 1
+    assert lib.ls_batch_describe(None, None, None, None) == 1
+    h = ctypes.c_void_p(1234)
+    assert lib.ls_batch_prepare(None, ctypes.byref(h), 1, None, None, None, None, None,
+                                1e-6, 0) == 1
+    assert h.value is None
+    h = ctypes.c_void_p(1234)
+    assert lib.ls_batch_prepare_shared(None, ctypes.byref(h), 4, 100, 0.1, 0.01, 1000,
+                                       1e-6, 0) == 1
+    assert h.value is None
