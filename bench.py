@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--no-fft-reference", action="store_true")
     ap.add_argument("--upsampling", type=float, default=0.0,
                     help="fine-grid upsampling: 0 (plan chooses), 2.0 or 1.5")
+    ap.add_argument("--batch-mode", default="graph", choices=["graph", "prepared", "direct"],
+                    help="batch workloads: replay a recorded graph of a prepared batch, run the "
+                         "prepared batch, or call ls_execute_batch(_shared) each step")
     ap.add_argument("--serving-results", default="host", choices=["host", "device"],
                     help="serving: deliver results as host arrays or device tensor views")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -335,6 +338,7 @@ def run_ours(args):
     clocks.start()
     barrier(pg)
     torch.cuda.synchronize()
+    k0 = nl.ls_kernel_launches()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))                 # evict L2 (outside the step's events)
@@ -342,6 +346,7 @@ def run_ours(args):
         plan.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
         ev1[i].record()
     torch.cuda.synchronize()
+    kernels = nl.ls_kernel_launches() - k0
     barrier(pg)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -537,7 +542,7 @@ def run_ours(args):
         "stage_ms": avg, "stage_gbs": kern_gbs,
         "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
         "graph_replay": graph, "fft_reference": fft_ref,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": kernels,
         "clocks": clk, "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -599,13 +604,51 @@ def run_batch(args):
     shared = args.workload == "uniform_batch"
     nd0 = int(offsets[1] - offsets[0])
 
-    def step():
+    def direct():
         if shared:
             plan.execute_shared(t, y.view(ns, nd0), dy, float(f0[0]), float(df[0]), int(nf[0]),
                                 out=out.view(ns, int(nf[0])), sync=False)
         else:
             plan.execute_batch(t, y, dy, offsets, f0, df, nf, out=out, sync=False)
 
+    # prepared layout (host work once) and its recorded graph
+    tp0 = time.perf_counter()
+    if shared:
+        pb = plan.prepare_shared(ns, nd0, float(f0[0]), float(df[0]), int(nf[0]))
+        yv, outv = y.view(ns, nd0), out.view(ns, int(nf[0]))
+    else:
+        pb = plan.prepare_batch(offsets, f0, df, nf)
+        yv, outv = y, out
+    prepare_s = time.perf_counter() - tp0
+
+    def prepared():
+        pb.run(t, yv, dy, out=outv, sync=False)
+
+    k0 = nl.ls_kernel_launches()
+    prepared()
+    kernels_per_step = nl.ls_kernel_launches() - k0
+    graph = pb.graph(t, yv, dy, out=outv)
+    modes = {"direct": direct, "prepared": prepared, "graph": graph.replay}
+    step = modes[args.batch_mode]
+
+    # the other modes, briefly (3 steps each, L2 flushed), for the record
+    mode_rates = {}
+    for name, fn in modes.items():
+        fn()
+        torch.cuda.synchronize()
+        ms, host = [], []
+        for i in range(3):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            h0 = time.perf_counter()
+            fn()
+            host.append((time.perf_counter() - h0) * 1e3)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        mode_rates[name] = {"periodograms_per_s": ns / (statistics.median(ms) * 1e-3),
+                            "ms": statistics.median(ms), "host_ms": statistics.median(host)}
     for _ in range(args.warmup):
         step()
     if nl.ls_sync(plan.handle) != 0:
@@ -631,6 +674,7 @@ def run_batch(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = allreduce_max(sum(step_ms), pg, device)
     value = world * ns * args.steps / (total_ms * 1e-3)
+    pb_info = pb.describe()
     P_gpu = out.cpu().numpy()
     out_off = np.zeros(ns, dtype=np.int64)
     out_off[1:] = np.cumsum(nf)[:-1]
@@ -672,7 +716,11 @@ def run_batch(args):
         dt = allreduce_max(time.perf_counter() - t0, pg, device)
         e2e = {"value": world * ns * nsteps / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(8 * (th.size + yh.size + dyh.size)), "d2h_bytes_per_step": int(8 * nf.sum()),
-               "steps": nsteps, "host_buffers": "pinned", "api": "Plan.execute_batch"}
+               "steps": nsteps, "host_buffers": "pinned",
+               "api": {"graph": "GraphedBatch.replay", "prepared": "PreparedBatch.run",
+                       "direct": "Plan.execute_batch"}[args.batch_mode]}
+    del graph
+    pb.close()
     plan.close()
     if rank != 0:
         return 0
@@ -711,7 +759,9 @@ def run_batch(args):
                    "l2": "flushed between steps (256 MB write, untimed)",
                    "parallelism": f"independent batches per GPU x{world}"},
         "roofline": roofline, "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": None, "clocks": clk, "wall_s": wall,
+        "gpu_launches": kernels_per_step * args.steps, "clocks": clk, "wall_s": wall,
+        "batch_mode": args.batch_mode, "modes": mode_rates, "prepare_s": prepare_s,
+        "prepared_layout": pb_info,
     }
     print(json.dumps(line), flush=True)
     if pg:

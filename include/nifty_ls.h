@@ -273,6 +273,11 @@ ls_status ls_batch_describe(ls_batch_t batch, int64_t *launches, int64_t *classe
                             int64_t *bytes);
 ls_status ls_batch_destroy(ls_batch_t batch);
 
+/* Pipeline kernels this process has enqueued through the library so far
+ * (recorded into a graph counts once, at recording; replays do not count):
+ * the difference around a call is the number of kernels the call launched. */
+ls_status ls_kernel_launches(int64_t *count);
+
 /* Wait for the plan's stream; return and clear the device-side status of every
  * execute since the previous ls_sync (LS_ERR_ARG for invalid values,
  * LS_ERR_DEGENERATE for a constant series, else LS_OK). */

@@ -23,7 +23,8 @@ __all__ = ["LSError", "Plan", "GraphedExecute", "lombscargle", "load_library", "
            "ls_destroy", "ls_set_stream", "ls_execute_noalloc", "ls_execute_batch", "ls_execute_batch_shared", "ls_plan_describe", "ls_status_str",
            "ls_choose_params", "ls_kernel_ft", "PlanInfo", "PlanOpts", "ls_timing_enable",
            "ls_timing_report", "STAGE_NAMES", "PreparedBatch", "GraphedBatch", "ls_batch_prepare",
-           "ls_batch_prepare_shared", "ls_batch_run", "ls_batch_describe", "ls_batch_destroy"]
+           "ls_batch_prepare_shared", "ls_batch_run", "ls_batch_describe", "ls_batch_destroy",
+           "ls_kernel_launches"]
 
 LS_FP64, LS_FP32 = 0, 1
 LS_NORM_STANDARD, LS_NORM_MODEL, LS_NORM_LOG, LS_NORM_PSD = range(4)
@@ -93,6 +94,7 @@ _SIGS = {
     "ls_batch_describe": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                          ctypes.POINTER(_i64)]),
     "ls_batch_destroy": (ctypes.c_int, [_c_void_p]),
+    "ls_kernel_launches": (ctypes.c_int, [ctypes.POINTER(_i64)]),
     "ls_timing_enable": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "ls_timing_report": (ctypes.c_int, [_c_void_p, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
 }
@@ -270,6 +272,13 @@ def ls_batch_describe(batch: int) -> dict:
 
 def ls_batch_destroy(batch: int) -> int:
     return load_library().ls_batch_destroy(_c_void_p(batch))
+
+
+def ls_kernel_launches() -> int:
+    """Pipeline kernels enqueued through the library by this process so far."""
+    c = _i64()
+    _check(load_library().ls_kernel_launches(ctypes.byref(c)), "ls_kernel_launches")
+    return c.value
 
 
 def ls_timing_enable(plan: int, enable: bool = True) -> None:

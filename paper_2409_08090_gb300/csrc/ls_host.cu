@@ -132,13 +132,24 @@ bool radix_schedule(int L, std::vector<int> &rad, int maxr = 16);
 // radix schedule (not the verified stage tables).
 bool passA_column_fits(int64_t N2, int prec)
 {
-    std::vector<int> rad;
-    if (N2 > (1 << 20) || !radix_schedule((int)N2, rad)) return false;
+    // the last radix of radix_schedule(N2) without building the schedule (this
+    // runs for every candidate split of every series of a batch call)
+    if (N2 > (1 << 20) || N2 < 2) return false;
+    int x = (int)N2, nst = 0, last = 0;
+    while (x % 9 == 0) { x /= 9; ++nst; last = 9; }
+    while (x % 3 == 0) { x /= 3; ++nst; last = 3; }
+    while (x % 5 == 0) { x /= 5; ++nst; last = 5; }
+    int k = 0;
+    while ((1 << k) < x) ++k;
+    if ((1 << k) != x || k == 0) return false;
+    if (k % 4) { ++nst; last = 1 << (k % 4); }
+    if (k >= 4) { nst += k / 4; last = 16; }
+    if (nst > kMaxStages) return false;
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     const size_t nhi = (size_t)(N2 + 63) / 64;
     const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
     const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
-                         sizeof(int) * (size_t)(N2 / rad.back()) + 2048;
+                         sizeof(int) * (size_t)(N2 / last) + 2048;
     return bytes <= kSmemOptinBytes;
 }
 
@@ -224,31 +235,41 @@ ls_status choose_grid(int64_t nf, double sigma, int w, int prec, int64_t *n_out,
     int64_t nmin = (int64_t)ceil(sigma * (double)nf - 1e-9);
     if (nmin < 2 * w) nmin = 2 * w;
     if (nmin < 64) nmin = 64;
+    // Candidates c 2^k in increasing order (the smallest untried multiple of
+    // each c); the first with an admissible split is the smallest admissible n
+    // (different c never give the same n).  Called for every series of a
+    // batch call, so only the candidates up to the answer are split.
+    const int64_t nlimit = (int64_t)n1max * n2max;
+    int64_t cand[11];
+    for (int i = 0; i < 11; ++i) {
+        cand[i] = odd[i];
+        while (cand[i] < nmin) cand[i] *= 2;
+    }
     int64_t best_n = -1;
     int best_n1 = 0;
-    for (int c : odd) {
-        int64_t n = c;
-        while (n < nmin) n *= 2;
-        for (; n <= (int64_t)n1max * n2max; n *= 2) {
-            // most balanced admissible split of this n
-            int pick = -1;
-            double bal = 1e300;
-            for (int k1 = ilog2_exact(kMinN1); ((int64_t)1 << k1) <= n1max; ++k1) {
-                const int64_t N1 = (int64_t)1 << k1;
-                if (n % N1) break;
-                const int64_t N2 = n / N1;
-                if (N2 > n2max || N2 < 2 || (N2 & 1) || !passA_column_fits(N2, prec)) continue;
-                const double b = fabs(log((double)N1) - log((double)N2));
-                if (b < bal) { bal = b; pick = (int)N1; }
-            }
-            if (pick > 0) {
-                if (best_n < 0 || n < best_n || (n == best_n && pick > best_n1)) {
-                    best_n = n;
-                    best_n1 = pick;
-                }
-                break;
-            }
+    for (;;) {
+        int i = -1;
+        for (int j = 0; j < 11; ++j)
+            if (cand[j] <= nlimit && (i < 0 || cand[j] < cand[i])) i = j;
+        if (i < 0) break;
+        const int64_t n = cand[i];
+        // most balanced admissible split of this n
+        int pick = -1;
+        double bal = 1e300;
+        for (int k1 = ilog2_exact(kMinN1); ((int64_t)1 << k1) <= n1max; ++k1) {
+            const int64_t N1 = (int64_t)1 << k1;
+            if (n % N1) break;
+            const int64_t N2 = n / N1;
+            if (N2 > n2max || N2 < 2 || (N2 & 1) || !passA_column_fits(N2, prec)) continue;
+            const double b = fabs(log((double)N1) - log((double)N2));
+            if (b < bal) { bal = b; pick = (int)N1; }
         }
+        if (pick > 0) {
+            best_n = n;
+            best_n1 = pick;
+            break;
+        }
+        cand[i] *= 2;
     }
     if (best_n < 0) return LS_ERR_UNSUPPORTED;
     *n_out = best_n;
@@ -1484,6 +1505,13 @@ ls_status ls_batch_destroy(ls_batch_t b)
         p->batches.erase(std::remove(p->batches.begin(), p->batches.end(), b), p->batches.end());
     }
     delete b;
+    return LS_OK;
+}
+
+ls_status ls_kernel_launches(int64_t *count)
+{
+    if (!count) return LS_ERR_ARG;
+    *count = (int64_t)pipeline_kernel_count();
     return LS_OK;
 }
 

@@ -140,6 +140,9 @@ void decompose_double(double x, uint64_t &m, int &e, int &neg);
 // `ev`, if not null, holds LS_NUM_STAGES + 1 events recorded at the stage
 // boundaries.  `capacity` = points the record arrays hold; `max_nd` = largest
 // series of the batch; nred = reduction blocks per series.
+// Pipeline kernels enqueued (or recorded into graphs) by this process.
+long long pipeline_kernel_count();
+
 template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &b, int64_t max_nd, const double *t, const double *y,

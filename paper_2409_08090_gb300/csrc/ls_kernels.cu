@@ -17,6 +17,7 @@
 // The FFT is four-step: m = a + N1 b; pass A transforms each column a over b
 // (length N2) and applies exp(2 pi i a d / n); pass B transforms each row d over
 // a (length N1) giving mode k = d + N2 c, k' = k or k - n.
+#include <atomic>
 #include <math.h>
 #include <string.h>
 
@@ -1662,12 +1663,18 @@ static cudaError_t allow_max_dynamic_smem(const void *fn)
     return cudaSuccess;
 }
 
+// Kernels launch_pipeline has enqueued (or recorded into graphs) in this process.
+static std::atomic<long long> g_pipeline_kernels{0};
+
+long long pipeline_kernel_count() { return g_pipeline_kernels.load(std::memory_order_relaxed); }
+
 template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &bt, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
                             cudaStream_t st, cudaEvent_t *ev, int shared, int mode)
 {
+    int nk = 4;    // kernels enqueued: stats, points, scan, scatter, then the passes
     const int nofit = (mode & kModeNoFit) ? 1 : 0;
     const int center = (!nofit || !(mode & kModeNoCenter)) ? 1 : 0;
     cudaError_t err;
@@ -1760,6 +1767,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         const bool loop = gyA < A.ny;
+        ++nk;
         if (cs > 1)
             err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true>, A)
                        : cudaLaunchKernelEx(&cfg, k_passA<T, true>, A);
@@ -1778,6 +1786,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         const int gcap = (target + g.nbins - 1) / g.nbins;
         if (gyS > gcap) gyS = gcap;
         k_passA_group<T><<<dim3(g.nbins, gyS), kThreadsA, smS, st>>>(A);
+        ++nk;
     }
 
     if (ev) cudaEventRecord(ev[3], st);
@@ -1832,8 +1841,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
         }
     }
+    nk += shared ? 2 : 1;
     if (ev) cudaEventRecord(ev[4], st);
-    return cudaGetLastError();
+    err = cudaGetLastError();
+    if (err == cudaSuccess) g_pipeline_kernels.fetch_add(nk, std::memory_order_relaxed);
+    return err;
 }
 
 template <typename T>
