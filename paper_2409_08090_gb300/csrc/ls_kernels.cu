@@ -992,7 +992,8 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
     }
 }
 
-// One instance per block (blockIdx.y), the usual launch.
+// One instance per block (blockIdx.y), the usual launch (two blocks per SM:
+// with three, 80 registers, small grids ran 4-12% slower).
 template <typename T, bool kCluster>
 __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 {
@@ -1004,8 +1005,11 @@ __global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
 // launch has rows of blocks); the tables depend only on the columns and are
 // built once.  An instance skipped without a fitted mean is skipped by the
 // whole block (and cluster), so the barriers stay uniform.
-template <typename T, bool kCluster>
-__global__ void __launch_bounds__(kThreadsA, 2) k_passA_loop(PassAArgs<T> A)
+// kMinB: blocks per SM the registers are sized for (2: 128 registers; 3: 80,
+// launched only where the shared memory lets three blocks share an SM, see
+// blocks_per_sm).
+template <typename T, bool kCluster, int kMinB>
+__global__ void __launch_bounds__(kThreadsA, kMinB) k_passA_loop(PassAArgs<T> A)
 {
     bool first = true;
     for (int y = blockIdx.y; y < A.ny; y += gridDim.y) {
@@ -1238,8 +1242,8 @@ template <> struct PowerOut<float> {
 
 // kStage is PassBArgs::stage as a template parameter: each launch carries only
 // its own code (fewer instruction-fetch stalls than one kernel for all stages).
-template <typename T, int kStage>
-__global__ void __launch_bounds__(kThreadsB, 2) k_passB(PassBArgs<T> B)
+template <typename T, int kStage, int kMinB>
+__global__ void __launch_bounds__(kThreadsB, kMinB) k_passB(PassBArgs<T> B)
 {
     using V = Cplx<T>;
     using F = typename FftOf<T>::type;   // the transform's type (double-float for FP64)
@@ -1571,6 +1575,17 @@ size_t point_record_bytes()
     return sizeof(uint32_t) + sizeof(T) + 2 * sizeof(Cplx<T>);
 }
 
+// Blocks of a pass kernel whose dynamic shared memory is smem that fit one
+// SM's shared memory (228 KB, 1 KB reserved per block).  Where three fit, the
+// loop form of pass A and pass B are launched compiled for three blocks per SM
+// (80 registers): on GB300 that ran ragged batches 4-7% and pass B of 3.7e5-
+// and 4.7e6-cell grids 8-14% faster; where only two fit, the 128-register form
+// keeps its registers (pass B of a 1.9e7-cell grid ran 6% slower with 80).
+static int blocks_per_sm(size_t smem)
+{
+    return (int)((size_t)228 * 1024 / (smem + 1024));
+}
+
 size_t passA_smem_bytes(const Geometry &g, size_t cx, int cs)
 {
     const size_t nhi = (size_t)(g.N2 + 63) / 64;
@@ -1715,9 +1730,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     {
-        const void *fns[4] = {(const void *)k_passA<T, false>, (const void *)k_passA<T, true>,
-                              (const void *)k_passA_loop<T, false>,
-                              (const void *)k_passA_loop<T, true>};
+        const void *fns[6] = {(const void *)k_passA<T, false>, (const void *)k_passA<T, true>,
+                              (const void *)k_passA_loop<T, false, 2>,
+                              (const void *)k_passA_loop<T, true, 2>,
+                              (const void *)k_passA_loop<T, false, 3>,
+                              (const void *)k_passA_loop<T, true, 3>};
         for (const void *f : fns)
             if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
     }
@@ -1755,7 +1772,15 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     int groupA = (int)((kGroupSmemBudget - tabA) / colA);
     groupA = groupA > 8 ? 8 : groupA;
     const int ninst = shared ? S : (nofit ? 2 * S : 3 * S);
-    const bool grouped = cs == 1 && g.BA >= 2 && groupA >= 2 && ninst >= 2;
+    // a launch whose instances all fit the two-block budget takes them in one
+    // block iteration (2 blocks per SM then)
+    if (ninst <= 8 && groupA < ninst && (size_t)ninst * colA + tabA <= 100 * 1024) groupA = ninst;
+    // (one series' 3 transforms are grouped only when the grid has a column
+    // block per SM: on narrower grids 3 rows of blocks give the launch the width
+    // it lacks, measured 18 vs 37 us for pass A of a 1.8e4-cell grid, while 256
+    // column blocks of FP64 ran 17% faster grouped)
+    const bool grouped = cs == 1 && g.BA >= 2 && groupA >= 2 && ninst >= 2 &&
+                         (ninst > 3 || g.nbins >= nsm);
     if (grouped) A.ny = shared ? 2 : 0;
     int gyA = (target + g.nbins - 1) / g.nbins;
     if (gyA < 3) gyA = 3;
@@ -1774,13 +1799,17 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         const bool loop = gyA < A.ny;
+        const bool three = blocks_per_sm(smA) >= 3;
         ++nk;
-        if (cs > 1)
-            err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true>, A)
-                       : cudaLaunchKernelEx(&cfg, k_passA<T, true>, A);
+        if (!loop)
+            err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA<T, true>, A)
+                         : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
+        else if (three)
+            err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true, 3>, A)
+                         : cudaLaunchKernelEx(&cfg, k_passA_loop<T, false, 3>, A);
         else
-            err = loop ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, false>, A)
-                       : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
+            err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true, 2>, A)
+                         : cudaLaunchKernelEx(&cfg, k_passA_loop<T, false, 2>, A);
         if (err != cudaSuccess) return err;
     }
     if (grouped) {
@@ -1815,8 +1844,13 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // arithmetic uses 1e-15).
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
-    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 0>)) != cudaSuccess) return err;
-    if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 1>)) != cudaSuccess) return err;
+    {
+        const void *fns[4] = {(const void *)k_passB<T, 0, 2>, (const void *)k_passB<T, 1, 2>,
+                              (const void *)k_passB<T, 0, 3>, (const void *)k_passB<T, 1, 3>};
+        for (const void *f : fns)
+            if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
+    }
+    const bool threeB = blocks_per_sm(smB) >= 3;
     if ((err = allow_max_dynamic_smem((const void *)k_passB_series<T>)) != cudaSuccess) return err;
     B.nser = S;
     int gyB = (target + g.N2 - 1) / g.N2;
@@ -1824,7 +1858,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     if (gyB > S) gyB = S;
     if (shared) {
         B.stage = 1;
-        k_passB<T, 1><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        if (threeB) k_passB<T, 1, 3><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        else k_passB<T, 1, 2><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
         B.stage = 2;
         B.group = passB_group(g, sizeof(Cplx<T>));
         int gy2 = (S + B.group - 1) / B.group;
@@ -1845,7 +1880,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             k_passB_group<T><<<dim3(g.N2, gy2), kThreadsB,
                                passB_group_smem_bytes(g, sizeof(Cplx<T>), GB, nr), st>>>(B);
         } else {
-            k_passB<T, 0><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+            if (threeB) k_passB<T, 0, 3><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+            else k_passB<T, 0, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
         }
     }
     nk += shared ? 2 : 1;
