@@ -702,23 +702,80 @@ def run_batch(args):
         tp = torch.from_numpy(th).pin_memory()
         yp = torch.from_numpy(yh).pin_memory()
         dp = torch.from_numpy(dyh).pin_memory()
-        ph = torch.empty(out.numel(), dtype=torch.float64).pin_memory()
-        nsteps = max(2, min(args.steps, 5))
+        phs = [torch.empty(out.numel(), dtype=torch.float64).pin_memory() for _ in range(2)]
+        # serial: copy in, compute, copy out and wait, step after step
+        nser = 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(nsteps):
+        for _ in range(nser):
             t.copy_(tp, non_blocking=True)
             y.copy_(yp, non_blocking=True)
             dy.copy_(dp, non_blocking=True)
             step()
-            ph.copy_(out, non_blocking=True)
+            phs[0].copy_(out, non_blocking=True)
             torch.cuda.synchronize()
+        dt_serial = allreduce_max(time.perf_counter() - t0, pg, device)
+        # pipelined over two buffer sets: step i+1's inputs go in and step i-1's
+        # results come out (copy streams) while step i computes
+        t1, y1, dy1, o1 = (a.clone() for a in (t, y, dy, out))   # valid values for recording
+        sets = [(t, y, dy, out), (t1, y1, dy1, o1)]
+        views = [(yv, outv),
+                 (y1.view(ns, nd0), o1.view(ns, int(nf[0]))) if shared else (y1, o1)]
+        graph1 = pb.graph(t1, views[1][0], dy1, out=views[1][1]) \
+            if args.batch_mode == "graph" else None
+
+        def run_set(k):
+            tk, _, dyk, _ = sets[k]
+            yk, ok = views[k]
+            if args.batch_mode == "graph":
+                (graph if k == 0 else graph1).replay()
+            elif args.batch_mode == "prepared":
+                pb.run(tk, yk, dyk, out=ok, sync=False)
+            elif shared:
+                plan.execute_shared(tk, yk, dyk, float(f0[0]), float(df[0]), int(nf[0]), out=ok,
+                                    sync=False)
+            else:
+                plan.execute_batch(tk, yk, dyk, offsets, f0, df, nf, out=ok, sync=False)
+
+        nsteps = max(4, min(args.steps, 8))
+        cs = torch.cuda.current_stream(device)
+        h2d, d2h = torch.cuda.Stream(device=device), torch.cuda.Stream(device=device)
+        ev_in, ev_done, ev_out = ([torch.cuda.Event() for _ in range(nsteps)] for _ in range(3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nsteps):
+            k = i % 2
+            tk, yk, dyk, ok = sets[k]
+            with torch.cuda.stream(h2d):
+                if i >= 2:
+                    h2d.wait_event(ev_done[i - 2])     # step i-2 has read this set's inputs
+                tk.copy_(tp, non_blocking=True)
+                yk.copy_(yp, non_blocking=True)
+                dyk.copy_(dp, non_blocking=True)
+                ev_in[i].record(h2d)
+            cs.wait_event(ev_in[i])
+            if i >= 2:
+                cs.wait_event(ev_out[i - 2])           # this set's results are copied out
+            run_set(k)
+            ev_done[i].record(cs)
+            with torch.cuda.stream(d2h):
+                d2h.wait_event(ev_done[i])
+                phs[k].copy_(ok, non_blocking=True)
+                ev_out[i].record(d2h)
+        torch.cuda.synchronize()
         dt = allreduce_max(time.perf_counter() - t0, pg, device)
+        if nl.ls_sync(plan.handle) != 0:
+            raise SystemExit("device status after the e2e steps")
         e2e = {"value": world * ns * nsteps / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(8 * (th.size + yh.size + dyh.size)), "d2h_bytes_per_step": int(8 * nf.sum()),
                "steps": nsteps, "host_buffers": "pinned",
                "api": {"graph": "GraphedBatch.replay", "prepared": "PreparedBatch.run",
-                       "direct": "Plan.execute_batch"}[args.batch_mode]}
+                       "direct": "Plan.execute_batch"}[args.batch_mode],
+               "pipelining": "two device buffer sets; host-to-device and device-to-host copies on "
+                             "their own streams overlap the neighbouring steps' compute",
+               "serial": {"value": world * ns * nser / dt_serial, "steps": nser,
+                          "pipelining": "none (copy in, compute, copy out, wait)"}}
+        del graph1
     del graph
     pb.close()
     plan.close()
