@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--batch-mode", default="graph", choices=["graph", "prepared", "direct"],
                     help="batch workloads: replay a recorded graph of a prepared batch, run the "
                          "prepared batch, or call ls_execute_batch(_shared) each step")
+    ap.add_argument("--serving-copy-limit", type=int, default=None,
+                    help="serving with host results: batches with at most this many output "
+                         "bytes are copied out per request, larger ones handed out as views")
     ap.add_argument("--serving-results", default="host", choices=["host", "device"],
                     help="serving: deliver results as host arrays or device tensor views")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -851,11 +854,14 @@ def run_serving(args):
     duration = 2.0 * args.batch_scale
     srv = PeriodogramServer(memory_budget=60 << 30, streams=2, max_batch=4096,
                             results=args.serving_results)
+    if args.serving_copy_limit is not None:
+        srv.copy_limit = int(args.serving_copy_limit)
     # warm the plans and grid classes once
     warm = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, p) for s in pool[:32]
             for p in ("fp32", "fp64")]
     for f in warm:
         f.result(timeout=600)
+    del warm, f
     per_rate = {}
     runs = [(r, "mixed") for r in rates] + [(rates[-1], "fp32"), (4 * rates[-1], "fp32")]
     for rate, mix in runs:
@@ -867,9 +873,24 @@ def run_serving(args):
             precs = np.where(rng.random(n) < 0.5, "fp32", "fp64")
         else:
             precs = np.full(n, "fp32")
-        futs = []
         srv.completed.clear()
         t0 = time.perf_counter()
+        left = [n]
+        failures = []
+        all_done = threading.Event()
+        lock = threading.Lock()
+
+        def consume(f):
+            # the client reads each result as it arrives and then drops it
+            exc = f.exception()
+            if exc is not None:
+                failures.append(repr(exc))
+            elif args.serving_results == "host":
+                _ = float(f.result()[0])
+            with lock:
+                left[0] -= 1
+                if left[0] == 0:
+                    all_done.set()
 
         def client():
             for i in range(n):
@@ -877,13 +898,13 @@ def run_serving(args):
                 if delay > 0:
                     time.sleep(delay)
                 s = pool[picks[i]]
-                futs.append(srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, str(precs[i])))
+                srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, str(precs[i])).add_done_callback(consume)
 
         th = threading.Thread(target=client)
         th.start()
         th.join()
-        for f in futs:
-            f.result(timeout=600)
+        if not all_done.wait(timeout=600) or failures:
+            raise SystemExit(f"serving run at {rate}/s did not complete: {failures[:3]}")
         st = srv.stats()
         st["offered_rate"] = rate
         st["precisions"] = "50/50 fp32 eps 1e-6 / fp64 eps 1e-9" if mix == "mixed" else "fp32 eps 1e-6"
@@ -918,7 +939,7 @@ def run_serving(args):
         "config": {"workload": "serving: Poisson arrivals of ragged-mix series (Nd log-uniform "
                                "in [100, 1e5], Nf = 12 Nd), 50/50 FP32 eps 1e-6 / FP64 eps 1e-9, "
                                "60 GB admission budget, 2 streams",
-                   "results": args.serving_results,
+                   "results": args.serving_results, "copy_limit": srv.copy_limit,
                    "pool_series": len(pool), "duration_s": duration},
         "per_rate": per_rate,
         "plain_fp64_one_at_a_time": {"value_by_eps": plain, "unit": UNIT, "series": len(sample),

@@ -69,18 +69,25 @@ def test_results_in_the_mix_equal_results_alone(nl):
 
 
 def test_device_results_equal_host_results(nl):
+    # host results as views of the batch's pinned buffer (the default) and as
+    # per-request copies (copy_limit above every batch), and device results
     import torch
     from paper_2409_08090_gb300.serving import PeriodogramServer
     reqs = [W.ragged_series(2000 + i, nd_lo=100, nd_hi=3000) for i in range(10)]
     out = {}
-    for mode in ("host", "device"):
-        srv = PeriodogramServer(memory_budget=256 << 20, streams=2, max_batch=4, results=mode)
+    for mode, limit in (("host", 0), ("host_copies", 1 << 40), ("device", 0)):
+        srv = PeriodogramServer(memory_budget=256 << 20, streams=2, max_batch=4,
+                                results="device" if mode == "device" else "host")
+        srv.copy_limit = limit
         futs = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, "fp32", 1e-6) for s in reqs]
         out[mode] = [f.result(timeout=120) for f in futs]
         srv.close()
-    for s, a, b in zip(reqs, out["host"], out["device"]):
+    for s, a, c, b in zip(reqs, out["host"], out["host_copies"], out["device"]):
         assert isinstance(b, torch.Tensor) and b.is_cuda and b.shape == (s.nf,)
+        assert isinstance(a, np.ndarray) and a.shape == (s.nf,)
+        assert isinstance(c, np.ndarray) and c.flags.owndata
         assert_rerun_close(b.cpu().numpy(), a, "fp32")
+        assert_rerun_close(c, a, "fp32")
 
 
 def test_model_variants_in_the_mix(nl):
