@@ -128,11 +128,12 @@ typedef struct {
     uint64_t batch_workspace_bytes;
     /* Fine-grid columns per pass-A block: the spreader's tile is this many
      * columns of n2 cells, and the bin sort's bins are this many columns wide.
-     * 0 lets the plan choose (the widest of 8, 4, 2 whose two blocks fit an
-     * SM); 1, 2, 4 or 8 request a width.  A grid that cannot use the request
-     * (fewer than two bins, or a block beyond the opt-in shared memory) takes
-     * the automatic width; ls_plan_describe reports the width taken.  Batch
-     * classes apply the same rule to their own grids. */
+     * 0 lets the plan choose (FP32: the widest of 8, 4, 2 whose two blocks
+     * fit an SM; FP64: 2, else 1); 1, 2, 4 or 8 request a width.  A grid that
+     * cannot use the request (fewer than two bins, or a block beyond the
+     * opt-in shared memory) takes the automatic width; ls_plan_describe
+     * reports the width taken.  Batch classes apply the same rule to their
+     * own grids. */
     int32_t cols_per_block;
     /* Largest radix of the fine-grid FFT stages (each sub-FFT runs the odd
      * radices 9, 3, 5 first, then powers of two): 16 for radix-16 stages, 8
