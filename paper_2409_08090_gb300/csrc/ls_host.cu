@@ -119,8 +119,14 @@ namespace {
 constexpr int kTimingRing = 64;
 constexpr int kEvPerSet = LS_NUM_STAGES + 1;
 
+// Largest row (N1, pass B) and column (N2, pass A) lengths of the four-step
+// split.  Pass B holds three rows of N1 in shared memory: 3 x 4096 FP64
+// (double-float) values take 209 KB, one block per SM.  The most balanced split
+// of a 1.9e7-cell FP64 grid is then 4096 x 4608 instead of 2048 x 9216, whose
+// 147 KB pass-A columns also ran one block per SM: measured pass A 4.93 ->
+// 3.78 ms, pass B 2.60 -> 3.35 ms.
 constexpr int kN1MaxF32 = 4096, kN2MaxF32 = 25600;
-constexpr int kN1MaxF64 = 2048, kN2MaxF64 = 12800;
+constexpr int kN1MaxF64 = 4096, kN2MaxF64 = 12800;
 constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
 
 bool radix_schedule(int L, std::vector<int> &rad, int maxr = 16);

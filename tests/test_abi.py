@@ -94,8 +94,9 @@ def test_choose_params(nf, eps, prec, ups, w, n):
         assert sigma == 1.5
         assert abs(p["beta"] - 0.976 * np.pi * (1 - 0.5 / sigma) * w) < 1e-12
         assert w == int(np.ceil(np.log(1 / eps) / (np.pi * np.sqrt(1 - 1 / sigma))))
-    # split limits of the two passes; N1 a power of two
-    assert 32 <= p["n1"] <= (4096 if prec == 1 else 2048)
+    # split limits of the two passes (pass B holds three rows of N1, pass A
+    # columns of N2, in shared memory); N1 a power of two
+    assert 32 <= p["n1"] <= 4096
     assert p["n1"] & (p["n1"] - 1) == 0
     assert p["n2"] <= (25600 if prec == 1 else 12800) and p["n2"] % 2 == 0
     assert p["n"] >= sigma * nf
