@@ -189,3 +189,31 @@ def test_prepared_batch_entry_points_reject_null_handles():
     assert lib.ls_batch_prepare_shared(None, ctypes.byref(h), 4, 100, 0.1, 0.01, 1000,
                                        1e-6, 0) == 1
     assert h.value is None
+
+
+@pytest.mark.parametrize("prec,eps,ups", [(1, 1e-6, 2.0), (1, 1e-6, 1.5), (0, 1e-9, 1.5),
+                                          (0, 1e-12, 2.0)])
+def test_grid_choice_is_minimal_for_every_precision_and_upsampling(prec, eps, ups):
+    # the candidate search (sizes c 2^k in increasing order, first admissible
+    # split wins) against enumerating every candidate size below the answer
+    import paper_2409_08090_gb300 as nl
+    rng = np.random.default_rng(11)
+    for nf in [1, 3, 50, 777] + [int(x) for x in np.exp(rng.uniform(np.log(1e3), np.log(8e6), 40))]:
+        p = nl.ls_choose_params(nf, eps, prec, upsampling=ups)
+        n, n1, n2 = p["n"], p["n1"], p["n2"]
+        assert p["sigma"] == ups and n1 * n2 == n and _is_allowed(n)
+        nmin = max(int(np.ceil(ups * nf - 1e-9)), 2 * p["width"], 64)
+        assert n >= nmin
+        # below 2^22 cells every c 2^k >= nmin with k >= 6 has an admissible split
+        # (N1 = 32..512, N2 even and within the column limit), so none may be skipped
+        if n <= 1 << 22:
+            smaller = [c * 2 ** k for c in ODD for k in range(6, 40) if nmin <= c * 2 ** k < n]
+            assert not smaller, (nf, n, smaller[:3])
+        # the split is the most balanced admissible one among powers of two N1
+        assert n1 & (n1 - 1) == 0 and n2 % 2 == 0
+        bal = abs(np.log(n1) - np.log(n2))
+        for k1 in range(5, 13):
+            m1 = 1 << k1
+            if n % m1 or m1 == n1 or (n // m1) % 2 or n // m1 > (25600 if prec == 1 else 12800):
+                continue
+            assert abs(np.log(m1) - np.log(n // m1)) >= bal - 1e-12, (nf, n1, m1)
