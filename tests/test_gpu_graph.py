@@ -66,18 +66,26 @@ def test_graph_reports_device_errors_at_sync(nl):
     plan.close()
 
 
-def test_tuned_plan_matches_the_oracle(nl, oracle_mod, tmp_path, monkeypatch):
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-9)])
+def test_tuned_plan_matches_the_oracle(nl, oracle_mod, tmp_path, monkeypatch, prec, eps):
+    # the autotuner measures its 8 configurations on the device; the plan built
+    # from the cached entry takes them and still meets the tolerance
     import torch
     from paper_2409_08090_gb300 import autotune
     monkeypatch.setenv("LS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     s = W.random_case(320, 3000, 30_000, baseline=300.0)
-    e = autotune.tune(s.nf, 1e-6, "fp32", nd=s.nd, reps=3)
-    assert e["upsampling"] in autotune.CANDIDATES and len(e["ms"]) >= 1
-    plan = nl.Plan(s.nd, s.nf, 1e-6, "fp32", upsampling="tuned")
+    e = autotune.tune(s.nf, eps, prec, nd=s.nd, reps=3)
+    assert e["upsampling"] in autotune.CANDIDATES and len(e["ms"]) >= 4
+    plan = nl.Plan(s.nd, s.nf, eps, prec, upsampling="tuned")
     assert abs(plan.info.sigma - e["upsampling"]) < 1e-12
+    if e["cols_per_block"]:
+        assert plan.info.cols_per_block in (e["cols_per_block"], 1, 2, 4, 8)
     dev = torch.device("cuda:0")
     P = plan.execute(torch.tensor(s.t, device=dev), torch.tensor(s.y, device=dev),
                      torch.tensor(s.dy, device=dev), s.f0, s.df).cpu().numpy()
     plan.close()
     P_o = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, np.arange(s.nf))
-    assert np.linalg.norm(P - P_o) / np.linalg.norm(P_o) <= 1e-5
+    if prec == "fp64":
+        assert np.max(np.abs(P - P_o)) <= 1e-6
+    else:
+        assert np.linalg.norm(P - P_o) / np.linalg.norm(P_o) <= 1e-5

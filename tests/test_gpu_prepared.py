@@ -153,6 +153,24 @@ def test_prepared_shared_layout_and_graph(nl):
     plan.close()
 
 
+@pytest.mark.parametrize("fit_mean,center,norm", [(False, True, "model"), (False, False, "psd"),
+                                                   (True, True, "log")])
+def test_prepared_shared_layout_variants(nl, fit_mean, center, norm):
+    t, Y, dy, f0, df, nf = W.uniform_batch(seed=21, nseries=24, nd=1500, nf=9000)
+    Y = Y + 0.7
+    plan = nl.Plan(2, 1, 1e-10, "fp64")
+    model = dict(fit_mean=fit_mean, center_data=center, normalization=norm)
+    pb = plan.prepare_shared(Y.shape[0], Y.shape[1], f0, df, nf, **model)
+    tt, YY, dd = _dev(t), _dev(Y), _dev(dy)
+    P = pb.run(tt, YY, dd).cpu().numpy()
+    Q = plan.execute_shared(tt, YY, dd, f0, df, nf, **model).cpu().numpy()
+    scale = max(1.0, float(np.max(np.abs(Q))))
+    for i in range(Y.shape[0]):
+        assert_rerun_close(P[i], Q[i], "fp64", scale, (i, fit_mean, center, norm))
+    pb.close()
+    plan.close()
+
+
 def test_prepare_rejects_bad_layouts(nl):
     plan = nl.Plan(2, 1, 1e-6, "fp32")
     with pytest.raises(nl.LSError):
