@@ -24,6 +24,7 @@ divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import functools
 import hashlib
 import json
 import os
@@ -864,6 +865,9 @@ def run_serving(args):
     del warm, f
     per_rate = {}
     runs = [(r, "mixed") for r in rates] + [(rates[-1], "fp32"), (4 * rates[-1], "fp32")]
+    # a few served results of the busiest mixed run are kept for the accuracy
+    # check against the oracle (the cpu_baseline leg)
+    kept, kept_req = {}, {}
     for rate, mix in runs:
         n = max(16, int(rate * duration))
         arrivals = W.poisson_arrivals(rate, n, seed=int(rate))
@@ -873,6 +877,11 @@ def run_serving(args):
             precs = np.where(rng.random(n) < 0.5, "fp32", "fp64")
         else:
             precs = np.full(n, "fp32")
+        keep = set()
+        if mix == "mixed" and rate == rates[-1] and not args.no_cpu_baseline:
+            for p in ("fp32", "fp64"):
+                keep.update(int(i) for i in np.flatnonzero(precs == p)[:4])
+            kept_req.update({i: (int(picks[i]), str(precs[i])) for i in keep})
         srv.completed.clear()
         t0 = time.perf_counter()
         left = [n]
@@ -880,11 +889,13 @@ def run_serving(args):
         all_done = threading.Event()
         lock = threading.Lock()
 
-        def consume(f):
+        def consume(i, f):
             # the client reads each result as it arrives and then drops it
             exc = f.exception()
             if exc is not None:
                 failures.append(repr(exc))
+            elif i in keep:
+                kept[i] = f.result()
             elif args.serving_results == "host":
                 _ = float(f.result()[0])
             with lock:
@@ -898,7 +909,8 @@ def run_serving(args):
                 if delay > 0:
                     time.sleep(delay)
                 s = pool[picks[i]]
-                srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, str(precs[i])).add_done_callback(consume)
+                srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, str(precs[i])).add_done_callback(
+                    functools.partial(consume, i))
 
         th = threading.Thread(target=client)
         th.start()
@@ -930,6 +942,31 @@ def run_serving(args):
         plain[f"eps_{eps64:g}"] = len(sample) / (time.perf_counter() - t0)
     for p in plans.values():
         p.close()
+    cpu = accuracy = None
+    if kept:
+        import oracle
+        oracle.build()
+        rng = np.random.default_rng(17)
+        errs = {"fp32": [], "fp64": []}
+        tot_freq = tot_time = 0.0
+        for i, res in sorted(kept.items()):
+            k_pool, prec = kept_req[i]
+            s = pool[k_pool]
+            P = res.cpu().numpy() if hasattr(res, "cpu") else np.asarray(res)
+            k = np.sort(rng.choice(s.nf, min(s.nf, 256), replace=False)).astype(np.int64)
+            t0 = time.perf_counter()
+            P_o = oracle.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+            tot_time += time.perf_counter() - t0
+            tot_freq += len(k) / s.nf
+            errs[prec].append((float(np.linalg.norm(P[k] - P_o) / np.linalg.norm(P_o)),
+                               float(np.max(np.abs(P[k] - P_o)))))
+        cpu = {"value": tot_freq / tot_time, "unit": UNIT, "cores": oracle.threads(),
+               "kind": "oracle",
+               "sample": f"{len(kept)} served requests x <=256 random frequencies"}
+        accuracy = {p: {"rel_l2_max": max(e[0] for e in v), "max_abs": max(e[1] for e in v),
+                        "requests": len(v)} for p, v in errs.items() if v}
+        accuracy["against"] = "FP64 oracle (direct sums), requests of the busiest mixed run"
+        kept.clear()
     top = per_rate[str(int(rates[-1]))]
     line = {
         "metric": METRIC, "value": top.get("periodograms_per_s"), "unit": UNIT, "n_gpus": world,
@@ -944,6 +981,7 @@ def run_serving(args):
         "per_rate": per_rate,
         "plain_fp64_one_at_a_time": {"value_by_eps": plain, "unit": UNIT, "series": len(sample),
                                      "note": "ls_execute per request, plans reused, same pool"},
+        "accuracy": accuracy, "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
     return 0
