@@ -106,3 +106,20 @@ def test_model_variants_are_batched_apart():
     s.submit(b)
     first, second = s.next_batch(), s.next_batch()
     assert len(first) == 1 and len(second) == 1 and first[0].key != second[0].key
+
+
+def test_server_stats_from_timestamps_only():
+    # the server keeps (arrival, done) pairs, not the requests (whose futures
+    # hold the results): stats come from the timestamps alone
+    import types
+
+    from paper_2409_08090_gb300.serving import PeriodogramServer
+    fake = types.SimpleNamespace(completed=[(0.0, 0.001), (0.5, 0.502), (1.0, 1.010)],
+                                 batches=2)
+    st = PeriodogramServer.stats(fake)
+    assert st["requests"] == 3 and st["batches"] == 2
+    assert st["p50_ms"] == pytest.approx(2.0)
+    assert st["periodograms_per_s"] == pytest.approx(3 / 1.010)
+    assert np.percentile([1.0, 2.0, 10.0], 99) == pytest.approx(st["p99_ms"])
+    assert PeriodogramServer.stats(types.SimpleNamespace(completed=[], batches=0)) == \
+        {"requests": 0}
