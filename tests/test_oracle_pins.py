@@ -149,6 +149,77 @@ def test_sums_match_brute_force_loops(oracle_mod):
             assert np.max(np.abs(np.array(row) - sums[i])) < 1e-12, (trial, i)
             if nd >= 3:
                 assert abs(P[i] - _lstsq_power(t, y, dy, f)) < 1e-8
+            elif abs(np.exp(2j * np.pi * f * t[0]) - np.exp(2j * np.pi * f * t[1])) > 1e-3:
+                # two points are fitted exactly by offset + sinusoid: chi2 = 0
+                assert abs(P[i] - 1.0) < 1e-9, (trial, i)
+
+
+def test_two_point_series_have_unit_power(oracle_mod):
+    # Degenerate normal matrix, rank one: two points are fitted exactly by an
+    # offset plus a sinusoid whenever their phasors e^{i w t_1}, e^{i w t_2}
+    # differ, so chi2 = 0 and P = 1.  After the tau rotation one of CC_tau,
+    # SS_tau is zero up to rounding and its term must be dropped; keeping it
+    # (0/0) or dropping the other term too (a threshold above the nonzero
+    # eigenvalue, ~ |e^{i w t_1} - e^{i w t_2}|^2 w^_1 w^_2) breaks P = 1.
+    rng = np.random.default_rng(7)
+    for trial in range(200):
+        t = rng.uniform(0, 50, 2)
+        y = rng.normal(0, 1, 2)
+        dy = rng.uniform(0.3, 3, 2)
+        f0, df = float(rng.uniform(0, 1)), float(rng.uniform(1e-3, 0.1))
+        k = _k_all(64)
+        f = f0 + k * df
+        sep = np.abs(np.exp(2j * np.pi * f * t[0]) - np.exp(2j * np.pi * f * t[1]))
+        P = oracle_mod.periodogram(t, y, dy, f0, df, k)
+        m = sep > 1e-3
+        assert np.all(np.isfinite(P)), trial
+        assert np.max(np.abs(P[m] - 1.0)) < 1e-9, trial
+
+
+def _fit_power(X, y, dy):
+    # 1 - chi2_min / chi2_0 of the weighted least-squares fit on the columns X.
+    w = 1.0 / dy ** 2
+    sw = np.sqrt(w)
+    beta, *_ = np.linalg.lstsq(X * sw[:, None], y * sw, rcond=None)
+    chi2 = np.sum(w * (y - X @ beta) ** 2)
+    ybar = np.sum(w * y) / np.sum(w)
+    return 1.0 - chi2 / np.sum(w * (y - ybar) ** 2)
+
+
+def test_collinear_phases_reduce_to_one_sinusoid(oracle_mod):
+    # Times t_j = n_j + delta (n_j integers) at f = 1/2 + m: every phase is
+    # delta/2 or delta/2 + 1/2 cycles, so all phasors lie on one line through the
+    # origin and cos(w t), sin(w t) are both multiples of (-1)^n_j.  The model
+    # then holds one sinusoid column, (-1)^n, besides the offset: the vanishing
+    # eigenvalue's term must be dropped and P equals that two-column fit
+    # (numpy lstsq).  The tilt delta makes the rounding of the vanishing
+    # CC_tau or SS_tau land on either side of zero, so a zero threshold (keeping
+    # a rounding-level denominator) fails here.
+    rng = np.random.default_rng(11)
+    for trial in range(100):
+        n = int(rng.integers(3, 40))
+        delta = float(rng.uniform(0, 1))
+        tn = np.sort(rng.choice(np.arange(0, 400), n, replace=False)).astype(np.float64)
+        t = tn + delta
+        y = rng.normal(0, 1, n)
+        dy = rng.uniform(0.3, 3, n)
+        P = oracle_mod.periodogram(t, y, dy, 0.5, 1.0, _k_all(3))   # f = 1/2, 3/2, 5/2
+        ref = _fit_power(np.stack([(-1.0) ** tn, np.ones(n)], 1), y, dy)
+        assert np.max(np.abs(P - ref)) < 1e-12, trial
+
+
+def test_integer_frequency_on_integer_times_has_zero_power(oracle_mod):
+    # Integer t at integer f: every phasor is 1, cos(w t) duplicates the offset
+    # column and sin(w t) vanishes, so both eigenvalues of the normal matrix are
+    # zero, the sinusoid explains nothing and P = 0.
+    rng = np.random.default_rng(12)
+    for trial in range(20):
+        n = int(rng.integers(3, 60))
+        t = np.sort(rng.choice(np.arange(0, 500), n, replace=False)).astype(np.float64)
+        y = rng.normal(0, 1, n)
+        dy = rng.uniform(0.3, 3, n)
+        P = oracle_mod.periodogram(t, y, dy, 0.0, 1.0, _k_all(4))
+        assert np.max(np.abs(P)) < 1e-14, trial
 
 
 def test_long_baseline_phase_reduction_is_exact(oracle_mod):
