@@ -163,8 +163,9 @@ ls_status ls_set_stream(ls_plan_t plan, void *stream);
  *   norm     an ls_norm value OR'ed with model flags (LS_NO_FIT_MEAN,
  *            LS_NO_CENTER); other bits: LS_ERR_UNSUPPORTED.
  *   power    nf outputs (standard normalisation: P_k in [0, 1]).
- * The inputs are taken as exact reals: phases are reduced in double-double,
- * so a time offset does not cost accuracy.
+ * The inputs are taken as exact reals: the phases f t are reduced modulo one
+ * cycle exactly, in 128-bit integer arithmetic on the mantissas, so a time
+ * offset does not cost accuracy.
  */
 ls_status ls_execute(ls_plan_t plan, const double *t, const double *y, const double *dy,
                      int64_t nd, double f0, double df, int64_t nf, double eps, int norm,
@@ -338,25 +339,29 @@ ls_status ls_selftest_kernel_eval(double beta, int n, int device, double *max_ab
 /*
  * ls_execute_noalloc: the periodogram of one small series without allocating
  * any memory.  The paper has no counterpart: this entry point exists for
- * callers that cannot allocate device memory -- code running while a CUDA
- * stream is being captured (cudaMalloc cannot be captured), programs whose
- * device memory belongs to another allocator or a fixed arena, and loops that
- * cannot afford an allocation's synchronisation -- and so cannot create an
- * ls_plan.  It runs the ls_execute pipeline on a fixed scratch area of
+ * callers that cannot allocate device memory -- programs whose device memory
+ * belongs to another allocator (a framework's caching allocator) or to a fixed
+ * arena, and loops that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may bring -- and so cannot create an ls_plan.  It
+ * runs the ls_execute pipeline on a fixed scratch area of
  * LS_NOALLOC_SCRATCH_BYTES that the library reserves in every GPU's memory
  * when it is loaded and keeps until the process exits.
  *   t, y, dy, power: device pointers (dy may be NULL); nd, f0, df, nf, eps and
- *   prec as for ls_plan/ls_execute (standard normalisation).
+ *   prec as for ls_plan/ls_execute (standard normalisation).  The tile width
+ *   and FFT schedules are those a plan would choose for the request.
  *   Limits: nd <= LS_NOALLOC_MAX_ND, nf <= LS_NOALLOC_MAX_NF, and the request's
  *   workspace must fit the scratch area; otherwise LS_ERR_UNSUPPORTED and
  *   nothing is launched.  Host pointers: LS_ERR_ARG.
- * The call is synchronous on `stream` (NULL: legacy default stream) and returns
- * the device-side status (LS_ERR_ARG for non-finite values or dy <= 0,
- * LS_ERR_DEGENERATE for a constant series).  The first call on a device looks
- * up the scratch area's device address (once per device); make it before any
- * stream capture.  Every call reuses the same scratch area and clears what must
- * start at zero: calls whose work overlaps on the GPU (other streams or host
- * threads) race on it and must be serialised by the caller.
+ * The call is synchronous on `stream` (NULL: legacy default stream): it
+ * copies a small table from host memory, waits for the stream and returns the
+ * device-side status (LS_ERR_ARG for non-finite values or dy <= 0,
+ * LS_ERR_DEGENERATE for a constant series).  It therefore cannot be recorded
+ * by stream capture.  The first call on a device looks up the scratch area's
+ * device address and keeps it for the life of the process; do not call this
+ * entry point on a device after cudaDeviceReset.  Every call reuses the same
+ * scratch area and clears what must start at zero: calls whose work overlaps
+ * on the GPU (other streams or host threads) race on it and must be
+ * serialised by the caller.
  */
 #define LS_NOALLOC_SCRATCH_BYTES (8u << 20)
 #define LS_NOALLOC_MAX_ND 16384

@@ -322,19 +322,29 @@ int quad_nodes(int w) { return 2 * w + 24; }
 // The substitution z = sin(theta) removes the square-root endpoint behaviour of
 // psi at z = 1 (sqrt(1 - z^2) = cos theta, dz = cos theta dtheta), so the
 // Gauss-Legendre rule on theta in [0, pi/2] converges geometrically.
-void es_quadrature(int w, double beta, std::vector<double> &z, std::vector<double> &wpsi)
+// Writes q = quad_nodes(w) nodes and weights and returns q, or returns -1 (and
+// writes nothing) when q exceeds cap.
+int es_quadrature_fill(int w, double beta, double *z, double *wpsi, int cap)
 {
     const int q = quad_nodes(w);
+    if (q > cap) return -1;
     std::vector<double> x, wt;
     gauss_legendre(q, x, wt);
-    z.resize(q);
-    wpsi.resize(q);
     for (int i = 0; i < q; ++i) {
         const double th = 0.25 * M_PI * (x[i] + 1.0);
         const double c = cos(th);
         z[i] = sin(th);
         wpsi[i] = 0.25 * M_PI * wt[i] * c * exp(beta * (c - 1.0));
     }
+    return q;
+}
+
+void es_quadrature(int w, double beta, std::vector<double> &z, std::vector<double> &wpsi)
+{
+    const int q = quad_nodes(w);
+    z.resize(q);
+    wpsi.resize(q);
+    es_quadrature_fill(w, beta, z.data(), wpsi.data(), q);
 }
 
 // exp(2 pi i p / L) for p in [0, L), from an exact integer reduction.
@@ -739,6 +749,66 @@ ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t c
                          nred);
 }
 
+// Tile width (columns per pass-A block, also the bin width) and the largest
+// FFT radix of pass A (length n2) and pass B (length n1), for both the planned
+// path and the allocation-free one.  cols_req / maxr_req: requested values
+// (0: automatic).  FFT schedules, automatic, from measurements on GB300: the
+// double-float transforms of the FP64 path run faster with radix-8
+// butterflies (fewer live registers) even where that adds a stage (pass A
+// 5.2 -> 4.9 ms on a 1.9e7-cell grid, pass B 1.55x faster on 3.7e5 cells);
+// on the FP32 path pass A keeps radix 16, and pass B takes radix 8 where
+// that adds no stage (N1 = 512: 8, 8, 8 instead of 2, 16, 16; 8% faster).
+void choose_tiling(int prec, int n1, int n2, int cols_req, int maxr_req, int *ba_out,
+                   int *maxrA, int *maxrB)
+{
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    auto nstages = [](int L, int r) {
+        std::vector<int> rad;
+        return radix_schedule(L, rad, r) ? (int)rad.size() : 1 << 20;
+    };
+    if (maxr_req == 8 || maxr_req == 16) {
+        *maxrA = *maxrB = maxr_req;
+    } else if (prec == LS_FP64) {
+        *maxrA = *maxrB = 8;
+    } else {
+        *maxrA = 16;
+        *maxrB = nstages(n1, 8) <= nstages(n1, 16) ? 8 : 16;
+    }
+    // Tile width: the widest candidate whose two blocks fit an SM.  FP64 takes
+    // at most 2 columns (measured: 2 columns ran pass A 1.8x faster than 8 on
+    // a 3.7e5-cell grid, and the ragged FP64 batch 13% faster than the widest).
+    static const int kColsF32[3] = {8, 4, 2}, kColsF64[1] = {2};
+    const int *cands = prec == LS_FP64 ? kColsF64 : kColsF32;
+    const int ncand = prec == LS_FP64 ? 1 : 3;
+    int BA = 1;
+    for (int i = 0; i < ncand; ++i) {
+        const int cand = cands[i];
+        if (n1 % cand == 0 && (size_t)cand * n2 * cx <= kSmemPairBudget && n1 / cand >= 2) {
+            BA = cand;
+            break;
+        }
+    }
+    // Shared memory of a pass-A block of ba columns without cluster tables
+    // (padded columns, root tables, slot table) plus 1 KB of margin.
+    auto tile_bytes = [&](int ba) {
+        std::vector<int> rad;
+        if (!radix_schedule(n2, rad, *maxrA)) return (size_t)-1;
+        const size_t nhi = (size_t)(n2 + 63) / 64;
+        const size_t padded = (size_t)n2 + n2 / 16 + 1;
+        return cx * ((size_t)ba * padded + (size_t)ba * (64 + nhi) + 64 + nhi) +
+               sizeof(int) * (size_t)(n2 / rad.back()) + 1024;
+    };
+    // radix-8 stages need a larger slot table: keep 16 where it would not fit
+    if (*maxrA == 8 && tile_bytes(BA) > kSmemOptinBytes) *maxrA = 16;
+    // A requested tile width is taken where the grid can use it: at least two
+    // bins, and the block within the opt-in shared memory (one block per SM
+    // at the widest).
+    if (cols_req > 0 && n1 % cols_req == 0 && n1 / cols_req >= 2 &&
+        tile_bytes(cols_req) <= kSmemOptinBytes)
+        BA = cols_req;
+    *ba_out = BA;
+}
+
 // Plan (geometry, tables and, unless tables_only, the single-series workspace)
 // for the parameters pp.
 ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int prec,
@@ -777,59 +847,8 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
     g.w = pp.w;
     g.beta = pp.beta;
     g.eps = eps;
-    const size_t cx = prec == LS_FP32 ? 8 : 16;
-    // FFT schedules (largest power-of-two radix of each sub-FFT).  A request
-    // applies to both.  Automatic, from measurements on GB300: the
-    // double-float transforms of the FP64 path run faster with radix-8
-    // butterflies (fewer live registers) even where that adds a stage (pass A
-    // 5.2 -> 4.9 ms on a 1.9e7-cell grid, pass B 1.55x faster on 3.7e5 cells);
-    // on the FP32 path pass A keeps radix 16, and pass B takes radix 8 where
-    // that adds no stage (N1 = 512: 8, 8, 8 instead of 2, 16, 16; 8% faster).
-    auto nstages = [](int L, int r) {
-        std::vector<int> rad;
-        return radix_schedule(L, rad, r) ? (int)rad.size() : 1 << 20;
-    };
-    if (pp.maxr == 8 || pp.maxr == 16) {
-        p->maxrA = p->maxrB = pp.maxr;
-    } else if (prec == LS_FP64) {
-        p->maxrA = p->maxrB = 8;
-    } else {
-        p->maxrA = 16;
-        p->maxrB = nstages(pp.n1, 8) <= nstages(pp.n1, 16) ? 8 : 16;
-    }
-    // Tile width: the widest candidate whose two blocks fit an SM.  FP64 takes
-    // at most 2 columns (measured: 2 columns ran pass A 1.8x faster than 8 on
-    // a 3.7e5-cell grid, and the ragged FP64 batch 13% faster than the widest).
-    static const int kColsF32[3] = {8, 4, 2}, kColsF64[1] = {2};
-    const int *cands = prec == LS_FP64 ? kColsF64 : kColsF32;
-    const int ncand = prec == LS_FP64 ? 1 : 3;
     int BA = 1;
-    for (int i = 0; i < ncand; ++i) {
-        const int cand = cands[i];
-        if (pp.n1 % cand == 0 && (size_t)cand * pp.n2 * cx <= kSmemPairBudget &&
-            pp.n1 / cand >= 2) {
-            BA = cand;
-            break;
-        }
-    }
-    // Shared memory of a pass-A block of ba columns without cluster tables
-    // (padded columns, root tables, slot table) plus 1 KB of margin.
-    auto tile_bytes = [&](int ba) {
-        std::vector<int> rad;
-        if (!radix_schedule(pp.n2, rad, p->maxrA)) return (size_t)-1;
-        const size_t nhi = (size_t)(pp.n2 + 63) / 64;
-        const size_t padded = (size_t)pp.n2 + pp.n2 / 16 + 1;
-        return cx * ((size_t)ba * padded + (size_t)ba * (64 + nhi) + 64 + nhi) +
-               sizeof(int) * (size_t)(pp.n2 / rad.back()) + 1024;
-    };
-    // radix-8 stages need a larger slot table: keep 16 where it would not fit
-    if (p->maxrA == 8 && tile_bytes(BA) > kSmemOptinBytes) p->maxrA = 16;
-    // A requested tile width is taken where the grid can use it: at least two
-    // bins, and the block within the opt-in shared memory (one block per SM
-    // at the widest).
-    if (pp.cols > 0 && pp.n1 % pp.cols == 0 && pp.n1 / pp.cols >= 2 &&
-        tile_bytes(pp.cols) <= kSmemOptinBytes)
-        BA = pp.cols;
+    choose_tiling(prec, pp.n1, pp.n2, pp.cols, pp.maxr, &BA, &p->maxrA, &p->maxrB);
     g.BA = BA;
     g.logBA = ilog2_exact(BA);
     g.nbins = pp.n1 / BA;
@@ -1194,7 +1213,17 @@ ls_status finish_prepare(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpe
 
 namespace nls {
 // Stage descriptors of a length-L FFT for callers outside this file.
-bool fft_plan_for_length(int L, FftPlan *fp) { return build_fft(L, fp); }
+bool fft_plan_for_length(int L, FftPlan *fp, int maxr) { return build_fft(L, fp, maxr); }
+
+void plan_tiling(int prec, int n1, int n2, int *ba, int *maxrA, int *maxrB)
+{
+    choose_tiling(prec, n1, n2, 0, 0, ba, maxrA, maxrB);
+}
+
+int es_quadrature_into(int w, double beta, double *z, double *wpsi, int cap)
+{
+    return es_quadrature_fill(w, beta, z, wpsi, cap);
+}
 }  // namespace nls
 
 extern "C" {

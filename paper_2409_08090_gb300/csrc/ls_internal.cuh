@@ -169,8 +169,18 @@ cudaError_t launch_kernel_eval_pair(int n, double beta, double *dfl_out, double 
 template <typename T>
 size_t point_record_bytes();
 
-// Stage descriptors of a length-L sub-FFT (false if L has no schedule).
-bool fft_plan_for_length(int L, FftPlan *fp);
+// Stage descriptors of a length-L sub-FFT with radices up to maxr (false if L
+// has no schedule).
+bool fft_plan_for_length(int L, FftPlan *fp, int maxr);
+
+// The planned path's automatic tile width (columns per pass-A block) and the
+// largest FFT radix of pass A (length n2) and pass B (length n1).
+void plan_tiling(int prec, int n1, int n2, int *ba, int *maxrA, int *maxrB);
+
+// Quadrature rule of the deconvolution table for kernel width w and shape
+// beta: nodes z in [0, 1] and weights times psi(z); returns the node count, or
+// -1 (nothing written) when it exceeds cap.
+int es_quadrature_into(int w, double beta, double *z, double *wpsi, int cap);
 
 size_t passA_smem_bytes(const Geometry &g, size_t cx_bytes, int cs);
 size_t passB_smem_bytes(const Geometry &g, size_t cx_bytes);

@@ -1185,13 +1185,17 @@ struct PassBArgs {
 // Normalisation of the standard power P = p / YY (p the explained weighted
 // sum of squares with w^): model p / (YY - p) = P / (1 - P); log -ln(1 - P);
 // psd p W / 2 = P YY W / 2 with the unscaled YY and W = sum w.
+// The FP32 path's log keeps FP32 relative accuracy over the whole range
+// without an FP64 logarithm: log1p(-P) for P < 1/2 (no cancellation in 1 - P
+// for small P), and the log of 1 - P, formed exactly in FP64, above.
 template <typename T>
 __device__ __forceinline__ double ls_normalise(double P, int norm, double psd_factor)
 {
     switch (norm) {
     case 1: return P * rcp_fp64(1.0 - P);
     case 2:
-        if (sizeof(T) == 4) return -(double)logf((float)(1.0 - P));
+        if (sizeof(T) == 4)
+            return P < 0.5 ? -(double)log1pf(-(float)P) : -(double)logf((float)(1.0 - P));
         return -log1p(-P);
     case 3: return P * psd_factor;
     default: return P;

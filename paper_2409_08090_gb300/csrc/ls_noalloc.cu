@@ -1,27 +1,32 @@
 // Periodogram entry point that allocates no memory: ls_execute_noalloc.
 //
 // Who needs it: callers that must not allocate device memory themselves or
-// through a library -- code running while a CUDA stream is being captured
-// (cudaMalloc is not capturable), processes whose device memory is owned by
-// another allocator (a framework's caching allocator or a fixed arena that a
-// raw cudaMalloc would fragment or exceed), and latency-bound loops where an
-// allocation's synchronisation is not acceptable.  Such callers cannot create
-// an ls_plan (ls_plan allocates its workspace), so this entry point runs the
-// same pipeline on a fixed scratch area that the library reserves when it is
-// loaded: a file-scope __device__ array, which every GPU that loads the library
-// holds until the process exits.
+// through a library -- processes whose device memory is owned by another
+// allocator (a framework's caching allocator, or a fixed arena that a raw
+// cudaMalloc would fragment or exceed), and loops that cannot afford the
+// device-wide synchronisation a cudaMalloc or cudaFree may bring.  Such
+// callers cannot create an ls_plan (ls_plan allocates its workspace), so this
+// entry point runs the same pipeline on a fixed scratch area that the library
+// reserves when it is loaded: a file-scope __device__ array, which every GPU
+// that loads the library holds until the process exits.
+//
+// The call is synchronous: it copies the deconvolution quadrature from a host
+// stack buffer, waits for its stream and reads the device-side status word
+// back.  It therefore cannot run while its stream is being captured into a
+// CUDA graph.
 //
 // Set-up: the host cannot use the array's name as a device address (in host
 // code it names a host-side stand-in).  The first call on each device, with
-// that device current, resolves the address once with cudaGetSymbolAddress and
-// keeps it; make that first call before any stream capture.
+// that device current, resolves the address with cudaGetSymbolAddress and
+// keeps it for the life of the process.  A cudaDeviceReset tears down the
+// context that address belongs to, so do not call this entry point on a
+// device after resetting it.
 //
 // Sharing: every call uses the same array and leaves its contents behind.
 // Counters and status words that must start at zero are cleared at the start
 // of each call; calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on the array and must be serialised by the
-// caller.  The call is synchronous: it waits for its stream before returning
-// the device-side status.
+// caller.
 #include <math.h>
 #include <mutex>
 
@@ -81,41 +86,7 @@ __global__ void k_root_table(T *out, int64_t L, int bits)
     }
 }
 
-// Gauss-Legendre rule after z = sin(theta) on [0, pi/2] into fixed arrays
-// (the plan's quadrature for 1/phi_hat), no heap.
-constexpr int kMaxQuad = 64;
-int quadrature_fixed(int w, double beta, double *z, double *wpsi)
-{
-    const int q = 2 * w + 24;
-    for (int i = 0; i < q; ++i) {
-        double x = cos(M_PI * (i + 0.75) / (q + 0.5)), dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= q; ++k) {
-                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = q * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (fabs(dx) < 1e-16) break;
-        }
-        double p0 = 1.0, p1 = x;
-        for (int k = 2; k <= q; ++k) {
-            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = q * (x * p1 - p0) / (x * x - 1.0);
-        const double wt = 2.0 / ((1.0 - x * x) * dp * dp);
-        const double th = 0.25 * M_PI * (x + 1.0);
-        const double c = cos(th);
-        z[i] = sin(th);
-        wpsi[i] = 0.25 * M_PI * wt * c * exp(beta * (c - 1.0));
-    }
-    return q;
-}
+constexpr int kMaxQuad = 64;   // nodes of the deconvolution quadrature
 
 bool device_pointer(const void *p)
 {
@@ -147,15 +118,11 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     g.w = w;
     g.beta = beta;
     g.eps = eps;
-    if (!fft_plan_for_length(n2, &g.fa) || !fft_plan_for_length(n1, &g.fb))
+    // the same tile width and FFT schedules as a plan for this request
+    int BA = 1, maxrA = 16, maxrB = 16;
+    plan_tiling(prec, n1, n2, &BA, &maxrA, &maxrB);
+    if (!fft_plan_for_length(n2, &g.fa, maxrA) || !fft_plan_for_length(n1, &g.fb, maxrB))
         return LS_ERR_UNSUPPORTED;
-    int BA = 1;
-    for (int cand : {8, 4, 2}) {
-        if (n1 % cand == 0 && (size_t)cand * n2 * sizeof(V) <= 100 * 1024 && n1 / cand >= 2) {
-            BA = cand;
-            break;
-        }
-    }
     g.BA = BA;
     g.logBA = BA == 8 ? 3 : BA == 4 ? 2 : BA == 2 ? 1 : 0;
     g.nbins = n1 / BA;
@@ -215,7 +182,8 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     k_root_table<T><<<64, 256, 0, st>>>(static_cast<T *>(ws.twB), n1, 6);
     k_root_table<T><<<256, 256, 0, st>>>(static_cast<T *>(ws.tw4), n, kTw4Bits);
     double quad[2 * kMaxQuad];
-    const int q = quadrature_fixed(w, beta, quad, quad + kMaxQuad);
+    const int q = es_quadrature_into(w, beta, quad, quad + kMaxQuad, kMaxQuad);
+    if (q < 0) return LS_ERR_UNSUPPORTED;
     double *dquad = reinterpret_cast<double *>(base + o_quad);
     e = cudaMemcpyAsync(dquad, quad, sizeof(quad), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return LS_ERR_CUDA;

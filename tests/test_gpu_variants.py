@@ -202,3 +202,27 @@ def test_double_float_kernel_evaluation_matches_fp64(nl, beta):
     st = nl._lib.ls_selftest_kernel_eval(beta, 200_001, 0, ctypes.byref(err))
     assert st == nl.LS_OK
     assert err.value <= beta * 2.0 ** -48 * 1.5, err.value
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_log_normalisation_keeps_relative_accuracy_at_small_power(nl, oracle_mod, prec, eps):
+    # -ln(1 - P) ~ P for small P: where P < 1e-5 the log-normalised output must
+    # carry no more relative error than the standard power itself (forming
+    # 1 - P in FP32 first loses everything below P ~ 6e-8).
+    s = W.random_case(91, 2000, 20000, df_t=0.9, baseline=300.0)
+    k = np.arange(s.nf)
+    ref_std = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k)
+    ref_log = oracle_mod.periodogram(s.t, s.y, s.dy, s.f0, s.df, k, normalization="log")
+    plan = nl.Plan(s.nd, s.nf, eps, prec)
+    P_std = plan.execute(_dev(s.t), _dev(s.y), _dev(s.dy), s.f0, s.df).cpu().numpy()
+    P_log = plan.execute(_dev(s.t), _dev(s.y), _dev(s.dy), s.f0, s.df,
+                         normalization="log").cpu().numpy()
+    plan.close()
+    small = ref_std < 1e-5
+    assert np.count_nonzero(small) >= 50
+    rel_std = np.abs(P_std[small] / ref_std[small] - 1.0)
+    rel_log = np.abs(P_log[small] / ref_log[small] - 1.0)
+    bound = 3.0 * float(np.max(rel_std)) + 1e-6
+    assert float(np.max(rel_log)) <= bound, (float(np.max(rel_log)), bound)
+    if prec == "fp64":
+        assert float(np.max(rel_log)) <= 1e-5

@@ -1,10 +1,10 @@
 """ls_execute_noalloc: the periodogram entry point that allocates nothing.
 
-It serves callers that cannot allocate device memory (work recorded into a
-CUDA graph by stream capture, programs whose device memory belongs to another
-allocator, allocation-free loops): they cannot create an ls_plan, so the
-library runs the same pipeline on a fixed scratch area it reserves at load
-time.  These tests call it through the C-ABI binding and compare its output
+It serves callers that cannot allocate device memory (programs whose device
+memory belongs to another allocator or a fixed arena, loops that cannot
+afford the synchronisation an allocation may bring): they cannot create an
+ls_plan, so the library runs the same pipeline on a fixed scratch area it
+reserves at load time.  The call is synchronous.  These tests call it through the C-ABI binding and compare its output
 with the planned entry point, ls_execute, at the parity tolerances used
 elsewhere (FP64 eps 1e-12: max |dP| <= 1e-9; FP32 eps 1e-6: relative l2
 <= 1e-5), on consecutive calls that reuse the scratch area.  The file sorts
