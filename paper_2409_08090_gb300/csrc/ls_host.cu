@@ -44,7 +44,8 @@ struct BatchWorkspace {
     int cap_S = 0;            // series per launch
     int64_t cap_cells = 0;    // elements of H (3 n S)
     int cap_nred = 0;         // reduction blocks per series
-    int64_t ws_bins = 0;      // entries of each of hist, binstart, cursor
+    int64_t ws_bins = 0;      // entries of each of hist, binstart
+    int64_t cap_chunk = 0;    // entries of chist
     SeriesDesc *desc = nullptr;
     std::vector<void *> allocs;
     int64_t bytes = 0;
@@ -496,7 +497,7 @@ ls_status plan_workspace(ls_plan_s *p, bool tables_only)
     const size_t cx = sizeof(typename Cx<T>::type);
     ls_status s;
     if ((s = plan_alloc(p, &p->ws.H, 3 * (size_t)g.n * cx)) != LS_OK) return s;
-    const size_t rec = point_record_bytes<T>() * (size_t)p->max_nd + 4 * 256;   // carve() alignment
+    const size_t rec = point_record_bytes<T>() * (size_t)p->max_nd + 5 * 256;   // carve() alignment
     for (int i = 0; i < 2; ++i) {
         if ((s = plan_alloc(p, &p->ws.pts_raw[i], rec)) != LS_OK) return s;
         if ((s = plan_alloc(p, &p->ws.pts_sorted[i], rec)) != LS_OK) return s;
@@ -506,8 +507,10 @@ ls_status plan_workspace(ls_plan_s *p, bool tables_only)
     p->ws.hist = static_cast<int *>(v);
     if ((s = plan_alloc(p, &v, sizeof(int) * 2 * ((size_t)g.nbins + 1))) != LS_OK) return s;
     p->ws.binstart = static_cast<int *>(v);
-    if ((s = plan_alloc(p, &v, sizeof(int) * 2 * (size_t)g.nbins)) != LS_OK) return s;
-    p->ws.cursor = static_cast<int *>(v);
+    if ((s = plan_alloc(p, &v, sizeof(int) * (size_t)chunk_hist_entries(p->max_nd, 1, g.nbins))) !=
+        LS_OK)
+        return s;
+    p->ws.chist = static_cast<int *>(v);
     if ((s = plan_alloc(p, &v, sizeof(double) * 3 * (size_t)p->nred)) != LS_OK) return s;
     p->ws.partials = static_cast<double *>(v);
     if ((s = plan_alloc(p, &v, 256)) != LS_OK) return s;
@@ -678,16 +681,17 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
 void batch_free(ls_plan_s *p);
 
 // Make the batch workspace b hold S series, `points` records, `cells`
-// elements of H, `bins` histogram entries per array and nred reduction blocks
-// per series (the buffers grow by a quarter beyond the request).  st is the
+// elements of H, `bins` entries in each of hist and binstart, `chunks` chunk
+// histogram entries and nred reduction blocks per series (the buffers grow by
+// a quarter beyond the request).  st is the
 // stream that last used b (synchronised before a reallocation); device errors
 // of its launches go to the status word `status`.
 template <typename T>
 ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int64_t points,
-                     int64_t cells, int64_t bins, int nred, bool exact = false)
+                     int64_t cells, int64_t bins, int64_t chunks, int nred, bool exact = false)
 {
     if (S <= b.cap_S && points <= b.cap_points && cells <= b.cap_cells && nred <= b.cap_nred &&
-        bins <= b.ws_bins)
+        bins <= b.ws_bins && chunks <= b.cap_chunk)
         return LS_OK;
     if (st) cudaStreamSynchronize(st);
     for (void *a : b.allocs) cudaFree(a);
@@ -701,6 +705,7 @@ ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int
     b.cap_cells = grow(cells, b.cap_cells);
     b.cap_nred = (int)grow(nred, b.cap_nred);
     b.ws_bins = grow(bins, b.ws_bins);
+    b.cap_chunk = grow(chunks, b.cap_chunk);
     auto alloc = [&](void **ptr, size_t bytes) -> ls_status {
         cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
         if (e != cudaSuccess) {
@@ -716,7 +721,7 @@ ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int
     ls_status s;
     void *v;
     if ((s = alloc(&ws.H, cx * (size_t)b.cap_cells)) != LS_OK) return s;
-    const size_t rec = point_record_bytes<T>() * (size_t)b.cap_points + 4 * 256;
+    const size_t rec = point_record_bytes<T>() * (size_t)b.cap_points + 5 * 256;
     for (int i = 0; i < 2; ++i) {
         if ((s = alloc(&ws.pts_raw[i], rec)) != LS_OK) return s;
         if ((s = alloc(&ws.pts_sorted[i], rec)) != LS_OK) return s;
@@ -725,8 +730,8 @@ ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int
     ws.hist = static_cast<int *>(v);
     if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
     ws.binstart = static_cast<int *>(v);
-    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
-    ws.cursor = static_cast<int *>(v);
+    if ((s = alloc(&v, sizeof(int) * (size_t)b.cap_chunk)) != LS_OK) return s;
+    ws.chist = static_cast<int *>(v);
     if ((s = alloc(&v, sizeof(double) * 3 * (size_t)b.cap_nred * b.cap_S)) != LS_OK) return s;
     ws.partials = static_cast<double *>(v);
     if ((s = alloc(&v, sizeof(unsigned int) * 2 * (size_t)b.cap_S)) != LS_OK) return s;
@@ -743,10 +748,10 @@ ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int
 
 template <typename T>
 ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t cells, int64_t bins,
-                        int nred)
+                        int64_t chunks, int nred)
 {
     return reserve_ws<T>(p->bws[lane], p->lane_stream[lane], p->ws.status, S, points, cells, bins,
-                         nred);
+                         chunks, nred);
 }
 
 // Tile width (columns per pass-A block, also the bin width) and the largest
@@ -998,7 +1003,8 @@ ls_status batch_launch(ls_plan_s *p, int lane, const ls_plan_s *sub, const std::
     const int64_t grids = shared ? S + 2 : 3 * (int64_t)S;
     const int nred = batch_nred(p, S, max_nd);
     ls_status s = batch_reserve<T>(p, lane, S, points, g.n * grids,
-                                   2 * ((int64_t)g.nbins + 1) * S, nred);
+                                   2 * ((int64_t)g.nbins + 1) * S,
+                                   chunk_hist_entries(points, S, g.nbins), nred);
     if (s != LS_OK) return s;
     BatchWorkspace &b = p->bws[lane];
     cudaStream_t st = p->lane_stream[lane];
@@ -1122,7 +1128,7 @@ ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec
     struct Need {
         bool used = false;
         int S = 0, nred = 0;
-        int64_t points = 0, cells = 0, bins = 0;
+        int64_t points = 0, cells = 0, bins = 0, chunks = 0;
     } need[kBatchLanes];
     std::vector<SeriesDesc> all;
     int lane = 0;
@@ -1146,13 +1152,15 @@ ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec
         n.points = std::max(n.points, pl.points);
         n.cells = std::max(n.cells, sub->g.n * grids);
         n.bins = std::max(n.bins, 2 * ((int64_t)sub->g.nbins + 1) * pl.S);
+        n.chunks = std::max(n.chunks, chunk_hist_entries(pl.points, pl.S, sub->g.nbins));
         b->launches.push_back(pl);
         lane = (lane + 1) % kBatchLanes;
     }
     for (int l = 0; l < kBatchLanes; ++l) {
         if (!need[l].used) continue;
         ls_status s = reserve_ws<T>(b->bws[l], nullptr, p->ws.status, need[l].S, need[l].points,
-                                    need[l].cells, need[l].bins, need[l].nred, true);
+                                    need[l].cells, need[l].bins, need[l].chunks, need[l].nred,
+                                    true);
         if (s != LS_OK) return s;
         b->bytes += b->bws[l].bytes;
     }

@@ -68,12 +68,30 @@ struct Geometry {
 
 // Point records, one set per spread geometry (x and 2x).  `ab` packs the
 // first covered cell c0 = a + N1 b as a | (b << 16); `roff` is such that the
-// kernel argument of cell c0 + i is z = (roff - w/2 + i) * 2/w.
+// kernel argument of cell c0 + i is z = (roff - w/2 + i) * 2/w.  `rank` (the
+// unsorted set of geometry x only) holds each record's stable rank among the
+// records of its chunk that share its bin, geometry x in the low and 2x in
+// the high 16 bits.
 template <typename T> struct PointSet {
     uint32_t *ab;
     T *roff;
     typename Cx<T>::type *s[2];   // strengths (geometry x: s1, s2; geometry 2x: s3)
+    uint32_t *rank;
 };
+
+// Stable bin sort: records are ranked in chunks of kChunk consecutive input
+// records (one block of kThreadsPts threads, each warp kChunk / 8 of them);
+// series s of a launch owns the chunk rows chunk_row0(s) .. of the chunk
+// histogram, so rows never overlap: (rec_off + nd) / kChunk - rec_off / kChunk
+// + 1 >= ceil(nd / kChunk).
+constexpr int kChunk = 2048;
+constexpr int kThreadsPts = 256;
+__host__ __device__ inline int64_t chunk_row0(int64_t rec_off, int s) { return rec_off / kChunk + s; }
+// Chunk-histogram entries a launch of S series over `points` records needs.
+__host__ __device__ inline int64_t chunk_hist_entries(int64_t points, int S, int nbins)
+{
+    return (points / kChunk + S) * 2 * (int64_t)nbins;
+}
 
 struct Stats {            // FP64 reductions, in device memory
     double W;             // sum of w_j
@@ -90,9 +108,10 @@ struct Workspace {
     void *H;              // 3 grids of n complex T, layout [grid][d][a]
     void *pts_raw[2];     // unsorted point records (two geometries), see PointSet
     void *pts_sorted[2];
-    int *hist;            // 2 * nbins counts
-    int *binstart;        // 2 * (nbins + 1)
-    int *cursor;          // 2 * nbins
+    int *hist;            // 2 * nbins records per bin, per series
+    int *binstart;        // 2 * (nbins + 1), per series
+    int *chist;           // chunk histograms, then their prefixes over chunks:
+                          // rows of 2 * nbins (chunk_row0, chunk_hist_entries)
     double *partials;     // reduction partials
     unsigned int *counter;// last-block tickets (2)
     Stats *stats;
@@ -126,7 +145,8 @@ struct SeriesDesc {
 // S series launched together (grid dimension y): `many` points to S device
 // descriptors, or is null and the single series is `one`.  Per-series
 // workspace: stats[s], counter[2s .. 2s+1], partials[s * 3 * nred ...],
-// hist/cursor[s * 2 * nbins ...], binstart[s * 2 * (nbins + 1) ...],
+// hist[s * 2 * nbins ...], binstart[s * 2 * (nbins + 1) ...], chist from row
+// chunk_row0(rec_off, s),
 // H[s * 3 * n ...].
 struct Batch {
     int S;

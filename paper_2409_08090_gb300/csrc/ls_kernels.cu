@@ -46,6 +46,7 @@ __device__ __forceinline__ PointSet<T> shifted(PointSet<T> p, int64_t off)
     p.roff += off;
     p.s[0] += off;
     p.s[1] += off;
+    p.rank += off;
     return p;
 }
 
@@ -266,36 +267,48 @@ template <> struct Cis<float> {
     }
 };
 
-// Warp-aggregated atomicAdd of 1 to counter[key] (threads with equal keys
-// share one atomic); returns the old value plus the thread's rank among them.
-__device__ __forceinline__ int agg_increment(int *counter, int key, bool active)
+// Stable rank of this lane's key among the warp's earlier keys, continuing
+// the warp-private counts cnt[key] (which it then advances): lanes with equal
+// keys are ranked in lane order after everything counted before.  Inactive
+// lanes take no part; the result is 0 for them.  Warp-uniform call.
+__device__ __forceinline__ int warp_stable_rank(unsigned short *cnt, int key, bool active)
 {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned mask = __ballot_sync(0xffffffffu, active);
     const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1 - (int)lane) & mask;
-    int old = 0;
+    int base = 0, r = 0;
     if (active) {
-        const int leader = __ffs(peers) - 1;
-        if ((int)lane == leader) old = atomicAdd(counter + key, __popc(peers));
-        old = __shfl_sync(peers, old, leader);
-        old += __popc(peers & ((1u << lane) - 1u));
+        base = cnt[key];
+        r = base + __popc(peers & ((1u << lane) - 1u));
     }
-    return old;
+    __syncwarp();
+    if (active && (int)lane == __ffs(peers) - 1) cnt[key] = (unsigned short)(base + __popc(peers));
+    __syncwarp();
+    return r;
 }
 
 
 // ---------------------------------------------------------------------------
-// K1b: per-point records + bin histogram + YY reduction.  Coordinates and
-// pre-phases come from the exact integer reduction; weights and the
-// mean-subtracted data are FP64; strengths are stored in T.
+// K1b: per-point records, their stable in-chunk bin ranks, the chunk
+// histograms and the YY reduction.  Coordinates and pre-phases come from the
+// exact integer reduction; weights and the mean-subtracted data are FP64;
+// strengths are stored in T.  A block takes chunks of kChunk consecutive
+// records (warp w the records w kChunk/8 .. of the chunk, 32 at a time), ranks
+// every record among the chunk's earlier records of its bin (warp-private
+// counts, then an exclusive scan over the warps) and writes the chunk's bin
+// counts to its row of chist.  Dynamic shared memory: 2 x 8 x nbins counts.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
-                         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
-                         PointSet<T> p2, int *hist, double *partials, unsigned int *counter,
-                         Stats *st, int *status)
+__global__ void __launch_bounds__(kThreadsPts)
+k_points(const double *__restrict__ t, const double *__restrict__ y,
+         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
+         PointSet<T> p2, int *chist, double *partials, unsigned int *counter,
+         Stats *st, int *status)
 {
     using V = Cplx<T>;
+    extern __shared__ __align__(16) unsigned short wcnt[];   // [geometry][warp][bin]
+    constexpr int kWarps = kThreadsPts / 32;
+    constexpr int kSteps = kChunk / kThreadsPts;             // records per thread per chunk
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
     t += sd.pt_off;
@@ -305,7 +318,8 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
     const PhaseArgs ph = sd.ph;
     px = shifted(px, sd.rec_off);
     p2 = shifted(p2, sd.rec_off);
-    hist += (size_t)ser * 2 * g.nbins;
+    const int nbins = g.nbins;
+    const int64_t row0 = chunk_row0(sd.rec_off, ser);
     partials += (size_t)ser * 3 * gridDim.x;
     counter += 2 * ser + 1;
     st += ser;
@@ -314,9 +328,19 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
     const double ybar = st->ybar;
     const double scale = st->scale;
     double syy = 0.0, sy2 = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < nd; j0 += stride) {
-        const int64_t j = j0 + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned short *cx = wcnt + (size_t)warp * nbins;                 // geometry x
+    unsigned short *c2 = wcnt + (size_t)(kWarps + warp) * nbins;      // geometry 2x
+    const int64_t nchunk = (nd + kChunk - 1) / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    __syncthreads();                      // the previous chunk is done with the counts
+    for (int i = threadIdx.x; i < kWarps * nbins; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(wcnt)[i] = 0u;   // 2 x 8 x nbins 16-bit counts
+    __syncthreads();
+    uint32_t rk[kSteps], bins[kSteps];
+#pragma unroll
+    for (int step = 0; step < kSteps; ++step) {
+        const int64_t j = ch * kChunk + (int64_t)warp * (kChunk / kWarps) + step * 32 + lane;
         const bool act = j < nd;
         uint32_t ab1 = 0, ab2 = 0;
         if (act) {
@@ -344,9 +368,36 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
             p2.roff[j] = r2;
             p2.s[0][j] = mk2(wt * q.x, wt * q.y);
         }
-        agg_increment(hist, (int)((ab1 & 0xFFFFu) >> g.logBA), act);
-        agg_increment(hist, g.nbins + (int)((ab2 & 0xFFFFu) >> g.logBA), act);
+        const int b1 = (int)((ab1 & 0xFFFFu) >> g.logBA), b2 = (int)((ab2 & 0xFFFFu) >> g.logBA);
+        bins[step] = (uint32_t)b1 | ((uint32_t)b2 << 16);
+        rk[step] = (uint32_t)warp_stable_rank(cx, b1, act) |
+                   ((uint32_t)warp_stable_rank(c2, b2, act) << 16);
     }
+    __syncthreads();
+    // exclusive scan of each bin's counts over the warps (input order), the
+    // chunk's totals to its histogram row
+    for (int col = threadIdx.x; col < 2 * nbins; col += blockDim.x) {
+        const int geo = col >= nbins ? 1 : 0;
+        unsigned short *c = wcnt + (size_t)geo * kWarps * nbins + (col - geo * nbins);
+        int acc = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const int v = c[(size_t)w * nbins];
+            c[(size_t)w * nbins] = (unsigned short)acc;
+            acc += v;
+        }
+        chist[(row0 + ch) * 2 * nbins + col] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int step = 0; step < kSteps; ++step) {
+        const int64_t j = ch * kChunk + (int64_t)warp * (kChunk / kWarps) + step * 32 + lane;
+        if (j < nd) {
+            const int b1 = (int)(bins[step] & 0xFFFFu), b2 = (int)(bins[step] >> 16);
+            px.rank[j] = ((rk[step] & 0xFFFFu) + cx[b1]) | (((rk[step] >> 16) + c2[b2]) << 16);
+        }
+    }
+    }   // chunks
     double a = block_sum(syy, sh);
     double b = block_sum(sy2, sh);
     if (threadIdx.x == 0) {
@@ -368,18 +419,55 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// K2: exclusive scan of the two histograms (one block) -> bin starts, cursors.
+// K2a: per (geometry, bin) column of a series' chunk histograms: exclusive
+// prefix over the chunks in place, and the column total to hist.  A block
+// takes 32 columns (one per lane); warp w the rows w R .. (w + 1) R - 1,
+// R = ceil(chunks / 8): each warp sums its rows, the warps' sums are scanned
+// in shared memory, then each warp writes its rows' prefixes.
 // ---------------------------------------------------------------------------
-__global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, int *cursor)
+__global__ void __launch_bounds__(256) k_chunk_scan(Batch bt, int nbins, int *chist, int *hist)
+{
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    const int64_t nchunk = (sd.nd + kChunk - 1) / kChunk;
+    const int ncol = 2 * nbins;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    __shared__ int part[8][32];
+    const int64_t per = (nchunk + 7) / 8;
+    const int64_t r0 = warp * per, r1 = min(nchunk, r0 + per);
+    int *cp = chist + chunk_row0(sd.rec_off, ser) * ncol + col;
+    int sum = 0;
+    if (col < ncol) {
+#pragma unroll 8
+        for (int64_t r = r0; r < r1; ++r) sum += cp[r * ncol];
+    }
+    part[warp][lane] = sum;
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += part[w][lane];
+    if (col < ncol) {
+        for (int64_t r = r0; r < r1; ++r) {
+            const int v = cp[r * ncol];
+            cp[r * ncol] = off;
+            off += v;
+        }
+        if (warp == 7) hist[(size_t)ser * ncol + col] = off;   // the column total
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2b: exclusive scan of the two bin-total arrays (one block per series) ->
+// bin starts.
+// ---------------------------------------------------------------------------
+__global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart)
 {
     hist += (size_t)blockIdx.x * 2 * nbins;
     binstart += (size_t)blockIdx.x * 2 * (nbins + 1);
-    cursor += (size_t)blockIdx.x * 2 * nbins;
     __shared__ int chunk_tot[1024];
     for (int geo = 0; geo < 2; ++geo) {
         const int *h = hist + geo * nbins;
         int *bs = binstart + geo * (nbins + 1);
-        int *cu = cursor + geo * nbins;
         const int per = (nbins + blockDim.x - 1) / blockDim.x;
         const int lo = threadIdx.x * per;
         const int hi = min(nbins, lo + per);
@@ -396,7 +484,6 @@ __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, i
         int run = (threadIdx.x == 0) ? 0 : chunk_tot[threadIdx.x - 1];
         for (int i = lo; i < hi; ++i) {
             bs[i] = run;
-            cu[i] = run;
             run += h[i];
         }
         if (threadIdx.x == blockDim.x - 1) bs[nbins] = chunk_tot[blockDim.x - 1];
@@ -405,11 +492,14 @@ __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart, i
 }
 
 // ---------------------------------------------------------------------------
-// K2b: scatter the point records into bin order (order inside a bin is free).
+// K2c: scatter the point records into bin order, stably: record j of chunk c
+// goes to binstart[bin] + (records of its bin in chunks before c) + (its rank
+// in chunk c), so a bin keeps its records in input order.  No atomics.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
-                          PointSet<T> sx, PointSet<T> s2, int *cursor)
+                          PointSet<T> sx, PointSet<T> s2, const int *__restrict__ binstart,
+                          const int *__restrict__ chist)
 {
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
@@ -418,24 +508,24 @@ __global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
     r2 = shifted(r2, sd.rec_off);
     sx = shifted(sx, sd.rec_off);
     s2 = shifted(s2, sd.rec_off);
-    cursor += (size_t)ser * 2 * g.nbins;
+    const int nbins = g.nbins;
+    const int *bs1 = binstart + (size_t)ser * 2 * (nbins + 1);
+    const int *bs2 = bs1 + nbins + 1;
+    const int *crow = chist + chunk_row0(sd.rec_off, ser) * 2 * nbins;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x; j0 < nd; j0 += stride) {
-        const int64_t j = j0 + threadIdx.x;
-        const bool act = j < nd;
-        const uint32_t c1 = act ? rx.ab[j] : 0u;
-        const uint32_t c2 = act ? r2.ab[j] : 0u;
-        const int d1 = agg_increment(cursor, (int)((c1 & 0xFFFFu) >> g.logBA), act);
-        const int d2 = agg_increment(cursor, g.nbins + (int)((c2 & 0xFFFFu) >> g.logBA), act);
-        if (act) {
-            sx.ab[d1] = c1;
-            sx.roff[d1] = rx.roff[j];
-            sx.s[0][d1] = rx.s[0][j];
-            sx.s[1][d1] = rx.s[1][j];
-            s2.ab[d2] = c2;
-            s2.roff[d2] = r2.roff[j];
-            s2.s[0][d2] = r2.s[0][j];
-        }
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd; j += stride) {
+        const uint32_t c1 = rx.ab[j], c2 = r2.ab[j], rk = rx.rank[j];
+        const int b1 = (int)((c1 & 0xFFFFu) >> g.logBA), b2 = (int)((c2 & 0xFFFFu) >> g.logBA);
+        const int *cr = crow + (j / kChunk) * 2 * nbins;
+        const int d1 = __ldg(bs1 + b1) + __ldg(cr + b1) + (int)(rk & 0xFFFFu);
+        const int d2 = __ldg(bs2 + b2) + __ldg(cr + nbins + b2) + (int)(rk >> 16);
+        sx.ab[d1] = c1;
+        sx.roff[d1] = rx.roff[j];
+        sx.s[0][d1] = rx.s[0][j];
+        sx.s[1][d1] = rx.s[1][j];
+        s2.ab[d2] = c2;
+        s2.roff[d2] = r2.roff[j];
+        s2.s[0][d2] = r2.s[0][j];
     }
 }
 
@@ -1576,7 +1666,7 @@ __global__ void k_deconv_slot(T *out, const T *__restrict__ compact, int64_t cou
 template <typename T>
 size_t point_record_bytes()
 {
-    return sizeof(uint32_t) + sizeof(T) + 2 * sizeof(Cplx<T>);
+    return 2 * sizeof(uint32_t) + sizeof(T) + 2 * sizeof(Cplx<T>);
 }
 
 // Blocks of a pass kernel whose dynamic shared memory is smem that fit one
@@ -1650,6 +1740,8 @@ static PointSet<T> carve(void *base, int64_t max_nd)
     p.roff = reinterpret_cast<T *>(b + off);
     off = align(off + sizeof(T) * (size_t)max_nd);
     p.ab = reinterpret_cast<uint32_t *>(b + off);
+    off = align(off + sizeof(uint32_t) * (size_t)max_nd);
+    p.rank = reinterpret_cast<uint32_t *>(b + off);
     return p;
 }
 
@@ -1700,7 +1792,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
                             const double *dy, double *power, double *sums, int nred,
                             cudaStream_t st, cudaEvent_t *ev, int shared, int mode)
 {
-    int nk = 4;    // kernels enqueued: stats, points, scan, scatter, then the passes
+    int nk = 5;    // kernels enqueued: stats, points, chunk scan, scan, scatter, then the passes
     const int nofit = (mode & kModeNoFit) ? 1 : 0;
     const int center = (!nofit || !(mode & kModeNoCenter)) ? 1 : 0;
     cudaError_t err;
@@ -1709,17 +1801,23 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     PointSet<T> sx = carve<T>(ws.pts_sorted[0], capacity), s2 = carve<T>(ws.pts_sorted[1], capacity);
 
     if (ev) cudaEventRecord(ev[0], st);
-    err = cudaMemsetAsync(ws.hist, 0, sizeof(int) * 2 * (size_t)g.nbins * S, st);
-    if (err != cudaSuccess) return err;
     k_stats<<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, ws.partials, ws.counter, ws.stats,
                                            ws.status, center);
-    k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, g, rx, r2, ws.hist, ws.partials,
-                                               ws.counter, ws.stats, ws.status);
+    // records and chunk ranks: at most one block per chunk of the largest series
+    {
+        const size_t smP = sizeof(unsigned short) * 2 * (kThreadsPts / 32) * (size_t)g.nbins;
+        if ((err = allow_max_dynamic_smem((const void *)k_points<T>)) != cudaSuccess) return err;
+        int64_t npts = (max_nd + kChunk - 1) / kChunk;
+        if (npts > nred) npts = nred;
+        k_points<T><<<dim3((unsigned)npts, S), kThreadsPts, smP, st>>>(
+            t, y, dy, bt, g, rx, r2, ws.chist, ws.partials, ws.counter, ws.stats, ws.status);
+    }
     if (ev) cudaEventRecord(ev[1], st);
-    k_scan<<<S, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart, ws.cursor);
+    k_chunk_scan<<<dim3((2 * g.nbins + 31) / 32, S), 256, 0, st>>>(bt, g.nbins, ws.chist, ws.hist);
+    k_scan<<<S, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart);
     int nsc = (int)((max_nd + 255) / 256);
     if (nsc > 4096) nsc = 4096;
-    k_scatter<T><<<dim3(nsc, S), 256, 0, st>>>(bt, g, rx, r2, sx, s2, ws.cursor);
+    k_scatter<T><<<dim3(nsc, S), 256, 0, st>>>(bt, g, rx, r2, sx, s2, ws.binstart, ws.chist);
 
     if (ev) cudaEventRecord(ev[2], st);
     PassAArgs<T> A;

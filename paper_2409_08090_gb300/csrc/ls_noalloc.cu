@@ -140,8 +140,8 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     const size_t o_partials = c.take(sizeof(double) * 3 * (size_t)nred);
     const size_t o_hist = c.take(sizeof(int) * 2 * (size_t)g.nbins);
     const size_t o_binstart = c.take(sizeof(int) * 2 * ((size_t)g.nbins + 1));
-    const size_t o_cursor = c.take(sizeof(int) * 2 * (size_t)g.nbins);
-    const size_t rec = point_record_bytes<T>() * (size_t)nd + 4 * 256;   // carve() alignment
+    const size_t o_chist = c.take(sizeof(int) * (size_t)chunk_hist_entries(nd, 1, g.nbins));
+    const size_t rec = point_record_bytes<T>() * (size_t)nd + 5 * 256;   // carve() alignment
     size_t o_pts[4];
     for (int i = 0; i < 4; ++i) o_pts[i] = c.take(rec);
     const size_t o_H = c.take(3 * (size_t)n * sizeof(V));
@@ -161,7 +161,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     ws.partials = reinterpret_cast<double *>(base + o_partials);
     ws.hist = reinterpret_cast<int *>(base + o_hist);
     ws.binstart = reinterpret_cast<int *>(base + o_binstart);
-    ws.cursor = reinterpret_cast<int *>(base + o_cursor);
+    ws.chist = reinterpret_cast<int *>(base + o_chist);
     ws.pts_raw[0] = base + o_pts[0];
     ws.pts_raw[1] = base + o_pts[1];
     ws.pts_sorted[0] = base + o_pts[2];
