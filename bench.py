@@ -71,6 +71,9 @@ def parse_args():
                     help="serving: deliver results as host arrays or device tensor views")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single_large: skip the uniform-batch, ragged-batch and serving "
+                         "sub-blocks of the default line")
     return ap.parse_args()
 
 
@@ -186,6 +189,27 @@ def recorded_traffic(kernel: str, precision: str, workload: str):
     if not ent or ent.get("source_digest") != source_digest():
         return None
     return ent.get("dram_bytes_per_launch")
+
+
+def fp32_issue_roof(sms: int, mhz: float | None = None) -> dict:
+    """Roof of the FP64 path's double-float FFTs: they run on the FP32 units,
+    one FP32 operation per lane per clock (128 lanes per SM).  In the code's
+    double-float arithmetic an addition takes 11 FP32 operations (Knuth's
+    two-sum of the high parts, the low parts added, a renormalising fast
+    two-sum) and a multiplication 7 (the fma two-product plus the cross terms
+    and a renormalisation); a radix-2 butterfly's 10 flops are 6 additions and
+    4 multiplications, 94 FP32 operations, so one FP64-equivalent flop costs 9.4
+    FP32 operations."""
+    if mhz is None:
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+        except (OSError, KeyError, ValueError):
+            mhz = 2070.0
+    ops = sms * 128 * mhz * 1e6
+    return {"tflops": ops / 9.4 / 1e12,
+            "derivation": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz = {ops / 1e12:.1f} T FP32 "
+                          "ops/s; 9.4 FP32 ops per double-float flop (add 11, mul 7; a "
+                          "radix-2 butterfly's 6 adds + 4 muls)"}
 
 
 def algorithmic_bytes(info, nd: int, nf: int, precision: str) -> dict:
@@ -483,14 +507,19 @@ def run_ours(args):
         del g
     plan.close()
 
-    # -- the plain single-series FP64 path on the same series (context)
+    # -- the paper's precision: the FP64 path (eps 1e-9) on the same series,
+    # timed like the headline (L2 flushed, CUDA events), with its own accuracy
+    # block (same oracle sample) and two roofs: HBM for pass A's algorithmic
+    # bytes, and the FP32 issue rate its double-float FFTs run on
     fp64 = None
+    P64 = None
     if not args.no_fp64_path and args.precision == "fp32":
         p64 = nl.Plan(s.nd, s.nf, 1e-9, "fp64", device=local)
-        for _ in range(2):
+        info64 = p64.info
+        for _ in range(3):
             p64.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
         nl.ls_timing_enable(p64.handle, True)
-        n64 = 3
+        n64 = args.steps
         a = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
         b = [torch.cuda.Event(enable_timing=True) for _ in range(n64)]
         for i in range(n64):
@@ -499,12 +528,67 @@ def run_ours(args):
             p64.execute(t, y, dy, s.f0, s.df, out=out, sync=False)
             b[i].record()
         torch.cuda.synchronize()
+        if nl.ls_sync(p64.handle) != 0:
+            raise SystemExit("device status after the FP64 steps")
         ms64 = [x.elapsed_time(z) for x, z in zip(a, b)]
         sm64, c64 = nl.ls_timing_report(p64.handle)
-        fp64 = {"value": n64 / (sum(ms64) * 1e-3), "unit": UNIT, "eps": 1e-9,
-                "ms_per_step": sum(ms64) / n64,
-                "stage_ms": {nm: sm64[i] / max(c64, 1) for i, nm in enumerate(nl.STAGE_NAMES)}}
+        avg64 = {nm: sm64[i] / max(c64, 1) for i, nm in enumerate(nl.STAGE_NAMES)}
+        P64 = out.cpu().numpy()
+        alg64 = algorithmic_bytes(info64, s.nd, s.nf, "fp64")
+        hbm64 = alg64["pass_a_spread_fft"] / (avg64["pass_a_spread_fft"] * 1e-3) / 1e9
+        props = torch.cuda.get_device_properties(local)
+        fft_flops = 3 * 5 * info64.n * float(np.log2(info64.n))
+        passes_s = (avg64["pass_a_spread_fft"] + avg64["pass_b_fft_deconv_power"]) * 1e-3
+        roof = fp32_issue_roof(props.multi_processor_count)
+        fp64 = {"value": n64 / (sum(ms64) * 1e-3), "unit": UNIT, "eps": 1e-9, "steps": n64,
+                "ms_per_step": sum(ms64) / n64, "p50_ms": statistics.median(ms64),
+                "config": {"n": info64.n, "n1": info64.n1, "n2": info64.n2,
+                           "width": info64.width, "sigma": info64.sigma},
+                "stage_ms": avg64,
+                "roofline": {
+                    "hbm": {"bound": "hbm", "kernel": "k_passA", "achieved": hbm64,
+                            "peak": peak, "unit": "GB/s", "frac": hbm64 / peak,
+                            "algorithmic_bytes": alg64["pass_a_spread_fft"]},
+                    "fp32_issue": {"bound": "alu", "achieved": fft_flops / passes_s / 1e12,
+                                   "peak": roof["tflops"], "unit": "TFLOP/s",
+                                   "frac": fft_flops / passes_s / 1e12 / roof["tflops"],
+                                   "work": "5 n log2 n flops per fine-grid FFT, 3 grids, over "
+                                           "pass A + pass B time (which also spread, "
+                                           "deconvolve and evaluate the power)",
+                                   "derivation": roof["derivation"]}}}
         p64.close()
+
+    # -- batched and served workloads (BASELINE's configurations 3-5), compact
+    extras = {}
+    if world == 1 and args.workload == "single_large" and not args.no_extras:
+        import copy
+
+        def sub(**kw):
+            a2 = copy.copy(args)
+            a2.__dict__.update(kw)
+            return a2
+        del flush
+        torch.cuda.empty_cache()
+        uni = run_batch(sub(workload="uniform_batch", steps=5, warmup=2, batch_scale=1.0,
+                            batch_mode="graph"))
+        extras["uniform_batch"] = compact_batch(uni)
+        rag = run_batch(sub(workload="ragged_batch", steps=3, warmup=1, batch_scale=1.0,
+                            batch_mode="graph", no_e2e=True))
+        extras["ragged_batch"] = compact_batch(rag)
+        extras["ragged_batch"]["note"] = (
+            "10,000 series as configured; e2e left out here (its two pinned output buffers "
+            "would hold 28 GB of host memory): bench.py --workload ragged_batch reports it")
+        srv = run_serving(sub(batch_scale=1.0, serving_results="host"))
+        extras["serving"] = compact_serving(srv)
+        plain = srv["plain_fp64_one_at_a_time"]["value_by_eps"]
+        top32 = srv["per_rate"].get("20000_fp32", {}).get("periodograms_per_s")
+        extras["equal_accuracy"] = {
+            "plain_fp64_eps_1e-6_per_s": plain.get("eps_1e-06"),
+            "batched_fp32_over_plain_fp64": rag["value"] / plain["eps_1e-06"],
+            "served_fp32_over_plain_fp64": (top32 / plain["eps_1e-06"]) if top32 else None,
+            "note": "FP32 at eps 1e-6 against the plain one-at-a-time FP64 path at eps 1e-6 "
+                    "(the same rel-l2 class), on series drawn like the ragged batch; served: "
+                    "saturated at 20,000 offered requests/s"}
 
     if rank != 0:
         if pg:
@@ -524,6 +608,11 @@ def run_ours(args):
         accuracy = {"rel_l2": float(np.linalg.norm(P_g - P_o) / np.linalg.norm(P_o)),
                     "max_abs": float(np.max(np.abs(P_g - P_o))),
                     "frequencies": nk, "against": "FP64 oracle (direct sums)"}
+        if fp64 is not None:
+            d64 = P64[k] - P_o
+            fp64["accuracy"] = {"rel_l2": float(np.linalg.norm(d64) / np.linalg.norm(P_o)),
+                                "max_abs": float(np.max(np.abs(d64))), "frequencies": nk,
+                                "against": "FP64 oracle (direct sums), the same sample"}
 
     ms_sorted = sorted(step_ms)
     line = {
@@ -546,6 +635,7 @@ def run_ours(args):
         "stage_ms": avg, "stage_gbs": kern_gbs,
         "accuracy": accuracy, "cpu_baseline": cpu, "e2e": e2e, "fp64_path": fp64,
         "graph_replay": graph, "fft_reference": fft_ref,
+        **extras,
         "gpu_launches": kernels,
         "clocks": clk, "wall_s": wall,
     }
@@ -655,8 +745,9 @@ def run_batch(args):
                             "ms": statistics.median(ms), "host_ms": statistics.median(host)}
     for _ in range(args.warmup):
         step()
-    if nl.ls_sync(plan.handle) != 0:
-        raise SystemExit("device status after warm-up")
+    st = nl.ls_sync(plan.handle)
+    if st != 0:
+        raise SystemExit(f"{args.workload}: device status after warm-up: {nl.ls_status_str(st)}")
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -673,8 +764,9 @@ def run_batch(args):
     barrier(pg)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    if nl.ls_sync(plan.handle) != 0:
-        raise SystemExit("device status after timing")
+    st = nl.ls_sync(plan.handle)
+    if st != 0:
+        raise SystemExit(f"{args.workload}: device status after timing: {nl.ls_status_str(st)}")
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = allreduce_max(sum(step_ms), pg, device)
     value = world * ns * args.steps / (total_ms * 1e-3)
@@ -784,7 +876,7 @@ def run_batch(args):
     pb.close()
     plan.close()
     if rank != 0:
-        return 0
+        return None
     cpu = accuracy = None
     if not args.no_cpu_baseline and world == 1:
         import oracle
@@ -824,11 +916,10 @@ def run_batch(args):
         "batch_mode": args.batch_mode, "modes": mode_rates, "prepare_s": prepare_s,
         "prepared_layout": pb_info,
     }
-    print(json.dumps(line), flush=True)
     if pg:
         import torch.distributed as dist
         dist.destroy_process_group()
-    return 0
+    return line
 
 
 def run_serving(args):
@@ -847,7 +938,7 @@ def run_serving(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if int(os.environ.get("RANK", "0")) != 0:
-        return 0
+        return None
     nl.build.build()
     nl.load_library()
     pool = W.ragged_batch(seed=W.BASE_SEED + 4, nseries=max(64, int(600 * args.batch_scale)))
@@ -857,8 +948,9 @@ def run_serving(args):
                             results=args.serving_results)
     if args.serving_copy_limit is not None:
         srv.copy_limit = int(args.serving_copy_limit)
-    # warm the plans and grid classes once
-    warm = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, p) for s in pool[:32]
+    # warm the plans and every grid class of the pool once (a class's tables
+    # are built on its first request), so the timed runs allocate nothing
+    warm = [srv.submit(s.t, s.y, s.dy, s.f0, s.df, s.nf, p) for s in pool
             for p in ("fp32", "fp64")]
     for f in warm:
         f.result(timeout=600)
@@ -983,8 +1075,32 @@ def run_serving(args):
                                      "note": "ls_execute per request, plans reused, same pool"},
         "accuracy": accuracy, "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+def compact_batch(line: dict) -> dict:
+    """The batch line's figures for a sub-block of the default line."""
+    keep = ("value", "unit", "ms_per_step", "p50_ms", "p99_ms", "steps", "gpu_launches",
+            "batch_mode", "prepare_s")
+    out = {k: line.get(k) for k in keep}
+    out["workload"] = line["config"]["workload"]
+    out["series"] = line["config"]["series"]
+    out["roofline"] = {k: line["roofline"][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    out["accuracy"] = line.get("accuracy")
+    out["modes"] = {k: v["periodograms_per_s"] for k, v in line.get("modes", {}).items()}
+    e2e = line.get("e2e")
+    out["e2e"] = None if e2e is None else {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                              "d2h_bytes_per_step")}
+    return out
+
+
+def compact_serving(line: dict) -> dict:
+    """The serving line's figures for a sub-block of the default line."""
+    keep = ("requests", "p50_ms", "p99_ms", "periodograms_per_s", "offered_rate", "batches",
+            "peak_device_bytes", "plan_bytes", "budget")
+    return {"per_rate": {r: {k: v.get(k) for k in keep} for r, v in line["per_rate"].items()},
+            "plain_fp64_one_at_a_time": line["plain_fp64_one_at_a_time"],
+            "accuracy": line.get("accuracy"), "config": line["config"]}
 
 
 def main():
@@ -992,10 +1108,14 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("uniform_batch", "ragged_batch"):
-        return run_batch(args)
-    if args.workload == "serving":
-        return run_serving(args)
-    return run_ours(args)
+        line = run_batch(args)
+    elif args.workload == "serving":
+        line = run_serving(args)
+    else:
+        return run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -90,6 +90,10 @@ typedef struct {
     int32_t cols_per_block; /* fine-grid columns per pass-A block (bin width)  */
     int32_t fft_max_radix;  /* largest power-of-two radix among the stages of
                                the two sub-FFT schedules (N2 and N1)           */
+    int64_t batch_bytes;    /* device bytes the plan holds for batch calls:
+                               the lanes' workspaces and the grid classes'
+                               tables (workspace_bytes: the single-series
+                               workspace and tables)                           */
 } ls_plan_info;
 
 /*
@@ -302,8 +306,21 @@ ls_status ls_sync(ls_plan_t plan);
 ls_status ls_timing_enable(ls_plan_t plan, int enable);
 ls_status ls_timing_report(ls_plan_t plan, double *ms, int64_t *count);
 
-/* Fill *info with the plan's parameters. */
+/* Fill *info with the plan's parameters and the device bytes it holds. */
 ls_status ls_plan_describe(ls_plan_t plan, ls_plan_info *info);
+
+/*
+ * ls_plan_reserve_batch: allocate the plan's batch workspaces now -- per
+ * stream lane, the per-series arrays and an arena of a quarter of the batch
+ * budget (ls_plan_opts.batch_workspace_bytes) -- and create the lane streams,
+ * so that later ls_execute_batch / ls_execute_batch_shared calls whose
+ * launches fit the budget allocate no device memory and wait for no
+ * reallocation.  (A launch holding one series larger than a lane's share
+ * still grows that lane's arena.)  Grid-class tables are still built on
+ * first use of a class.  ls_plan_describe reports the bytes held
+ * (batch_bytes).
+ */
+ls_status ls_plan_reserve_batch(ls_plan_t plan);
 
 /* Release the plan and its device memory (synchronises its stream). */
 ls_status ls_destroy(ls_plan_t plan);

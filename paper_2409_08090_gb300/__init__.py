@@ -43,7 +43,7 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("nf", _i64), ("max_nd", _i64), ("n", _i64), ("n1", _i32), ("n2", _i32),
                 ("width", _i32), ("prec", _i32), ("beta", _dbl), ("eps", _dbl),
                 ("sigma", _dbl), ("workspace_bytes", _i64), ("cols_per_block", _i32),
-                ("fft_max_radix", _i32)]
+                ("fft_max_radix", _i32), ("batch_bytes", _i64)]
 
 
 class LSError(RuntimeError):
@@ -66,6 +66,7 @@ _SIGS = {
                                        _dbl, _i64, _dbl, ctypes.c_int, _c_void_p, _c_void_p]),
     "ls_sync": (ctypes.c_int, [_c_void_p]),
     "ls_plan_describe": (ctypes.c_int, [_c_void_p, ctypes.POINTER(PlanInfo)]),
+    "ls_plan_reserve_batch": (ctypes.c_int, [_c_void_p]),
     "ls_destroy": (ctypes.c_int, [_c_void_p]),
     "ls_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ls_choose_params": (ctypes.c_int, [_i64, _dbl, ctypes.c_int, _i64, _dbl,
@@ -225,6 +226,10 @@ def ls_plan_describe(plan: int) -> PlanInfo:
     return info
 
 
+def ls_plan_reserve_batch(plan: int) -> None:
+    _check(load_library().ls_plan_reserve_batch(_c_void_p(plan)), "ls_plan_reserve_batch")
+
+
 def ls_choose_params(nf: int, eps: float, prec: int = LS_FP64, max_nd: int | None = None,
                      upsampling: float = 0.0) -> dict:
     w, b, n, n1, n2, sg = _i32(), _dbl(), _i64(), _i32(), _i32(), _dbl()
@@ -350,6 +355,17 @@ class Plan:
                               batch_workspace_bytes, cols_per_block, fft_max_radix)
         self.info = ls_plan_describe(self.handle)
         self._batches = weakref.WeakSet()
+
+    def reserve_batch(self):
+        """Allocate the batch workspaces now (``ls_plan_reserve_batch``), so
+        that batch calls within the plan's batch budget allocate nothing."""
+        ls_plan_reserve_batch(self.handle)
+
+    def device_bytes(self) -> int:
+        """Device memory the plan holds: its single-series workspace and
+        tables, its batch workspaces and its grid classes' tables."""
+        info = ls_plan_describe(self.handle)
+        return int(info.workspace_bytes + info.batch_bytes)
 
     def close(self):
         """Destroy the plan (its prepared batches first: finalizers of objects
@@ -552,6 +568,11 @@ class GraphedExecute:
         return self.out
 
     def sync(self):
+        """Wait for the replays on the current stream and raise their device
+        errors.  The plan's stream is set to the current stream first: the
+        plan last ran on the capture's stream, which replays are not ordered
+        with, and the status read must follow the replays."""
+        ls_set_stream(self.plan.handle, self.plan._stream())
         _check(ls_sync(self.plan.handle), "graph replay (device status)")
         return self.out
 
@@ -632,6 +653,8 @@ class GraphedBatch:
         return self.out
 
     def sync(self):
+        """As GraphedExecute.sync: the status is read on the current stream."""
+        ls_set_stream(self.batch.plan.handle, self.batch.plan._stream())
         _check(ls_sync(self.batch.plan.handle), "graph replay (device status)")
         return self.out
 

@@ -341,6 +341,88 @@ __device__ __forceinline__ void dif_stage(V *buf, int colstride, const FftStage 
     }
 }
 
+// The first stage over columns that still hold the spread's fixed-point pairs
+// (FP32 path): element i of column c is the int pair at slot pad16(i), in
+// units of 2^(e - 30) with e = rexp of its row (rows of column c: rexp +
+// (c / BA) * rstride), or zero without a load where e marks an empty row.
+// The stage converts while it loads and writes FP32 complex values back to the
+// same slots (same bytes per cell), so no separate conversion pass is needed.
+constexpr signed char kEmptyRow = -128;
+template <int R, int NC>
+__device__ __forceinline__ void dif_stage_first_fixed(float2 *buf, int colstride, const FftStage &st,
+                                                      const float2 *roots, int L,
+                                                      const signed char *rexp, int BA, int rstride,
+                                                      int c0)
+{
+    const int m = st.m;
+    const int tmul = L / st.Ls;
+    const int2 *ibuf = reinterpret_cast<const int2 *>(buf);
+    for (int bi = threadIdx.x; bi < st.nb; bi += blockDim.x) {
+        int q, j;
+        if (st.shift >= 0) {
+            q = bi >> st.shift;
+            j = bi & (m - 1);
+        } else {
+            q = small_div(bi, m, st.inv_m);
+            j = bi - q * m;
+        }
+        const int base = q * st.Ls + j;
+        const int pb = pad16(base);
+        int off[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) off[r] = st.lin ? pb + st.off[r] : pad16(base + r * m);
+        float2 v[NC][R];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const signed char *re = rexp + ((c0 + c) / BA) * rstride;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int e = re[base + r * m];
+                if (e == kEmptyRow) {
+                    v[c][r] = make_float2(0.f, 0.f);
+                } else {
+                    const int2 iv = ibuf[c * colstride + off[r]];
+                    const float unit = __int_as_float((127 - 30 + e) << 23);
+                    v[c][r] = make_float2(__int2float_rn(iv.x) * unit, __int2float_rn(iv.y) * unit);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
+        if (j != 0) {
+            const int step = j * tmul;
+#pragma unroll
+            for (int k = 1; k < R; ++k) {
+                const float2 w = root_tw(roots, k * step);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[c * colstride + off[r]] = v[c][r];
+        }
+    }
+}
+
+template <int R, int G>
+__device__ __forceinline__ void first_stage_fixed_cols(float2 *buf, int ncol, int colstride,
+                                                       const FftStage &st, const float2 *roots,
+                                                       int L, const signed char *rexp, int BA,
+                                                       int rstride)
+{
+    int c0 = 0;
+    if (G > 1) {
+        for (; c0 + G <= ncol; c0 += G)
+            dif_stage_first_fixed<R, G>(buf + c0 * colstride, colstride, st, roots, L, rexp, BA,
+                                        rstride, c0);
+    }
+    for (; c0 < ncol; ++c0)
+        dif_stage_first_fixed<R, 1>(buf + c0 * colstride, colstride, st, roots, L, rexp, BA,
+                                    rstride, c0);
+}
+
 // One stage over `ncol` transforms, G at a time (G = 1 for the remainder).
 template <int R, int G, typename V>
 __device__ __forceinline__ void dif_stage_cols(V *buf, int ncol, int colstride, const FftStage &st,
@@ -358,10 +440,11 @@ __device__ __forceinline__ void dif_stage_cols(V *buf, int ncol, int colstride, 
 // time (at most 2 for radix 16, to stay within 128 registers in FP32).
 // Ends with a barrier; output in digit-reversed order (see slot_to_freq).
 template <int NC, typename V>
-__device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots)
+__device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots,
+                        int first = 0)
 {
     constexpr int NC16 = NC < 2 ? NC : 2;
-    for (int s = 0; s < fp.nstages; ++s) {
+    for (int s = first; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
         case 16: dif_stage_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L); break;
@@ -374,6 +457,28 @@ __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, cons
         }
         __syncthreads();
     }
+}
+
+// fft_dif over FP32 columns holding the spread's fixed-point pairs: the
+// first stage converts as it loads (dif_stage_first_fixed), the rest run as
+// usual.  Ends with a barrier.
+template <int NC>
+__device__ void fft_dif_fixed(float2 *buf, int ncol, int colstride, const FftPlan &fp,
+                              const float2 *roots, const signed char *rexp, int BA, int rstride)
+{
+    constexpr int NC16 = NC < 2 ? NC : 2;
+    const FftStage &st = fp.st[0];
+    switch (st.R) {
+    case 16: first_stage_fixed_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    case 9: first_stage_fixed_cols<9, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    case 8: first_stage_fixed_cols<8, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    case 4: first_stage_fixed_cols<4, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    case 5: first_stage_fixed_cols<5, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    case 3: first_stage_fixed_cols<3, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    default: first_stage_fixed_cols<2, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
+    }
+    __syncthreads();
+    fft_dif<NC>(buf, ncol, colstride, fp, roots, 1);
 }
 
 }  // namespace nls

@@ -38,18 +38,52 @@ struct BatchClass {
 // overlap on the device; the plan's stream waits for all of them.
 constexpr int kBatchLanes = 4;
 
+constexpr int kMaxBatchS = 16384;   // series per batch launch
+
+// Workspace of one batch lane.  The per-launch buffers (fine grids, point
+// records, bin totals and starts, chunk histograms) are carved for each launch
+// from one arena (carve_launch); the per-series arrays are sized once for
+// kMaxBatchS series.  The arena grows only when a launch needs more than it
+// holds; ls_plan_reserve_batch sizes it to the plan's lane budget up front, so
+// that later batch calls within the budget allocate nothing.
 struct BatchWorkspace {
-    Workspace ws;
-    int64_t cap_points = 0;   // point records
-    int cap_S = 0;            // series per launch
-    int64_t cap_cells = 0;    // elements of H (3 n S)
-    int cap_nred = 0;         // reduction blocks per series
-    int64_t ws_bins = 0;      // entries of each of hist, binstart
-    int64_t cap_chunk = 0;    // entries of chist
-    SeriesDesc *desc = nullptr;
-    std::vector<void *> allocs;
-    int64_t bytes = 0;
+    void *arena = nullptr;
+    int64_t arena_bytes = 0;
+    double *partials = nullptr;        // 3 (8 nsm + kMaxBatchS) reduction partials
+    unsigned int *counter = nullptr;   // 2 kMaxBatchS last-block tickets
+    Stats *stats = nullptr;            // kMaxBatchS
+    SeriesDesc *desc = nullptr;        // kMaxBatchS
+    std::vector<void *> allocs;        // the per-series arrays
+    int64_t bytes = 0;                 // arena + per-series arrays
 };
+
+// Offsets of one launch's buffers inside a lane arena (256-byte aligned).
+struct LaunchCarve {
+    size_t H, pts[4], hist, binstart, chist, bytes;
+};
+
+LaunchCarve carve_launch(int64_t n, int nbins, size_t cx, size_t recb, int64_t S, int64_t points,
+                         int64_t grids)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    LaunchCarve c;
+    size_t off = 0;
+    c.H = off;
+    off = al(off + cx * (size_t)n * (size_t)grids);
+    const size_t rec = recb * (size_t)points + 5 * 256;   // carve() alignment of each set
+    for (int i = 0; i < 4; ++i) {
+        c.pts[i] = off;
+        off = al(off + rec);
+    }
+    c.hist = off;
+    off = al(off + sizeof(int) * 2 * (size_t)nbins * (size_t)S);
+    c.binstart = off;
+    off = al(off + sizeof(int) * 2 * ((size_t)nbins + 1) * (size_t)S);
+    c.chist = off;
+    off = al(off + sizeof(int) * (size_t)chunk_hist_entries(points, (int)S, nbins));
+    c.bytes = off;
+    return c;
+}
 
 struct ls_plan_s {
     int device;
@@ -133,7 +167,8 @@ constexpr size_t kSmemPairBudget = 100 * 1024;   // two pass-A blocks per SM
 bool radix_schedule(int L, std::vector<int> &rad, int maxr = 16);
 
 // Shared memory of a one-column pass-A block (the smallest block a split can
-// use: padded column, per-column and root tables, slot table) plus 2 KB of
+// use: padded column, per-column and root tables, slot table, row exponents)
+// plus 2 KB of
 // margin: a column length above the opt-in limit cannot launch.  Called for
 // every candidate split of every series of a batch, so it only derives the
 // radix schedule (not the verified stage tables).
@@ -156,7 +191,7 @@ bool passA_column_fits(int64_t N2, int prec)
     const size_t nhi = (size_t)(N2 + 63) / 64;
     const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
     const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
-                         sizeof(int) * (size_t)(N2 / last) + 2048;
+                         sizeof(int) * (size_t)(N2 / last) + (size_t)N2 + 2048;   // + row exponents
     return bytes <= kSmemOptinBytes;
 }
 
@@ -449,7 +484,10 @@ ls_status upload(ls_plan_s *p, void **dst, const void *src, size_t bytes)
 {
     ls_status s = plan_alloc(p, dst, bytes);
     if (s != LS_OK) return s;
-    return cuda_status(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    // on the plan's stream, ahead of the kernels that read the table: a copy on
+    // the legacy stream is not ordered with non-blocking streams, and a
+    // pageable copy may return before its data has landed
+    return cuda_status(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, p->stream));
 }
 
 template <typename T>
@@ -472,21 +510,25 @@ ls_status upload_tables(ls_plan_s *p)
     if ((s = plan_alloc(p, &p->ws.deconv, (size_t)p->deconv_count * sizeof(T))) != LS_OK) return s;
     std::vector<double> z, wpsi;
     es_quadrature(g.w, g.beta, z, wpsi);
+    // The quadrature nodes stay with the plan (no free, which would
+    // synchronise the device); the table kernels run on the plan's stream,
+    // ahead of every launch that reads them (batch lanes wait for that stream).
     void *dq = nullptr;
-    cudaError_t e;
-    if ((e = cudaMalloc(&dq, 2 * z.size() * sizeof(double)))) return cuda_status(e);
+    if ((s = plan_alloc(p, &dq, 2 * z.size() * sizeof(double))) != LS_OK) return s;
     double *dz = static_cast<double *>(dq), *dw = dz + z.size();
-    cudaMemcpy(dz, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(dw, wpsi.data(), wpsi.size() * sizeof(double), cudaMemcpyHostToDevice);
-    e = launch_deconv_table<T>(g, p->ws.deconv, p->deconv_count, dz, dw, (int)z.size(), 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaFree(dq);
+    cudaError_t e = cudaMemcpyAsync(dz, z.data(), z.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dw, wpsi.data(), wpsi.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            p->stream);
+    if (e == cudaSuccess)
+        e = launch_deconv_table<T>(g, p->ws.deconv, p->deconv_count, dz, dw, (int)z.size(),
+                                   p->stream);
     if (e != cudaSuccess) return cuda_status(e);
     // the same table in pass-B order (coalesced reads in pass B)
     if ((s = plan_alloc(p, &p->ws.deconv_slot, (size_t)g.n * sizeof(T))) != LS_OK) return s;
-    e = launch_deconv_slot<T>(g, p->ws.deconv_slot, p->ws.deconv, p->deconv_count, 0);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    return cuda_status(e);
+    return cuda_status(
+        launch_deconv_slot<T>(g, p->ws.deconv_slot, p->ws.deconv, p->deconv_count, p->stream));
 }
 
 template <typename T>
@@ -518,7 +560,7 @@ ls_status plan_workspace(ls_plan_s *p, bool tables_only)
     p->ws.status = reinterpret_cast<int *>(static_cast<char *>(v) + 64);
     if ((s = plan_alloc(p, &v, sizeof(Stats))) != LS_OK) return s;
     p->ws.stats = static_cast<Stats *>(v);
-    cudaError_t e = cudaMemset(p->ws.counter, 0, 256);
+    cudaError_t e = cudaMemsetAsync(p->ws.counter, 0, 256, p->stream);
     if (e != cudaSuccess) return cuda_status(e);
     return upload_tables<T>(p);
 }
@@ -680,78 +722,84 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
 // ---------------------------------------------------------------------------
 void batch_free(ls_plan_s *p);
 
-// Make the batch workspace b hold S series, `points` records, `cells`
-// elements of H, `bins` entries in each of hist and binstart, `chunks` chunk
-// histogram entries and nred reduction blocks per series (the buffers grow by
-// a quarter beyond the request).  st is the
-// stream that last used b (synchronised before a reallocation); device errors
-// of its launches go to the status word `status`.
-template <typename T>
-ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int *status, int S, int64_t points,
-                     int64_t cells, int64_t bins, int64_t chunks, int nred, bool exact = false)
+// Give lane workspace b its per-series arrays (once) and an arena of at least
+// arena_need bytes (exact: no headroom).  st is the stream that last used b
+// (synchronised before the arena is replaced); device errors of its launches go
+// to the status word `status`.
+ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int nsm, int64_t arena_need,
+                     bool exact = false)
 {
-    if (S <= b.cap_S && points <= b.cap_points && cells <= b.cap_cells && nred <= b.cap_nred &&
-        bins <= b.ws_bins && chunks <= b.cap_chunk)
-        return LS_OK;
-    if (st) cudaStreamSynchronize(st);
-    for (void *a : b.allocs) cudaFree(a);
-    b.allocs.clear();
-    b.bytes = 0;
-    auto grow = [exact](int64_t need, int64_t have) {
-        return need > have ? need + (exact ? 0 : need / 4) : have;
-    };
-    b.cap_S = (int)grow(S, b.cap_S);
-    b.cap_points = grow(points, b.cap_points);
-    b.cap_cells = grow(cells, b.cap_cells);
-    b.cap_nred = (int)grow(nred, b.cap_nred);
-    b.ws_bins = grow(bins, b.ws_bins);
-    b.cap_chunk = grow(chunks, b.cap_chunk);
     auto alloc = [&](void **ptr, size_t bytes) -> ls_status {
         cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
         if (e != cudaSuccess) {
             *ptr = nullptr;
             return cuda_status(e);
         }
-        b.allocs.push_back(*ptr);
         b.bytes += (int64_t)bytes;
         return LS_OK;
     };
-    const size_t cx = sizeof(typename Cx<T>::type);
-    Workspace &ws = b.ws;
     ls_status s;
-    void *v;
-    if ((s = alloc(&ws.H, cx * (size_t)b.cap_cells)) != LS_OK) return s;
-    const size_t rec = point_record_bytes<T>() * (size_t)b.cap_points + 5 * 256;
-    for (int i = 0; i < 2; ++i) {
-        if ((s = alloc(&ws.pts_raw[i], rec)) != LS_OK) return s;
-        if ((s = alloc(&ws.pts_sorted[i], rec)) != LS_OK) return s;
+    if (!b.stats) {
+        void *v;
+        const size_t np = 3 * ((size_t)8 * nsm + kMaxBatchS);
+        if ((s = alloc(&v, sizeof(double) * np)) != LS_OK) return s;
+        b.allocs.push_back(v);
+        b.partials = static_cast<double *>(v);
+        if ((s = alloc(&v, sizeof(unsigned int) * 2 * kMaxBatchS)) != LS_OK) return s;
+        b.allocs.push_back(v);
+        b.counter = static_cast<unsigned int *>(v);
+        // cleared on the stream that will run the lane's launches (a clear on the
+        // legacy stream would not be ordered with the non-blocking lane streams)
+        if (cudaMemsetAsync(b.counter, 0, sizeof(unsigned int) * 2 * kMaxBatchS, st) !=
+            cudaSuccess)
+            return LS_ERR_CUDA;
+        if ((s = alloc(&v, sizeof(Stats) * kMaxBatchS)) != LS_OK) return s;
+        b.allocs.push_back(v);
+        b.stats = static_cast<Stats *>(v);
+        if ((s = alloc(&v, sizeof(SeriesDesc) * kMaxBatchS)) != LS_OK) return s;
+        b.allocs.push_back(v);
+        b.desc = static_cast<SeriesDesc *>(v);
     }
-    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
-    ws.hist = static_cast<int *>(v);
-    if ((s = alloc(&v, sizeof(int) * (size_t)b.ws_bins)) != LS_OK) return s;
-    ws.binstart = static_cast<int *>(v);
-    if ((s = alloc(&v, sizeof(int) * (size_t)b.cap_chunk)) != LS_OK) return s;
-    ws.chist = static_cast<int *>(v);
-    if ((s = alloc(&v, sizeof(double) * 3 * (size_t)b.cap_nred * b.cap_S)) != LS_OK) return s;
-    ws.partials = static_cast<double *>(v);
-    if ((s = alloc(&v, sizeof(unsigned int) * 2 * (size_t)b.cap_S)) != LS_OK) return s;
-    ws.counter = static_cast<unsigned int *>(v);
-    if (cudaMemset(ws.counter, 0, sizeof(unsigned int) * 2 * (size_t)b.cap_S) != cudaSuccess)
-        return LS_ERR_CUDA;
-    if ((s = alloc(&v, sizeof(Stats) * (size_t)b.cap_S)) != LS_OK) return s;
-    ws.stats = static_cast<Stats *>(v);
-    if ((s = alloc(&v, sizeof(SeriesDesc) * (size_t)b.cap_S)) != LS_OK) return s;
-    b.desc = static_cast<SeriesDesc *>(v);
-    ws.status = status;   // errors of batch launches reach ls_sync too
+    if (arena_need <= b.arena_bytes) return LS_OK;
+    if (b.arena) {
+        if (st) cudaStreamSynchronize(st);
+        cudaFree(b.arena);
+        b.bytes -= b.arena_bytes;
+        b.arena = nullptr;
+        b.arena_bytes = 0;
+    }
+    const int64_t want = exact ? arena_need : arena_need + arena_need / 4;
+    if ((s = alloc(&b.arena, (size_t)want)) != LS_OK) return s;
+    b.arena_bytes = want;
     return LS_OK;
 }
 
-template <typename T>
-ls_status batch_reserve(ls_plan_s *p, int lane, int S, int64_t points, int64_t cells, int64_t bins,
-                        int64_t chunks, int nred)
+void release_ws(BatchWorkspace &b)
 {
-    return reserve_ws<T>(p->bws[lane], p->lane_stream[lane], p->ws.status, S, points, cells, bins,
-                         chunks, nred);
+    if (b.arena) cudaFree(b.arena);
+    for (void *a : b.allocs) cudaFree(a);
+    b = BatchWorkspace();
+}
+
+// The workspace of one launch: its buffers carved from the lane arena, the
+// lane's per-series arrays, the plan's status word.
+Workspace lane_workspace(const BatchWorkspace &b, const LaunchCarve &c, int *status)
+{
+    Workspace ws = {};
+    char *a = static_cast<char *>(b.arena);
+    ws.H = a + c.H;
+    ws.pts_raw[0] = a + c.pts[0];
+    ws.pts_raw[1] = a + c.pts[1];
+    ws.pts_sorted[0] = a + c.pts[2];
+    ws.pts_sorted[1] = a + c.pts[3];
+    ws.hist = reinterpret_cast<int *>(a + c.hist);
+    ws.binstart = reinterpret_cast<int *>(a + c.binstart);
+    ws.chist = reinterpret_cast<int *>(a + c.chist);
+    ws.partials = b.partials;
+    ws.counter = b.counter;
+    ws.stats = b.stats;
+    ws.status = status;
+    return ws;
 }
 
 // Tile width (columns per pass-A block, also the bin width) and the largest
@@ -801,7 +849,7 @@ void choose_tiling(int prec, int n1, int n2, int cols_req, int maxr_req, int *ba
         const size_t nhi = (size_t)(n2 + 63) / 64;
         const size_t padded = (size_t)n2 + n2 / 16 + 1;
         return cx * ((size_t)ba * padded + (size_t)ba * (64 + nhi) + 64 + nhi) +
-               sizeof(int) * (size_t)(n2 / rad.back()) + 1024;
+               sizeof(int) * (size_t)(n2 / rad.back()) + (size_t)n2 + 1024;
     };
     // radix-8 stages need a larger slot table: keep 16 where it would not fit
     if (*maxrA == 8 && tile_bytes(BA) > kSmemOptinBytes) *maxrA = 16;
@@ -864,7 +912,12 @@ ls_status create_plan(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, in
     p->nred = 8 * nsm;
     ls_status s = (prec == LS_FP32) ? plan_workspace<float>(p, tables_only)
                                     : plan_workspace<double>(p, tables_only);
+    // A plan the caller holds may later run on another stream (ls_set_stream):
+    // its tables are complete when it is returned.  Batch classes (tables
+    // only) are used on lanes that wait for the creating stream instead.
+    if (s == LS_OK && !tables_only) s = cuda_status(cudaStreamSynchronize(p->stream));
     if (s != LS_OK) {
+        if (p->stream) cudaStreamSynchronize(p->stream);
         plan_free(p);
         delete p;
         return s;
@@ -883,8 +936,7 @@ void batch_free(ls_plan_s *p)
     }
     p->classes.clear();
     for (int l = 0; l < kBatchLanes; ++l) {
-        for (void *a : p->bws[l].allocs) cudaFree(a);
-        p->bws[l] = BatchWorkspace();
+        release_ws(p->bws[l]);
         if (p->lane_stream[l]) cudaStreamDestroy(p->lane_stream[l]);
         if (p->lane_done[l]) cudaEventDestroy(p->lane_done[l]);
         p->lane_stream[l] = nullptr;
@@ -975,21 +1027,52 @@ int batch_nred(const ls_plan_s *p, int S, int64_t max_nd)
     return nred < 1 ? 1 : nred;
 }
 
-// Enqueue the pipeline of one batch launch on stream st: workspace b (sized
-// for it), tables of the class plan `sub`, descriptors already on the device.
-// Kernels and memsets only, so the launch can be recorded by stream capture.
-template <typename T>
-ls_status enqueue_batch(const BatchWorkspace &b, cudaStream_t st, const ls_plan_s *sub,
-                        const Batch &bt, int64_t max_nd, int nred, const double *t,
-                        const double *y, const double *dy, double *power, int shared, int mode)
+// Arena carve of a launch of S series over `points` records on a grid of n
+// cells and nbins bins.
+LaunchCarve carve_for(int prec, int64_t n, int nbins, int64_t S, int64_t points, int shared)
 {
-    Workspace ws = b.ws;
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    const size_t recb = prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    const int64_t grids = shared ? S + 2 : 3 * S;
+    return carve_launch(n, nbins, cx, recb, S, points, grids);
+}
+
+LaunchCarve launch_carve(const ls_plan_s *sub, int64_t S, int64_t points, int shared)
+{
+    return carve_for(sub->prec, sub->g.n, sub->g.nbins, S, points, shared);
+}
+
+// Series per launch of a shared-times batch: as many of the `left` series as
+// fit lane_budget (at least one).
+int64_t shared_launch_size(int prec, int64_t n, int nbins, int64_t nd, int64_t left,
+                           int64_t lane_budget)
+{
+    int64_t S = 1;
+    while (S < kMaxBatchS && S < left &&
+           (int64_t)carve_for(prec, n, nbins, S + 1, (S + 1) * nd, 1).bytes <= lane_budget)
+        ++S;
+    return S;
+}
+
+// Enqueue the pipeline of one batch launch on stream st: its buffers carved
+// from lane workspace b (which holds them), tables of the class plan `sub`,
+// descriptors already on the device.  Kernels and memsets only, so the launch
+// can be recorded by stream capture.
+template <typename T>
+ls_status enqueue_batch(const BatchWorkspace &b, int *status, cudaStream_t st, const ls_plan_s *sub,
+                        const Batch &bt, int64_t points, int64_t max_nd, int nred,
+                        const double *t, const double *y, const double *dy, double *power,
+                        int shared, int mode)
+{
+    const LaunchCarve c = launch_carve(sub, bt.S, points, shared);
+    if ((int64_t)c.bytes > b.arena_bytes) return LS_ERR_ARG;
+    Workspace ws = lane_workspace(b, c, status);
     ws.twA = sub->ws.twA;
     ws.twB = sub->ws.twB;
     ws.tw4 = sub->ws.tw4;
     ws.deconv = sub->ws.deconv;
     ws.deconv_slot = sub->ws.deconv_slot;
-    return cuda_status(launch_pipeline<T>(sub->g, ws, b.cap_points, bt, max_nd, t, y, dy, power,
+    return cuda_status(launch_pipeline<T>(sub->g, ws, points, bt, max_nd, t, y, dy, power,
                                           nullptr, nred, st, nullptr, shared, mode));
 }
 
@@ -998,13 +1081,10 @@ ls_status batch_launch(ls_plan_s *p, int lane, const ls_plan_s *sub, const std::
                        int64_t points, int64_t max_nd, const double *t, const double *y,
                        const double *dy, double *power, int shared, int mode)
 {
-    const Geometry &g = sub->g;
     const int S = (int)descs.size();
-    const int64_t grids = shared ? S + 2 : 3 * (int64_t)S;
     const int nred = batch_nred(p, S, max_nd);
-    ls_status s = batch_reserve<T>(p, lane, S, points, g.n * grids,
-                                   2 * ((int64_t)g.nbins + 1) * S,
-                                   chunk_hist_entries(points, S, g.nbins), nred);
+    const LaunchCarve c = launch_carve(sub, S, points, shared);
+    ls_status s = reserve_ws(p->bws[lane], p->lane_stream[lane], p->nsm, (int64_t)c.bytes);
     if (s != LS_OK) return s;
     BatchWorkspace &b = p->bws[lane];
     cudaStream_t st = p->lane_stream[lane];
@@ -1015,7 +1095,8 @@ ls_status batch_launch(ls_plan_s *p, int lane, const ls_plan_s *sub, const std::
     bt.S = S;
     bt.many = b.desc;
     bt.one = descs[0];
-    return enqueue_batch<T>(b, st, sub, bt, max_nd, nred, t, y, dy, power, shared, mode);
+    return enqueue_batch<T>(b, p->ws.status, st, sub, bt, points, max_nd, nred, t, y, dy, power,
+                            shared, mode);
 }
 
 // Default batch budget: half of the free device memory, at most 8 GiB.
@@ -1076,7 +1157,6 @@ ls_status split_batch(const ls_plan_s *p, int64_t nseries, const int64_t *offset
     });
     const size_t cx = p->prec == LS_FP32 ? 8 : 16;
     const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
-    constexpr int kMaxBatchS = 16384;
     size_t i = 0;
     while (i < items.size()) {
         size_t j = i;
@@ -1087,6 +1167,10 @@ ls_status split_batch(const ls_plan_s *p, int64_t nseries, const int64_t *offset
             ++j;
         }
         classes.push_back(ClassSpec{items[i].pp, nf_max});
+        int BA = 1, mA = 16, mB = 16;     // the class plan's tile width, hence its bins
+        choose_tiling(p->prec, items[i].pp.n1, items[i].pp.n2, items[i].pp.cols, items[i].pp.maxr,
+                      &BA, &mA, &mB);
+        const int nbins = items[i].pp.n1 / BA;
         size_t k = i;
         while (k < j) {
             LaunchSpec L;
@@ -1094,8 +1178,11 @@ ls_status split_batch(const ls_plan_s *p, int64_t nseries, const int64_t *offset
             while (k < j && (int)L.descs.size() < kMaxBatchS) {
                 const int64_t s = items[k].s;
                 const int64_t nd = offsets[s + 1] - offsets[s];
-                const int64_t bytes = (int64_t)(3 * (size_t)items[k].pp.n * cx * (L.descs.size() + 1) +
-                                                4 * recb * (size_t)(L.points + nd));
+                const int64_t bytes = (int64_t)carve_launch(items[k].pp.n, nbins, cx, recb,
+                                                            (int64_t)L.descs.size() + 1,
+                                                            L.points + nd,
+                                                            3 * ((int64_t)L.descs.size() + 1))
+                                          .bytes;
                 if (!L.descs.empty() && bytes > lane_budget) break;
                 L.descs.push_back(make_series(offsets[s], L.points, nd, out_offsets[s], nf[s], f0[s],
                                               df[s]));
@@ -1125,11 +1212,8 @@ ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec
         b->subs.push_back(np);
         b->bytes += np->bytes;
     }
-    struct Need {
-        bool used = false;
-        int S = 0, nred = 0;
-        int64_t points = 0, cells = 0, bins = 0, chunks = 0;
-    } need[kBatchLanes];
+    int64_t need[kBatchLanes] = {};   // arena bytes per lane (largest launch)
+    bool used[kBatchLanes] = {};
     std::vector<SeriesDesc> all;
     int lane = 0;
     for (const LaunchSpec &L : launches) {
@@ -1144,23 +1228,14 @@ ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec
         pl.one = L.descs[0];
         pl.shared = shared;
         all.insert(all.end(), L.descs.begin(), L.descs.end());
-        const int64_t grids = shared ? pl.S + 2 : 3 * (int64_t)pl.S;
-        Need &n = need[lane];
-        n.used = true;
-        n.S = std::max(n.S, pl.S);
-        n.nred = std::max(n.nred, batch_nred(p, pl.S, pl.max_nd));
-        n.points = std::max(n.points, pl.points);
-        n.cells = std::max(n.cells, sub->g.n * grids);
-        n.bins = std::max(n.bins, 2 * ((int64_t)sub->g.nbins + 1) * pl.S);
-        n.chunks = std::max(n.chunks, chunk_hist_entries(pl.points, pl.S, sub->g.nbins));
+        used[lane] = true;
+        need[lane] = std::max(need[lane], (int64_t)launch_carve(sub, pl.S, pl.points, shared).bytes);
         b->launches.push_back(pl);
         lane = (lane + 1) % kBatchLanes;
     }
     for (int l = 0; l < kBatchLanes; ++l) {
-        if (!need[l].used) continue;
-        ls_status s = reserve_ws<T>(b->bws[l], nullptr, p->ws.status, need[l].S, need[l].points,
-                                    need[l].cells, need[l].bins, need[l].chunks, need[l].nred,
-                                    true);
+        if (!used[l]) continue;
+        ls_status s = reserve_ws(b->bws[l], p->stream, p->nsm, need[l], true);
         if (s != LS_OK) return s;
         b->bytes += b->bws[l].bytes;
     }
@@ -1170,7 +1245,11 @@ ls_status prepare_batch(ls_plan_s *p, ls_batch_s *b, const std::vector<ClassSpec
     if (e != cudaSuccess) return cuda_status(e);
     b->desc_all = static_cast<SeriesDesc *>(v);
     b->bytes += (int64_t)db;
-    return cuda_status(cudaMemcpy(b->desc_all, all.data(), db, cudaMemcpyHostToDevice));
+    // the class tables, counter clears and descriptors were enqueued on the
+    // plan's stream: complete before any run, whatever stream it comes on
+    cudaError_t e2 = cudaMemcpyAsync(b->desc_all, all.data(), db, cudaMemcpyHostToDevice, p->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(p->stream);
+    return cuda_status(e2);
 }
 
 void batch_release(ls_batch_s *b)
@@ -1180,10 +1259,7 @@ void batch_release(ls_batch_s *b)
         delete sp;
     }
     b->subs.clear();
-    for (BatchWorkspace &w : b->bws) {
-        for (void *a : w.allocs) cudaFree(a);
-        w = BatchWorkspace();
-    }
+    for (BatchWorkspace &w : b->bws) release_ws(w);
     if (b->desc_all) cudaFree(b->desc_all);
     b->desc_all = nullptr;
 }
@@ -1327,6 +1403,23 @@ ls_status ls_plan_ex(ls_plan_t *out, int64_t max_nd, int64_t nf, double eps, int
     return s;
 }
 
+ls_status ls_plan_reserve_batch(ls_plan_t p)
+{
+    if (!p) return LS_ERR_ARG;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    if (p->batch_budget <= 0) init_batch_budget(p);
+    ls_status st = lanes_begin(p);
+    if (st != LS_OK) return st;
+    LanesJoin join{p};
+    const int64_t lane_budget = p->batch_budget / kBatchLanes;
+    for (int l = 0; l < kBatchLanes; ++l) {
+        st = reserve_ws(p->bws[l], p->lane_stream[l], p->nsm, lane_budget, true);
+        if (st != LS_OK) return st;
+    }
+    return LS_OK;
+}
+
 ls_status ls_execute_batch(ls_plan_t p, int64_t nseries, const int64_t *offsets, const double *t,
                            const double *y, const double *dy, const double *f0, const double *df,
                            const int64_t *nf, const int64_t *out_offsets, double eps, int norm,
@@ -1391,9 +1484,6 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     ls_plan_s *sub = nullptr;
     if ((st = batch_class(p, pp, nf, &sub)) != LS_OK) return st;
     if (p->batch_budget <= 0) init_batch_budget(p);
-    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
-    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
-    constexpr int kMaxBatchS = 16384;
     const int64_t lane_budget = p->batch_budget / kBatchLanes;
     ls_status lst = lanes_begin(p);
     if (lst != LS_OK) return lst;
@@ -1402,11 +1492,8 @@ ls_status ls_execute_batch_shared(ls_plan_t p, int64_t nseries, int64_t nd, cons
     int64_t s0 = 0;
     while (s0 < nseries) {
         // series per launch within the budget: H holds S + 2 grids
-        int64_t S = 1;
-        while (S < kMaxBatchS && s0 + S < nseries &&
-               (int64_t)((size_t)pp.n * cx * (S + 3) + 4 * recb * (size_t)nd * (S + 1)) <=
-                   lane_budget)
-            ++S;
+        const int64_t S = shared_launch_size(p->prec, sub->g.n, sub->g.nbins, nd, nseries - s0,
+                                             lane_budget);
         std::vector<SeriesDesc> descs;
         descs.reserve((size_t)S);
         for (int64_t k = 0; k < S; ++k) {
@@ -1467,17 +1554,15 @@ ls_status ls_batch_prepare_shared(ls_plan_t p, ls_batch_t *out, int64_t nseries,
                           &pp.n2, &pp.sigma);
     if (st != LS_OK) return st;
     if (p->batch_budget <= 0) init_batch_budget(p);
-    const size_t cx = p->prec == LS_FP32 ? 8 : 16;
-    const size_t recb = p->prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
     const int64_t lane_budget = p->batch_budget / kBatchLanes;
     std::vector<ClassSpec> classes{ClassSpec{pp, nf}};
     std::vector<LaunchSpec> launches;
+    int BA = 1, mA = 16, mB = 16;     // the class plan's tile width, hence its bins
+    choose_tiling(p->prec, pp.n1, pp.n2, pp.cols, pp.maxr, &BA, &mA, &mB);
     for (int64_t s0 = 0; s0 < nseries;) {
-        int64_t S = 1;     // series per launch within the lane budget (as ls_execute_batch_shared)
-        while (S < 16384 && s0 + S < nseries &&
-               (int64_t)((size_t)pp.n * cx * (S + 3) + 4 * recb * (size_t)nd * (S + 1)) <=
-                   lane_budget)
-            ++S;
+        // series per launch within the lane budget (as ls_execute_batch_shared)
+        const int64_t S = shared_launch_size(p->prec, pp.n, pp.n1 / BA, nd, nseries - s0,
+                                             lane_budget);
         LaunchSpec L;
         L.cls = 0;
         L.points = S * nd;
@@ -1519,10 +1604,10 @@ ls_status ls_batch_run(ls_batch_t b, const double *t, const double *y, const dou
         const ls_plan_s *sub = b->subs[L.cls];
         cudaStream_t ls = p->lane_stream[L.lane];
         st = (p->prec == LS_FP32)
-                 ? enqueue_batch<float>(b->bws[L.lane], ls, sub, bt, L.max_nd, nred, t, y, dy, power,
-                                        L.shared, b->norm)
-                 : enqueue_batch<double>(b->bws[L.lane], ls, sub, bt, L.max_nd, nred, t, y, dy,
-                                         power, L.shared, b->norm);
+                 ? enqueue_batch<float>(b->bws[L.lane], p->ws.status, ls, sub, bt, L.points,
+                                        L.max_nd, nred, t, y, dy, power, L.shared, b->norm)
+                 : enqueue_batch<double>(b->bws[L.lane], p->ws.status, ls, sub, bt, L.points,
+                                         L.max_nd, nred, t, y, dy, power, L.shared, b->norm);
         if (st != LS_OK) return st;
     }
     return LS_OK;
@@ -1640,6 +1725,10 @@ ls_status ls_plan_describe(ls_plan_t p, ls_plan_info *info)
     info->eps = p->eps;
     info->sigma = p->sigma;
     info->workspace_bytes = p->bytes;
+    int64_t bb = 0;
+    for (int l = 0; l < kBatchLanes; ++l) bb += p->bws[l].bytes;
+    for (const BatchClass &c : p->classes) bb += c.sub->bytes;
+    info->batch_bytes = bb;
     info->cols_per_block = p->g.BA;
     int r = 0;
     for (const FftPlan *f : {&p->g.fa, &p->g.fb})

@@ -102,6 +102,8 @@ struct Stats {            // FP64 reductions, in device memory
     double scale;         // ~1/std(y): strengths are formed from scale * (y - ybar)
     double YY;            // sum of w^_j (scale (y_j - ybar))^2, the power's denominator
     double Y2;            // sum of w^_j y_j^2 (scale for the degeneracy test)
+    unsigned smax[3];     // per transform (s1, s2, s3): bits of an FP32 upper bound of the
+                          // largest strength component magnitude (the FP64 spread's grid)
 };
 
 struct Workspace {

@@ -179,6 +179,7 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
             const double m2 = WY2 / W;
             const double var = fmax(m2 - st->ybar * st->ybar, 1e-20 * m2);
             st->scale = (var > 0.0 && isfinite(var)) ? 1.0 / sqrt(var) : 1.0;
+            st->smax[0] = st->smax[1] = st->smax[2] = 0u;   // k_points takes the maxima
             *counter = 0u;
         }
     }
@@ -269,13 +270,13 @@ template <> struct Cis<float> {
 
 // Stable rank of this lane's key among the warp's earlier keys, continuing
 // the warp-private counts cnt[key] (which it then advances): lanes with equal
-// keys are ranked in lane order after everything counted before.  Inactive
-// lanes take no part; the result is 0 for them.  Warp-uniform call.
-__device__ __forceinline__ int warp_stable_rank(unsigned short *cnt, int key, bool active)
+// keys (peers: this lane's match mask among the active lanes) are ranked in lane
+// order after everything counted before.  Inactive lanes take no part; the
+// result is 0 for them.  Warp-uniform call.
+__device__ __forceinline__ int warp_stable_rank(unsigned short *cnt, int key, bool active,
+                                                unsigned peers)
 {
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
-    const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1 - (int)lane) & mask;
     int base = 0, r = 0;
     if (active) {
         base = cnt[key];
@@ -287,28 +288,28 @@ __device__ __forceinline__ int warp_stable_rank(unsigned short *cnt, int key, bo
     return r;
 }
 
+// Bits of an FP32 upper bound of max(|s.x|, |s.y|) (ordered like the value).
+__device__ __forceinline__ unsigned strength_bound_bits(float2 s)
+{
+    return __float_as_uint(fmaxf(fabsf(s.x), fabsf(s.y)));
+}
+__device__ __forceinline__ unsigned strength_bound_bits(double2 s)
+{
+    return __float_as_uint(__double2float_ru(fmax(fabs(s.x), fabs(s.y))));
+}
+
 
 // ---------------------------------------------------------------------------
-// K1b: per-point records, their stable in-chunk bin ranks, the chunk
-// histograms and the YY reduction.  Coordinates and pre-phases come from the
-// exact integer reduction; weights and the mean-subtracted data are FP64;
-// strengths are stored in T.  A block takes chunks of kChunk consecutive
-// records (warp w the records w kChunk/8 .. of the chunk, 32 at a time), ranks
-// every record among the chunk's earlier records of its bin (warp-private
-// counts, then an exclusive scan over the warps) and writes the chunk's bin
-// counts to its row of chist.  Dynamic shared memory: 2 x 8 x nbins counts.
+// K1b: per-point records + YY reduction.  Coordinates and pre-phases come
+// from the exact integer reduction; weights and the mean-subtracted data are
+// FP64; strengths are stored in T.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreadsPts)
-k_points(const double *__restrict__ t, const double *__restrict__ y,
-         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
-         PointSet<T> p2, int *chist, double *partials, unsigned int *counter,
-         Stats *st, int *status)
+__global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
+                         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
+                         PointSet<T> p2, double *partials, unsigned int *counter, Stats *st,
+                         int *status)
 {
-    using V = Cplx<T>;
-    extern __shared__ __align__(16) unsigned short wcnt[];   // [geometry][warp][bin]
-    constexpr int kWarps = kThreadsPts / 32;
-    constexpr int kSteps = kChunk / kThreadsPts;             // records per thread per chunk
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
     t += sd.pt_off;
@@ -318,8 +319,6 @@ k_points(const double *__restrict__ t, const double *__restrict__ y,
     const PhaseArgs ph = sd.ph;
     px = shifted(px, sd.rec_off);
     p2 = shifted(p2, sd.rec_off);
-    const int nbins = g.nbins;
-    const int64_t row0 = chunk_row0(sd.rec_off, ser);
     partials += (size_t)ser * 3 * gridDim.x;
     counter += 2 * ser + 1;
     st += ser;
@@ -328,76 +327,49 @@ k_points(const double *__restrict__ t, const double *__restrict__ y,
     const double ybar = st->ybar;
     const double scale = st->scale;
     double syy = 0.0, sy2 = 0.0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned short *cx = wcnt + (size_t)warp * nbins;                 // geometry x
-    unsigned short *c2 = wcnt + (size_t)(kWarps + warp) * nbins;      // geometry 2x
-    const int64_t nchunk = (nd + kChunk - 1) / kChunk;
-    for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-    __syncthreads();                      // the previous chunk is done with the counts
-    for (int i = threadIdx.x; i < kWarps * nbins; i += blockDim.x)
-        reinterpret_cast<uint32_t *>(wcnt)[i] = 0u;   // 2 x 8 x nbins 16-bit counts
-    __syncthreads();
-    uint32_t rk[kSteps], bins[kSteps];
-#pragma unroll
-    for (int step = 0; step < kSteps; ++step) {
-        const int64_t j = ch * kChunk + (int64_t)warp * (kChunk / kWarps) + step * 32 + lane;
-        const bool act = j < nd;
-        uint32_t ab1 = 0, ab2 = 0;
-        if (act) {
-            const double tj = t[j], yj = y[j];
-            const double d = dy ? dy[j] : 1.0;
-            const double wh = rcp_fp64(d * d) * invW;
-            const double yc = yj - ybar;
-            const double wyc = wh * yc;
-            syy = fma(wyc, yc, syy);
-            sy2 = fma(wh * yj, yj, sy2);
-            const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);          // frac(df t)
-            const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj)
-                          + (u128)(uint64_t)ph.K0 * Fx;                   // frac(fc t)
-            T r1, r2;
-            split_fixed<T>(Fx, g, ab1, r1);
-            split_fixed<T>(Fx << 1, g, ab2, r2);
-            const V p = Cis<T>::of(Fc);
-            const V q = Cis<T>::of(Fc << 1);
-            const T at = (T)(wyc * scale), wt = (T)wh;
-            px.ab[j] = ab1;
-            px.roff[j] = r1;
-            px.s[0][j] = mk2(at * p.x, at * p.y);
-            px.s[1][j] = mk2(wt * p.x, wt * p.y);
-            p2.ab[j] = ab2;
-            p2.roff[j] = r2;
-            p2.s[0][j] = mk2(wt * q.x, wt * q.y);
-        }
-        const int b1 = (int)((ab1 & 0xFFFFu) >> g.logBA), b2 = (int)((ab2 & 0xFFFFu) >> g.logBA);
-        bins[step] = (uint32_t)b1 | ((uint32_t)b2 << 16);
-        rk[step] = (uint32_t)warp_stable_rank(cx, b1, act) |
-                   ((uint32_t)warp_stable_rank(c2, b2, act) << 16);
+    unsigned m1 = 0u, m2 = 0u, m3 = 0u;   // strength bounds (bits), this thread's records
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double tj = t[j], yj = y[j];
+        const double d = dy ? dy[j] : 1.0;
+        const double wh = rcp_fp64(d * d) * invW;
+        const double yc = yj - ybar;
+        const double wyc = wh * yc;
+        syy = fma(wyc, yc, syy);
+        sy2 = fma(wh * yj, yj, sy2);
+        const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);          // frac(df t)
+        const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj)
+                      + (u128)(uint64_t)ph.K0 * Fx;                   // frac(fc t)
+        uint32_t ab1, ab2;
+        T r1, r2;
+        split_fixed<T>(Fx, g, ab1, r1);
+        split_fixed<T>(Fx << 1, g, ab2, r2);
+        const Cplx<T> p = Cis<T>::of(Fc);
+        const Cplx<T> q = Cis<T>::of(Fc << 1);
+        const T at = (T)(wyc * scale), wt = (T)wh;
+        const Cplx<T> s1 = mk2(at * p.x, at * p.y), s2 = mk2(wt * p.x, wt * p.y),
+                      s3 = mk2(wt * q.x, wt * q.y);
+        px.ab[j] = ab1;
+        px.roff[j] = r1;
+        px.s[0][j] = s1;
+        px.s[1][j] = s2;
+        p2.ab[j] = ab2;
+        p2.roff[j] = r2;
+        p2.s[0][j] = s3;
+        m1 = max(m1, strength_bound_bits(s1));
+        m2 = max(m2, strength_bound_bits(s2));
+        m3 = max(m3, strength_bound_bits(s3));
     }
-    __syncthreads();
-    // exclusive scan of each bin's counts over the warps (input order), the
-    // chunk's totals to its histogram row
-    for (int col = threadIdx.x; col < 2 * nbins; col += blockDim.x) {
-        const int geo = col >= nbins ? 1 : 0;
-        unsigned short *c = wcnt + (size_t)geo * kWarps * nbins + (col - geo * nbins);
-        int acc = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const int v = c[(size_t)w * nbins];
-            c[(size_t)w * nbins] = (unsigned short)acc;
-            acc += v;
-        }
-        chist[(row0 + ch) * 2 * nbins + col] = acc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int step = 0; step < kSteps; ++step) {
-        const int64_t j = ch * kChunk + (int64_t)warp * (kChunk / kWarps) + step * 32 + lane;
-        if (j < nd) {
-            const int b1 = (int)(bins[step] & 0xFFFFu), b2 = (int)(bins[step] >> 16);
-            px.rank[j] = ((rk[step] & 0xFFFFu) + cx[b1]) | (((rk[step] >> 16) + c2[b2]) << 16);
+    {
+        m1 = __reduce_max_sync(0xffffffffu, m1);
+        m2 = __reduce_max_sync(0xffffffffu, m2);
+        m3 = __reduce_max_sync(0xffffffffu, m3);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&st->smax[0], m1);
+            atomicMax(&st->smax[1], m2);
+            atomicMax(&st->smax[2], m3);
         }
     }
-    }   // chunks
     double a = block_sum(syy, sh);
     double b = block_sum(sy2, sh);
     if (threadIdx.x == 0) {
@@ -414,6 +386,86 @@ k_points(const double *__restrict__ t, const double *__restrict__ y,
             // A constant series: variance zero up to the rounding of the mean.
             if (!(YY > 1e-24 * Y2)) atomicOr(status, kStatDegenerate);
             *counter = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1c: stable in-chunk bin ranks and the chunk histograms.  A block takes
+// chunks of kChunk consecutive records (warp w the records w kChunk/8 .. of
+// the chunk, 32 at a time), ranks every record among the chunk's earlier
+// records of its bin (warp-private counts, then an exclusive scan over the
+// warps) and writes the chunk's bin counts to its row of chist.  Dynamic
+// shared memory: 2 x 8 x nbins 16-bit counts.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreadsPts)
+k_rank(Batch bt, Geometry g, const uint32_t *__restrict__ abx, const uint32_t *__restrict__ ab2x,
+       uint32_t *rank, int *chist)
+{
+    extern __shared__ __align__(16) unsigned short wcnt[];   // [geometry][warp][bin]
+    constexpr int kWarps = kThreadsPts / 32;
+    constexpr int kSteps = kChunk / kThreadsPts;             // records per thread per chunk
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    const int64_t nd = sd.nd;
+    abx += sd.rec_off;
+    ab2x += sd.rec_off;
+    rank += sd.rec_off;
+    const int nbins = g.nbins;
+    const int64_t row0 = chunk_row0(sd.rec_off, ser);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned short *cx = wcnt + (size_t)warp * nbins;                 // geometry x
+    unsigned short *c2 = wcnt + (size_t)(kWarps + warp) * nbins;      // geometry 2x
+    const int64_t nchunk = (nd + kChunk - 1) / kChunk;
+    for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+        __syncthreads();                      // the previous chunk is done with the counts
+        for (int i = threadIdx.x; i < kWarps * nbins; i += blockDim.x)
+            reinterpret_cast<uint32_t *>(wcnt)[i] = 0u;   // 2 x 8 x nbins 16-bit counts
+        __syncthreads();
+        uint32_t rk[kSteps], bins[kSteps];
+        uint32_t a1[kSteps], a2[kSteps];
+        const int64_t jw = ch * kChunk + (int64_t)warp * (kChunk / kWarps) + lane;
+#pragma unroll
+        for (int step = 0; step < kSteps; ++step) {      // all loads in flight first
+            const int64_t j = jw + step * 32;
+            a1[step] = j < nd ? __ldg(abx + j) : 0u;
+            a2[step] = j < nd ? __ldg(ab2x + j) : 0u;
+        }
+#pragma unroll
+        for (int step = 0; step < kSteps; ++step) {
+            const bool act = jw + step * 32 < nd;
+            const int b1 = (int)((a1[step] & 0xFFFFu) >> g.logBA);
+            const int b2 = (int)((a2[step] & 0xFFFFu) >> g.logBA);
+            bins[step] = (uint32_t)b1 | ((uint32_t)b2 << 16);
+            const unsigned amask = __ballot_sync(0xffffffffu, act);
+            const unsigned pe1 = __match_any_sync(0xffffffffu, act ? b1 : -1 - lane) & amask;
+            const unsigned pe2 = __match_any_sync(0xffffffffu, act ? b2 : -1 - lane) & amask;
+            rk[step] = (uint32_t)warp_stable_rank(cx, b1, act, pe1) |
+                       ((uint32_t)warp_stable_rank(c2, b2, act, pe2) << 16);
+        }
+        __syncthreads();
+        // exclusive scan of each bin's counts over the warps (input order), the
+        // chunk's totals to its histogram row
+        for (int col = threadIdx.x; col < 2 * nbins; col += blockDim.x) {
+            const int geo = col >= nbins ? 1 : 0;
+            unsigned short *c = wcnt + (size_t)geo * kWarps * nbins + (col - geo * nbins);
+            int acc = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const int v = c[(size_t)w * nbins];
+                c[(size_t)w * nbins] = (unsigned short)acc;
+                acc += v;
+            }
+            chist[(row0 + ch) * 2 * nbins + col] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int step = 0; step < kSteps; ++step) {
+            const int64_t j = jw + step * 32;
+            if (j < nd) {
+                const int b1 = (int)(bins[step] & 0xFFFFu), b2 = (int)(bins[step] >> 16);
+                rank[j] = ((rk[step] & 0xFFFFu) + cx[b1]) | (((rk[step] >> 16) + c2[b2]) << 16);
+            }
         }
     }
 }
@@ -538,6 +590,127 @@ __device__ __forceinline__ V tw4_root(const V *__restrict__ tw4, int64_t p)
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-point spreading.  Every cell of a column block is a sum of at most
+// `count` contributions s_j psi (count = the block's records, psi <= 1), each
+// at most maxs (the largest strength component among the block's bins) in
+// magnitude, so |cell| <= maxs count <= 2^e.  Each contribution is rounded to
+// a multiple of 2^(e - kBits) and the multiples are added exactly in integers
+// (range 2^(kBits + 1): one bit of headroom for the rounding, whose total is at
+// most count / 2 units).  Integer addition is associative, so a cell's value is
+// the same whatever the order of its additions: every kernel and grouping of
+// the spread gives bit-identical grids.  The rounding error per contribution is
+// at most 2^(e - kBits - 1): with kBits = 30 (FP32 path) about 1e-9 of the
+// block's bound, far below the FP32 tolerance, and with kBits = 62 (FP64 path)
+// about 2e-19 of it.
+// ---------------------------------------------------------------------------
+template <typename T> struct Fixed;
+template <> struct Fixed<float> {
+    using I = int;
+    static constexpr int kBits = 30;
+    __device__ static int of(float x) { return __float2int_rn(x); }
+    __device__ static void add(int *a, int v) { atomicAdd(a, v); }
+    __device__ static float to(int v, float lsb) { return __int2float_rn(v) * lsb; }
+};
+template <> struct Fixed<double> {
+    using I = long long;
+    static constexpr int kBits = 62;
+    __device__ static long long of(double x) { return __double2ll_rn(x); }
+    __device__ static void add(long long *a, long long v)
+    {
+        atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
+    }
+    __device__ static double to(long long v, double lsb) { return __ll2double_rn(v) * lsb; }
+};
+
+// Exponent e with 2^e above a nonnegative bound held as a float, read off its
+// bits (FP32 and integer operations only: this part issues FP64 at 1/64 of the
+// FP32 rate).  e is clamped to [-60, 100]: strengths are normalised (sum w^ =
+// 1, y scaled to unit variance), so contributions below 2^(-60 - kBits) are
+// negligible and bounds beyond 2^100 do not occur.
+__device__ __forceinline__ signed char exponent_above(float bound)
+{
+    const int ex = (int)((__float_as_uint(bound) >> 23) & 0xFFu);   // 0 for zero (or subnormal)
+    const int e = ex == 0 ? -60 : ex - 127 + 1;                     // bound < 2^(ex - 127 + 1)
+    return (signed char)min(max(e, -60), 100);
+}
+
+// Grid exponent for a cell bound of maxbits (a float's bits) times count,
+// the product rounded up.
+__device__ __forceinline__ signed char row_exponent(unsigned maxbits, unsigned count)
+{
+    return exponent_above(__fmul_ru(__uint_as_float(maxbits), __uint2float_ru(count)));
+}
+
+// 2^(kBits - e) and 2^(e - kBits), built from the exponent bits.
+__device__ __forceinline__ float fixed_scale(float, int e)
+{
+    return __int_as_float((127 + Fixed<float>::kBits - e) << 23);
+}
+__device__ __forceinline__ double fixed_scale(double, int e)
+{
+    return __longlong_as_double((long long)(1023 + Fixed<double>::kBits - e) << 52);
+}
+__device__ __forceinline__ float fixed_unit(float, int e)
+{
+    return __int_as_float((127 - Fixed<float>::kBits + e) << 23);
+}
+__device__ __forceinline__ double fixed_unit(double, int e)
+{
+    return __longlong_as_double((long long)(1023 - Fixed<double>::kBits + e) << 52);
+}
+
+// Exponent of the FP64 path's grid, one per block: every cell is a sum of at
+// most `count` contributions each at most the series' largest strength
+// component (smax bits); int64 leaves 62 bits below that bound, ample for it.
+__device__ __forceinline__ signed char block_exponent(unsigned smax_bits, int count)
+{
+    return row_exponent(smax_bits, (unsigned)count);
+}
+
+// The FP32 path's per-row bound.  Each record adds q = ceil(|s| 2^16 / M) to
+// its row (M: the series' largest strength component, so q <= 2^16; rounded
+// up, so M q / 2^16 >= |s|), an integer sum whatever the order; a row's cells
+// are then at most M qsum / 2^16, close to the sum of its records'
+// magnitudes.  Rows of 65536 or more records (qsum could overflow) take
+// M count instead.
+__device__ __forceinline__ unsigned row_units(unsigned sbits, float inv_m)
+{
+    return __float2uint_ru(__fmul_ru(__uint_as_float(sbits), inv_m));
+}
+constexpr signed char kRowEmpty = kEmptyRow;   // row exponent of a row no record reaches
+__device__ __forceinline__ signed char row_exponent_sum(unsigned m_bits, unsigned qsum,
+                                                       unsigned count)
+{
+    if (count == 0) return kRowEmpty;
+    const float m = __uint_as_float(m_bits);
+    const float bound = count < 65536u ? __fmul_ru(m, __uint2float_ru(qsum)) * 0x1p-16f
+                                       : __fmul_ru(m, __uint2float_ru(count));
+    return exponent_above(bound);
+}
+
+// Footprint of a record (first covered cell a + N1 b) in the column block
+// a0 .. a0 + BA - 1: the cells (cs + u, row), u < cnt, take kernel offsets
+// i0 + u.  All of them lie in one row (b, or b + 1 where the footprint wraps
+// past column N1 - 1): a block never holds both column N1 - 1 and column 0.
+struct Foot {
+    int i0, cs, cnt, row;
+};
+__device__ __forceinline__ Foot footprint(uint32_t ab, int a0, int BA, int N1, int N2, int w)
+{
+    const int aj = (int)(ab & 0xFFFFu);
+    const int bj = (int)(ab >> 16);
+    int o = aj - a0;
+    if (o < 0) o += N1;
+    Foot f;
+    if (o < BA) { f.i0 = 0; f.cs = o; }
+    else { f.i0 = N1 - o; f.cs = 0; }
+    f.cnt = min(BA - f.cs, w - f.i0);
+    f.row = bj + ((aj + f.i0 >= N1) ? 1 : 0);
+    if (f.row >= N2) f.row -= N2;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
 // Pass A: spread the block's points into BA columns of length N2 held in shared
 // memory, FFT each column, multiply by exp(2 pi i a d / n) and store
 // H[grid][d][a].  blockIdx.y selects the transform: 0 -> s1 (x), 1 -> s2 (x),
@@ -551,6 +724,7 @@ struct PassAArgs {
     int nofit;             // 1: the model has no offset; s2 is not needed
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
+    const Stats *st;       // per series: the strength maxima (FP64 grids)
     const Cplx<T> *twA;    // two-level root table, length N2
     const Cplx<T> *tw4;    // four-step table (lo 4096, hi)
     Cplx<T> *H;
@@ -687,6 +861,79 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     }
     const int cnt0 = r0e - r0s;
     const int total = cnt0 + (r1e - r1s);
+    using I = typename Fixed<T>::I;
+    // Per-row bounds of the fixed-point grids (FP32; pass 1 over the block's
+    // records): count and strength units (row_units) of the records whose
+    // footprint row is b, gathered with integer atomics (order-free) in the
+    // column buffer before it is zeroed, then one exponent per row.  The FP64
+    // grid takes one exponent for the block (block_exponent).
+    uint32_t *rcnt = reinterpret_cast<uint32_t *>(smem_raw);    // N2 counts, N2 unit sums
+    uint32_t *rmax = rcnt + N2;
+    signed char *rexp = reinterpret_cast<signed char *>(dtab + (N2 >> g.fa.logRlast));
+    for (int i = threadIdx.x; i < 2 * N2; i += blockDim.x) rcnt[i] = 0u;
+    if (build_tables) {
+        load_roots(roots, A.twA, N2);
+        fill_slot_table(dtab, g.fa);
+        for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
+            const int col = i >> 6;
+            alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
+        }
+        for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
+            const int col = i / nhi;
+            const int dh = i - col * nhi;
+            ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
+        }
+    }
+    __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+        const unsigned mbits = A.st[ser].smax[grid];
+        const float inv_m = __fdiv_ru(65536.0f, __uint_as_float(mbits));
+        // kRow records per thread in flight at a time
+        constexpr int kRow = 4;
+        for (int e0 = threadIdx.x; e0 < total; e0 += kRow * blockDim.x) {
+            uint32_t abq[kRow];
+            V sq[kRow];
+#pragma unroll
+            for (int q = 0; q < kRow; ++q) {
+                const int e = e0 + q * (int)blockDim.x;
+                if (e < total) {
+                    const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
+                    abq[q] = __ldg(P.ab + j);
+                    sq[q] = __ldg(str + j);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRow; ++q) {
+                if (e0 + q * (int)blockDim.x >= total) break;
+                const Foot f = footprint(abq[q], a0, BA, N1, N2, g.w);
+                if (f.cnt <= 0) continue;
+                atomicAdd(rcnt + f.row, 1u);
+                atomicAdd(rmax + f.row, row_units(strength_bound_bits(sq[q]), inv_m));
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < N2; b += blockDim.x)
+            rexp[b] = row_exponent_sum(mbits, rmax[b], rcnt[b]);
+    } else {
+        const signed char eb = block_exponent(A.st[ser].smax[grid], total);
+        for (int b = threadIdx.x; b < N2; b += blockDim.x) rexp[b] = eb;
+    }
+    __syncthreads();
+    I *ibuf = reinterpret_cast<I *>(buf);       // the columns as fixed-point pairs while spreading
+    if constexpr (sizeof(T) == 4) {
+        // only rows that records reach take additions; the conversion below
+        // writes the others' zeros
+        for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+            if (rexp[b] == kRowEmpty) continue;
+            for (int col = 0; col < BA; ++col) {
+                I *c = ibuf + 2 * ((size_t)col * Lp + pad16(b));
+                c[0] = 0;
+                c[1] = 0;
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < 2 * BA * Lp; i += blockDim.x) ibuf[i] = 0;
+    }
     // kPre records per thread are loaded before any is used, so their global
     // loads overlap instead of forming one dependent chain per record.
     constexpr int kPre = 4;
@@ -706,24 +953,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         }
     };
     load_chunk((int)threadIdx.x);
-
-    for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
-    if (build_tables) {
-        load_roots(roots, A.twA, N2);
-        fill_slot_table(dtab, g.fa);
-        for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
-            const int col = i >> 6;
-            alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
-        }
-        for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
-            const int col = i / nhi;
-            const int dh = i - col * nhi;
-            ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
-        }
-    }
     __syncthreads();
 
-    // ---- spread ----
+    // ---- spread: each contribution rounded to its row's grid, added exactly ----
     const T halfw = T(0.5) * T(g.w);
     const T zscale = T(2) / T(g.w);
     const T beta = T(g.beta);
@@ -737,42 +969,43 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
 #pragma unroll
         for (int q = 0; q < kPre; ++q) {
             if (e0 + q * (int)blockDim.x >= total) break;
-            const uint32_t ab = abv[q];
-            const int aj = (int)(ab & 0xFFFFu);
-            const int bj = (int)(ab >> 16);
-            // footprint columns aj .. aj+w-1 (mod N1) against block a0 .. a0+BA-1
-            int o = aj - a0;
-            if (o < 0) o += N1;
-            int i0, cs;
-            if (o < BA) { i0 = 0; cs = o; }
-            else { i0 = N1 - o; cs = 0; }
-            const int cnt = min(BA - cs, g.w - i0);
+            const Foot f = footprint(abv[q], a0, BA, N1, N2, g.w);
+            if (f.cnt <= 0) continue;
             const T roff = rv[q];
-            const V s = sv[q];
-            for (int u = 0; u < cnt; ++u) {
-                const int i = i0 + u;
-                int b = bj + ((aj + i >= N1) ? 1 : 0);
-                if (b >= N2) b -= N2;
-                const T z = (roff - halfw + T(i)) * zscale;
+            const T fs = fixed_scale(T(0), rexp[f.row]);
+            const V s = mk2(sv[q].x * fs, sv[q].y * fs);     // exact: a power of two
+            I *dst = ibuf + 2 * ((size_t)f.cs * Lp + pad16(f.row));
+            for (int u = 0; u < f.cnt; ++u) {
+                const T z = (roff - halfw + T(f.i0 + u)) * zscale;
                 T v;
                 if constexpr (sizeof(T) == 8) v = dfl_ok ? es_kernel_dfl(z, beta_dfl) : es_kernel(z, beta);
                 else v = es_kernel(z, beta);
-                V *dst = buf + (size_t)(cs + u) * Lp + pad16(b);
-                atomicAdd(&dst->x, s.x * v);
-                atomicAdd(&dst->y, s.y * v);
+                Fixed<T>::add(dst, Fixed<T>::of(s.x * v));
+                Fixed<T>::add(dst + 1, Fixed<T>::of(s.y * v));
+                dst += 2 * (size_t)Lp;
             }
         }
     }
     __syncthreads();
 
-    // ---- column FFTs over b ----
-    if constexpr (sizeof(T) == 8) {
-        // FP64 accumulators -> double-float, in place (same 16 bytes per cell)
-        for (int i = threadIdx.x; i < BA * Lp; i += blockDim.x) bufF[i] = to_fft(buf[i]);
+    // ---- column FFTs over b.  FP32: the first stage reads the fixed-point
+    // pairs, converts them with their rows' units and skips empty rows' loads.
+    // FP64: convert in place first (same 16 bytes per cell) ----
+    if constexpr (sizeof(T) == 4) {
+        if ((BA & 1) == 0) fft_dif_fixed<2>(bufF, BA, Lp, g.fa, roots, rexp, BA, 0);
+        else fft_dif_fixed<1>(bufF, BA, Lp, g.fa, roots, rexp, BA, 0);
+    } else {
+        for (int col = 0; col < BA; ++col) {
+            for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+                const size_t i = (size_t)col * Lp + pad16(b);
+                const T unit = fixed_unit(T(0), rexp[b]);
+                bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
+                                     Fixed<T>::to(ibuf[2 * i + 1], unit)));
+            }
+        }
         __syncthreads();
+        fft_dif<1>(bufF, BA, Lp, g.fa, roots);
     }
-    if (sizeof(T) == 4 && (BA & 1) == 0) fft_dif<2>(bufF, BA, Lp, g.fa, roots);
-    else fft_dif<1>(bufF, BA, Lp, g.fa, roots);
 
     // ---- twiddle exp(2 pi i a d / n) and store H[grid][d][a], slot order ----
     if constexpr (kCluster) {
@@ -901,7 +1134,11 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
     __shared__ const T *g_roff[kMaxGroup];
     __shared__ const Cplx<T> *g_str[kMaxGroup];
     __shared__ int g_slot[kMaxGroup];
+    __shared__ signed char g_exp[kMaxGroup];   // FP64: one grid exponent per member
+    __shared__ unsigned g_mbits[kMaxGroup];    // FP32: the member's strength maximum (bits)
+    __shared__ float g_invm[kMaxGroup];        // and 2^16 over it, rounded up
     using V = Cplx<T>;
+    using I = typename Fixed<T>::I;
     using F = typename FftOf<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geometry &g = A.g;
@@ -937,11 +1174,19 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
     const int S = A.shared ? A.ny - 2 : A.ny / 3;
     const int ni = A.shared ? S : (A.nofit ? 2 * S : 3 * S);
 
+    signed char *rexp = reinterpret_cast<signed char *>(dtab + (N2 >> g.fa.logRlast));   // G x N2
+
     for (int s0 = blockIdx.y * G; s0 < ni; s0 += gridDim.y * G) {
         const int gact = min(G, ni - s0);
         __syncthreads();                  // tables ready / the previous group is stored
-        for (int i = threadIdx.x; i < gact * BA * Lp; i += blockDim.x) buf[i] = mk2(T(0), T(0));
-        __syncthreads();
+        I *ibuf = reinterpret_cast<I *>(buf);   // fixed-point pairs while spreading
+        // per-row bounds of member r: N2 counts and N2 max bits at the start of
+        // its column region (before the region is zeroed for the spread)
+        auto rows_of = [&](int r) {
+            return reinterpret_cast<uint32_t *>(buf + (size_t)r * BA * Lp);
+        };
+        for (int r = 0; r < gact; ++r)
+            for (int i = threadIdx.x; i < 2 * N2; i += blockDim.x) rows_of(r)[i] = 0u;
         // record ranges of the group's series (rows of grp: first range start,
         // its length, second range start, exclusive prefix of the totals)
         if ((int)threadIdx.x < gact) {
@@ -985,6 +1230,9 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
             grp[4 * r + 1] = r0e - r0s;
             grp[4 * r + 2] = r1s;
             grp[4 * r + 3] = (r0e - r0s) + (r1e - r1s);
+            g_exp[r] = block_exponent(A.st[ser].smax[grid], grp[4 * r + 3]);
+            g_mbits[r] = A.st[ser].smax[grid];
+            g_invm[r] = __fdiv_ru(65536.0f, __uint_as_float(g_mbits[r]));
         }
         __syncthreads();
         if (threadIdx.x == 0) {           // prefix of the totals
@@ -998,6 +1246,71 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
         }
         __syncthreads();
         const int all = grp[4 * kMaxGroup];
+        // member and record index of the group's e-th record
+        auto locate = [&](int e, int &r) {
+            r = 0;
+            while (r + 1 < gact && grp[4 * (r + 1) + 3] <= e) ++r;
+            const int el = e - grp[4 * r + 3];
+            return (el < grp[4 * r + 1]) ? grp[4 * r] + el : grp[4 * r + 2] + el - grp[4 * r + 1];
+        };
+        if constexpr (sizeof(T) == 4) {
+            // pass 1: per-row counts and largest strength bounds (integer
+            // atomics), kRow records per thread in flight
+            constexpr int kRow = 4;
+            for (int e0 = threadIdx.x; e0 < all; e0 += kRow * blockDim.x) {
+                uint32_t abq[kRow];
+                V sq[kRow];
+                int rq[kRow];
+#pragma unroll
+                for (int q = 0; q < kRow; ++q) {
+                    const int e = e0 + q * (int)blockDim.x;
+                    rq[q] = -1;
+                    if (e < all) {
+                        int r;
+                        const int j = locate(e, r);
+                        abq[q] = __ldg(g_ab[r] + j);
+                        sq[q] = __ldg(g_str[r] + j);
+                        rq[q] = r;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kRow; ++q) {
+                    if (rq[q] < 0) break;
+                    const Foot f = footprint(abq[q], a0, BA, N1, N2, g.w);
+                    if (f.cnt <= 0) continue;
+                    uint32_t *rc = rows_of(rq[q]);
+                    atomicAdd(rc + f.row, 1u);
+                    atomicAdd(rc + N2 + f.row, row_units(strength_bound_bits(sq[q]), g_invm[rq[q]]));
+                }
+            }
+            __syncthreads();
+            for (int r = 0; r < gact; ++r) {
+                const uint32_t *rc = rows_of(r);
+                for (int b = threadIdx.x; b < N2; b += blockDim.x)
+                    rexp[r * N2 + b] = row_exponent_sum(g_mbits[r], rc[N2 + b], rc[b]);
+            }
+        } else {
+            for (int r = 0; r < gact; ++r)
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) rexp[r * N2 + b] = g_exp[r];
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            // only rows that records reach take additions (the conversion
+            // writes the others' zeros)
+            for (int r = 0; r < gact; ++r) {
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+                    if (rexp[r * N2 + b] == kRowEmpty) continue;
+                    for (int col = 0; col < BA; ++col) {
+                        I *c = ibuf + 2 * ((size_t)(r * BA + col) * Lp + pad16(b));
+                        c[0] = 0;
+                        c[1] = 0;
+                    }
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < 2 * gact * BA * Lp; i += blockDim.x) ibuf[i] = 0;
+        }
+        __syncthreads();
         // kPre records per thread in flight, over the group's records in turn
         constexpr int kPre = 4;
         for (int e0 = threadIdx.x; e0 < all; e0 += kPre * blockDim.x) {
@@ -1010,11 +1323,8 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
                 const int e = e0 + q * (int)blockDim.x;
                 rr[q] = -1;
                 if (e < all) {
-                    int r = 0;
-                    while (r + 1 < gact && grp[4 * (r + 1) + 3] <= e) ++r;
-                    const int el = e - grp[4 * r + 3];
-                    const int j = (el < grp[4 * r + 1]) ? grp[4 * r] + el
-                                                        : grp[4 * r + 2] + el - grp[4 * r + 1];
+                    int r;
+                    const int j = locate(e, r);
                     abv[q] = __ldg(g_ab[r] + j);
                     rv[q] = __ldg(g_roff[r] + j);
                     sv[q] = __ldg(g_str[r] + j);
@@ -1024,37 +1334,41 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
 #pragma unroll
             for (int q = 0; q < kPre; ++q) {
                 if (rr[q] < 0) break;
-                const uint32_t ab = abv[q];
-                const int aj = (int)(ab & 0xFFFFu);
-                const int bj = (int)(ab >> 16);
-                int o = aj - a0;
-                if (o < 0) o += N1;
-                int i0, cs;
-                if (o < BA) { i0 = 0; cs = o; }
-                else { i0 = N1 - o; cs = 0; }
-                const int cnt = min(BA - cs, g.w - i0);
-                V *cols = buf + (size_t)rr[q] * BA * Lp;
-                for (int u = 0; u < cnt; ++u) {
-                    const int i = i0 + u;
-                    int b = bj + ((aj + i >= N1) ? 1 : 0);
-                    if (b >= N2) b -= N2;
-                    const T z = (rv[q] - halfw + T(i)) * zscale;
+                const Foot f = footprint(abv[q], a0, BA, N1, N2, g.w);
+                if (f.cnt <= 0) continue;
+                const T fs = fixed_scale(T(0), rexp[rr[q] * N2 + f.row]);
+                const V sq = mk2(sv[q].x * fs, sv[q].y * fs);     // exact: a power of two
+                I *dst = ibuf + 2 * ((size_t)(rr[q] * BA + f.cs) * Lp + pad16(f.row));
+                for (int u = 0; u < f.cnt; ++u) {
+                    const T z = (rv[q] - halfw + T(f.i0 + u)) * zscale;
                     T v;
                     if constexpr (sizeof(T) == 8) v = dfl_ok ? es_kernel_dfl(z, beta_dfl) : es_kernel(z, beta);
                     else v = es_kernel(z, beta);
-                    V *dst = cols + (size_t)(cs + u) * Lp + pad16(b);
-                    atomicAdd(&dst->x, sv[q].x * v);
-                    atomicAdd(&dst->y, sv[q].y * v);
+                    Fixed<T>::add(dst, Fixed<T>::of(sq.x * v));
+                    Fixed<T>::add(dst + 1, Fixed<T>::of(sq.y * v));
+                    dst += 2 * (size_t)Lp;
                 }
             }
         }
         __syncthreads();
+        // FP32: the first FFT stage converts the fixed-point pairs as it loads
+        // (fft_dif_fixed); FP64: convert in place first
         if constexpr (sizeof(T) == 8) {
-            for (int i = threadIdx.x; i < gact * BA * Lp; i += blockDim.x) bufF[i] = to_fft(buf[i]);
+            for (int c = 0; c < gact * BA; ++c) {
+                const signed char *re = rexp + (c / BA) * N2;
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+                    const size_t i = (size_t)c * Lp + pad16(b);
+                    const T unit = fixed_unit(T(0), re[b]);
+                    bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
+                                         Fixed<T>::to(ibuf[2 * i + 1], unit)));
+                }
+            }
             __syncthreads();
         }
-        if (sizeof(T) == 4) fft_dif<2>(bufF, gact * BA, Lp, g.fa, roots);
-        else fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
+        if constexpr (sizeof(T) == 4)
+            fft_dif_fixed<2>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
+        else
+            fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
         // twiddle exp(2 pi i a d / n) and store H[2 + s][d][a], slot order; the
         // BA columns of a row go out as 16-byte units
         for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
@@ -1680,11 +1994,13 @@ static int blocks_per_sm(size_t smem)
     return (int)((size_t)228 * 1024 / (smem + 1024));
 }
 
+// Columns, per-column and root tables, slot table, and one exponent byte per
+// row (the spread's per-row fixed-point grids).
 size_t passA_smem_bytes(const Geometry &g, size_t cx, int cs)
 {
     const size_t nhi = (size_t)(g.N2 + 63) / 64;
     return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)cs * g.BA * (64 + nhi) + 64 + nhi) +
-           sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
+           sizeof(int) * (size_t)(g.N2 / g.fa.Rlast) + (size_t)g.N2;
 }
 
 size_t passB_smem_bytes(const Geometry &g, size_t cx)
@@ -1792,7 +2108,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
                             const double *dy, double *power, double *sums, int nred,
                             cudaStream_t st, cudaEvent_t *ev, int shared, int mode)
 {
-    int nk = 5;    // kernels enqueued: stats, points, chunk scan, scan, scatter, then the passes
+    int nk = 6;    // kernels enqueued: stats, points, rank, chunk scan, scan, scatter, then the passes
     const int nofit = (mode & kModeNoFit) ? 1 : 0;
     const int center = (!nofit || !(mode & kModeNoCenter)) ? 1 : 0;
     cudaError_t err;
@@ -1800,19 +2116,27 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     PointSet<T> rx = carve<T>(ws.pts_raw[0], capacity), r2 = carve<T>(ws.pts_raw[1], capacity);
     PointSet<T> sx = carve<T>(ws.pts_sorted[0], capacity), s2 = carve<T>(ws.pts_sorted[1], capacity);
 
+    int nsm = 0, dev_id = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+    if (nsm <= 0) nsm = 152;
     if (ev) cudaEventRecord(ev[0], st);
     k_stats<<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, ws.partials, ws.counter, ws.stats,
                                            ws.status, center);
-    // records and chunk ranks: at most one block per chunk of the largest series
-    {
-        const size_t smP = sizeof(unsigned short) * 2 * (kThreadsPts / 32) * (size_t)g.nbins;
-        if ((err = allow_max_dynamic_smem((const void *)k_points<T>)) != cudaSuccess) return err;
-        int64_t npts = (max_nd + kChunk - 1) / kChunk;
-        if (npts > nred) npts = nred;
-        k_points<T><<<dim3((unsigned)npts, S), kThreadsPts, smP, st>>>(
-            t, y, dy, bt, g, rx, r2, ws.chist, ws.partials, ws.counter, ws.stats, ws.status);
-    }
+    k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, g, rx, r2, ws.partials, ws.counter,
+                                               ws.stats, ws.status);
     if (ev) cudaEventRecord(ev[1], st);
+    // stable ranks and chunk histograms: at most one block per chunk of the
+    // largest series, at most about eight blocks per SM over the launch
+    {
+        const size_t smR = sizeof(unsigned short) * 2 * (kThreadsPts / 32) * (size_t)g.nbins;
+        if ((err = allow_max_dynamic_smem((const void *)k_rank)) != cudaSuccess) return err;
+        int64_t nrk = (max_nd + kChunk - 1) / kChunk;
+        const int64_t cap = (8 * (int64_t)nsm + S - 1) / S;
+        if (nrk > cap) nrk = cap;
+        k_rank<<<dim3((unsigned)nrk, S), kThreadsPts, smR, st>>>(bt, g, rx.ab, r2.ab, rx.rank,
+                                                               ws.chist);
+    }
     k_chunk_scan<<<dim3((2 * g.nbins + 31) / 32, S), 256, 0, st>>>(bt, g.nbins, ws.chist, ws.hist);
     k_scan<<<S, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart);
     int nsc = (int)((max_nd + 255) / 256);
@@ -1828,6 +2152,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.px = sx;
     A.p2 = s2;
     A.binstart = ws.binstart;
+    A.st = ws.stats;
     A.twA = static_cast<const Cplx<T> *>(ws.twA);
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
@@ -1858,17 +2183,14 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // Rows of blocks: every instance gets its own row of blocks while that
     // keeps the launch within about eight blocks per SM; beyond that the blocks
     // loop over instances (tables built once per block).
-    int nsm = 0, dev_id = 0;
-    cudaGetDevice(&dev_id);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-    if (nsm <= 0) nsm = 152;
     const int target = 8 * nsm;
     A.ny = shared ? S + 2 : 3 * S;
     // Small grids: the instances go through k_passA_group, `group` per block
     // iteration (in a shared-times batch only the series grids; the common
     // grids through the usual kernel first).
     const size_t cxA = sizeof(Cplx<T>);
-    const size_t colA = (size_t)g.BA * padded_len(g.N2) * cxA;
+    // a member's columns and its rows' exponent bytes
+    const size_t colA = (size_t)g.BA * padded_len(g.N2) * cxA + (size_t)g.N2;
     const size_t tabA = cxA * ((size_t)g.BA * (64 + (g.N2 + 63) / 64) + 64 + (g.N2 + 63) / 64) +
                         sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
     int groupA = (int)((kGroupSmemBudget - tabA) / colA);

@@ -23,18 +23,31 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-__all__ = ["Request", "Scheduler", "PeriodogramServer", "request_bytes"]
+__all__ = ["Request", "Scheduler", "PeriodogramServer", "request_bytes", "lane_bytes"]
 
 _ids = itertools.count()
 
 
 def request_bytes(nd: int, nf: int, precision: str) -> int:
-    """Device bytes a request holds while in flight: its inputs (t, y, dy), its
-    output, its point records and its share of the fine grids (three grids of
-    about 2 nf complex cells)."""
+    """Device bytes a request holds while in flight outside the plans: its
+    inputs (t, y, dy) and its output.  Its fine grids and point records live in
+    the serving plans' reserved batch workspaces, which the server counts
+    separately (``Scheduler.reserved``)."""
+    return int(24 * nd + 8 * nf)
+
+
+def lane_bytes(nd: int, nf: int, precision: str, eps: float) -> int:
+    """Upper bound of the batch-workspace bytes one series occupies alone in a
+    launch (its three fine grids, four point-record sets, bin and chunk
+    tables), from the grid the library chooses for it."""
+    import paper_2409_08090_gb300 as nl
+    q = nl.ls_choose_params(int(nf), float(eps), nl.LS_FP32 if precision == "fp32" else nl.LS_FP64,
+                            int(nd))
     cx = 8 if precision == "fp32" else 16
-    rec = (4 + cx // 2 + cx) * 4
-    return int(24 * nd + 8 * nf + rec * nd + 3 * 2 * nf * cx)
+    recb = 28 if precision == "fp32" else 48
+    n, nbins = int(q["n"]), int(q["n1"])
+    return int(3 * n * cx + 4 * (recb * nd + 1280) + 4 * (4 * nbins + 2)
+               + 4 * (nd // 2048 + 1) * 2 * nbins + 12 * nbins + 8 * 256)
 
 
 @dataclass
@@ -70,8 +83,9 @@ class Scheduler:
     """Admission and batching policy (host only).
 
     * FIFO: a request is admitted only after every earlier one; when the head
-      does not fit the free budget, admission waits for memory to be released
-      (no overtaking, so large requests are not starved).
+      does not fit the free budget (budget - reserved - in use), admission
+      waits for memory to be released (no overtaking, so large requests are
+      not starved).
     * A request larger than the whole budget is rejected with MemoryError.
     * Admitted requests with the same (precision, eps, model) form a batch of at most
       `max_batch` series; `next_batch` returns the largest group first.
@@ -82,6 +96,7 @@ class Scheduler:
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
         self.in_use = 0
+        self.reserved = 0       # bytes held outside requests (the server's plans)
         self.pending: collections.deque[Request] = collections.deque()
         self.admitted: list[Request] = []
         self.lock = threading.Lock()
@@ -101,7 +116,7 @@ class Scheduler:
             if head.future.cancelled():
                 self.pending.popleft()
                 continue
-            if self.in_use + head.nbytes > self.budget:
+            if self.reserved + self.in_use + head.nbytes > self.budget:
                 break
             if not head.future.set_running_or_notify_cancel():
                 self.pending.popleft()
@@ -129,6 +144,12 @@ class Scheduler:
         with self.lock:
             for r in batch:
                 self.in_use -= r.nbytes
+
+    def set_reserved(self, nbytes: int):
+        """Bytes held outside the requests (resident plans); admission counts
+        them against the budget."""
+        with self.lock:
+            self.reserved = int(nbytes)
 
     def idle(self) -> bool:
         with self.lock:
@@ -173,7 +194,8 @@ class PeriodogramServer:
     """
 
     def __init__(self, device: int = 0, memory_budget: int = 60 << 30, streams: int = 2,
-                 max_batch: int = 4096, results: str = "host"):
+                 max_batch: int = 4096, results: str = "host",
+                 plan_workspace_bytes: int | None = None):
         import torch
 
         import paper_2409_08090_gb300 as nl
@@ -192,6 +214,14 @@ class PeriodogramServer:
         # (3.5k/s, p50 0.8 s, against 4.9k/s, p50 34 ms with views), so 0.
         self.copy_limit = 0
         self.sched = Scheduler(memory_budget, max_batch)
+        self.budget = int(memory_budget)
+        # Each resident plan (one per stream and (precision, eps)) reserves a
+        # fixed batch workspace when it is created, so serving never grows or
+        # reallocates one; its bytes, with its grid classes' tables, are counted
+        # against the budget before any request.  A lane holds a quarter.
+        self.plan_ws = int(plan_workspace_bytes if plan_workspace_bytes is not None
+                           else min(1 << 30, max(64 << 20, self.budget // 16)))
+        self.peak_device_bytes = 0    # torch allocations + plans, sampled per batch
         self.slots = [_Slot(self.device) for _ in range(max(1, int(streams)))]
         self.cv = threading.Condition()
         self.stop = False
@@ -225,6 +255,15 @@ class PeriodogramServer:
         if bad:
             req.future.set_exception(ValueError("invalid request"))
             return req.future
+        try:
+            need = lane_bytes(req.nd, req.nf, precision, eps)
+        except Exception as exc:          # no admissible grid for this request
+            req.future.set_exception(exc)
+            return req.future
+        if need > self.plan_ws // 4:
+            req.future.set_exception(MemoryError(
+                f"request needs {need} B of batch workspace, a plan lane holds {self.plan_ws // 4} B"))
+            return req.future
         self.sched.submit(req)
         with self.cv:
             self.cv.notify()
@@ -246,6 +285,10 @@ class PeriodogramServer:
                 raise TimeoutError("server did not drain")
             time.sleep(0.001)
 
+    def plan_bytes(self) -> int:
+        """Device bytes the resident plans hold (workspaces and tables)."""
+        return sum(p.device_bytes() for sl in self.slots for p in sl.plans.values())
+
     def stats(self) -> dict:
         lat = np.array([done - arrival for arrival, done in self.completed])
         if lat.size == 0:
@@ -254,15 +297,35 @@ class PeriodogramServer:
         return {"requests": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "periodograms_per_s": float(lat.size / span) if span > 0 else None,
-                "batches": self.batches}
+                "batches": self.batches, "plan_bytes": self.sched.reserved,
+                "peak_device_bytes": self.peak_device_bytes, "budget": self.budget}
+
+    def _account(self):
+        """Refresh the plans' bytes in the scheduler and the high-water mark of
+        the device bytes this server holds (torch allocations + plans)."""
+        import torch
+        reserved = self.plan_bytes()
+        self.sched.set_reserved(reserved)
+        used = int(torch.cuda.memory_allocated(self.device)) + reserved
+        self.peak_device_bytes = max(self.peak_device_bytes, used)
 
     # ---- GPU loop ----------------------------------------------------------
     def _plan(self, slot: _Slot, key):
         pk = key[:2]            # (precision, eps): the model word is per call
         p = slot.plans.get(pk)
         if p is None:
-            p = self._nl.Plan(2, 1, key[1], key[0], device=self.device)
+            # plans of other keys on this stream are closed first when the new
+            # one's reservation would not fit the budget beside what is in use
+            while (slot.plans and self.sched.reserved + self.sched.in_use + self.plan_ws
+                   > self.budget):
+                _, old = slot.plans.popitem()
+                old.close()
+                self.sched.set_reserved(self.plan_bytes())
+            p = self._nl.Plan(2, 1, key[1], key[0], device=self.device,
+                              batch_workspace_bytes=self.plan_ws)
+            p.reserve_batch()
             slot.plans[pk] = p
+            self._account()
         return p
 
     def _launch(self, slot: _Slot, batch: list[Request]):
@@ -311,6 +374,7 @@ class PeriodogramServer:
         slot.plan = plan
         slot.keep = (host, dev, out)
         self.batches += 1
+        self._account()
 
     def _finish(self, slot: _Slot):
         nl = self._nl
@@ -327,8 +391,9 @@ class PeriodogramServer:
             else:
                 r.future.set_result(res[int(o):int(o) + r.nf])
         self.completed.extend((r.arrival, r.done) for r in batch)
-        self.sched.release(batch)
         slot.batch = slot.done_event = slot.out_host = slot.keep = None
+        self._account()        # a new grid class may have added tables
+        self.sched.release(batch)
 
     def _loop(self):
         import torch

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2409_08090_gb300 import workloads as W
-from tests.rerun_tolerance import assert_rerun_close
+from tests.rerun_tolerance import assert_identical, assert_rerun_close
 
 pytestmark = pytest.mark.gpu
 
@@ -77,10 +77,13 @@ def test_ragged_batch_matches_oracle_and_single(nl, oracle_mod, prec, eps):
             assert np.max(np.abs(P - P_o)) <= 1e-9
         else:
             assert np.max(np.abs(P - P_o)) <= 1e-4
-            if s.nd >= 500:
+            # relative l2 is the FP32 bar for a periodogram; over one or a few
+            # small values it is their relative error, which FP32 sums
+            # (rounding ~1e-7 of sum |h|) cannot bound at P ~ 1e-4
+            if s.nd >= 500 and s.nf >= 100:
                 assert np.linalg.norm(P - P_o) / np.linalg.norm(P_o) <= 1e-5
         P_1 = _run_single(nl, s, eps, prec)
-        assert_rerun_close(P, P_1, prec)
+        assert_identical(P, P_1, (s.nd, s.nf))
 
 
 def test_small_budget_splits_launches_without_changing_results(nl):

@@ -48,5 +48,5 @@ def test_large_then_small_in_another_thread_then_large(nl, prec, eps):
     th.join()
     again = _run(nl, big, prec, eps)
     assert box["P"].shape == (small.nf,) and np.all(np.isfinite(box["P"]))
-    from tests.rerun_tolerance import assert_rerun_close
-    assert_rerun_close(again, first, prec)
+    from tests.rerun_tolerance import assert_identical
+    assert_identical(again, first)

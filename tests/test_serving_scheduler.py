@@ -93,9 +93,20 @@ def test_concurrent_submitters_and_release_balance():
     assert s.in_use == 0 and s.idle()
 
 
-def test_request_bytes_scale():
-    assert request_bytes(1000, 12000, "fp64") > request_bytes(1000, 12000, "fp32")
-    assert request_bytes(10, 100, "fp32") > 0
+def test_request_bytes_count_inputs_and_output():
+    # t, y, dy in and the power out (FP64); grids live in the plans' workspaces
+    assert request_bytes(1000, 12000, "fp32") == 24 * 1000 + 8 * 12000
+    assert request_bytes(1000, 12000, "fp64") == request_bytes(1000, 12000, "fp32")
+
+
+def test_reserved_bytes_count_against_the_budget():
+    a = _req()
+    s = Scheduler(a.nbytes * 3)
+    s.set_reserved(a.nbytes * 2 + 1)            # resident plans leave room for less than one
+    s.submit(a)
+    assert s.next_batch() == []
+    s.set_reserved(a.nbytes * 2)
+    assert s.next_batch() == [a]
 
 
 def test_model_variants_are_batched_apart():
@@ -115,9 +126,11 @@ def test_server_stats_from_timestamps_only():
 
     from paper_2409_08090_gb300.serving import PeriodogramServer
     fake = types.SimpleNamespace(completed=[(0.0, 0.001), (0.5, 0.502), (1.0, 1.010)],
-                                 batches=2)
+                                 batches=2, sched=types.SimpleNamespace(reserved=7),
+                                 peak_device_bytes=11, budget=13)
     st = PeriodogramServer.stats(fake)
     assert st["requests"] == 3 and st["batches"] == 2
+    assert (st["plan_bytes"], st["peak_device_bytes"], st["budget"]) == (7, 11, 13)
     assert st["p50_ms"] == pytest.approx(2.0)
     assert st["periodograms_per_s"] == pytest.approx(3 / 1.010)
     assert np.percentile([1.0, 2.0, 10.0], 99) == pytest.approx(st["p99_ms"])
