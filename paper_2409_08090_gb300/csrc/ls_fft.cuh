@@ -293,51 +293,75 @@ __device__ __forceinline__ void fill_slot_table(int *D, const FftPlan &fp)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) D[i] = slot_to_freq(i << fp.logRlast, fp);
 }
 
-// One DIF stage of radix R over NC transforms (stride colstride) processed
-// together: a thread takes butterfly (q, j) of every transform, so the NC
-// groups of loads are in flight at once and each twiddle is formed once.
+// Butterfly bi of one DIF stage of radix R over NC transforms (stride
+// colstride) processed together: the NC groups of loads are in flight at once
+// and each twiddle is formed once.
+template <int R, int NC, typename V>
+__device__ __forceinline__ void dif_butterfly(V *buf, int colstride, const FftStage &st,
+                                              const V *roots, int tmul, int bi)
+{
+    const int m = st.m;
+    int q, j;
+    if (st.shift >= 0) {
+        q = bi >> st.shift;
+        j = bi & (m - 1);
+    } else {
+        q = small_div(bi, m, st.inv_m);
+        j = bi - q * m;
+    }
+    const int base = q * st.Ls + j;
+    const int pb = pad16(base);
+    int off[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) off[r] = st.lin ? pb + st.off[r] : pad16(base + r * m);
+    V v[NC][R];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[c][r] = buf[c * colstride + off[r]];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
+    if (j != 0) {
+        const int step = j * tmul;             // W_Ls^(j k) = W_L^(k step)
+#pragma unroll
+        for (int k = 1; k < R; ++k) {
+            const V w = root_tw(roots, k * step);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[c * colstride + off[r]] = v[c][r];
+    }
+}
+
+// One DIF stage of radix R over NC transforms: a thread takes butterfly (q, j)
+// of every transform.
 template <int R, int NC, typename V>
 __device__ __forceinline__ void dif_stage(V *buf, int colstride, const FftStage &st,
                                           const V *roots, int L)
 {
-    const int m = st.m;
     const int tmul = L / st.Ls;
-    for (int bi = threadIdx.x; bi < st.nb; bi += blockDim.x) {
-        int q, j;
-        if (st.shift >= 0) {
-            q = bi >> st.shift;
-            j = bi & (m - 1);
-        } else {
-            q = small_div(bi, m, st.inv_m);
-            j = bi - q * m;
-        }
-        const int base = q * st.Ls + j;
-        const int pb = pad16(base);
-        int off[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) off[r] = st.lin ? pb + st.off[r] : pad16(base + r * m);
-        V v[NC][R];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) v[c][r] = buf[c * colstride + off[r]];
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
-        if (j != 0) {
-            const int step = j * tmul;             // W_Ls^(j k) = W_L^(k step)
-#pragma unroll
-            for (int k = 1; k < R; ++k) {
-                const V w = root_tw(roots, k * step);
-#pragma unroll
-                for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) buf[c * colstride + off[r]] = v[c][r];
-        }
+    for (int bi = threadIdx.x; bi < st.nb; bi += blockDim.x)
+        dif_butterfly<R, NC>(buf, colstride, st, roots, tmul, bi);
+}
+
+// One DIF stage over ncol transforms with the (transform, butterfly) pairs
+// dealt to the block's threads in turn, one transform per thread at a time:
+// for blocks with more threads than a stage has butterflies per transform.
+template <int R, typename V>
+__device__ __forceinline__ void dif_stage_dealt(V *buf, int ncol, int colstride,
+                                                const FftStage &st, const V *roots, int L)
+{
+    const int tmul = L / st.Ls;
+    const int nb = st.nb;
+    const float inv_nb = 1.0f / (float)nb;
+    for (int u = threadIdx.x; u < ncol * nb; u += blockDim.x) {
+        const int c = small_div(u, nb, inv_nb);
+        dif_butterfly<R, 1>(buf + c * colstride, colstride, st, roots, tmul, u - c * nb);
     }
 }
 
@@ -454,6 +478,27 @@ __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, cons
         case 5: dif_stage_cols<5, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         case 3: dif_stage_cols<3, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         default: dif_stage_cols<2, NC>(buf, ncol, colstride, st, roots, fp.L); break;
+        }
+        __syncthreads();
+    }
+}
+
+// In-place DIF FFT of `ncol` transforms of length fp.L with every stage's
+// (transform, butterfly) pairs dealt to all threads (dif_stage_dealt).  Ends
+// with a barrier; output in digit-reversed order.
+template <typename V>
+__device__ void fft_dif_dealt(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots)
+{
+    for (int s = 0; s < fp.nstages; ++s) {
+        const FftStage &st = fp.st[s];
+        switch (st.R) {
+        case 16: dif_stage_dealt<16>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 9: dif_stage_dealt<9>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 8: dif_stage_dealt<8>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 4: dif_stage_dealt<4>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 5: dif_stage_dealt<5>(buf, ncol, colstride, st, roots, fp.L); break;
+        case 3: dif_stage_dealt<3>(buf, ncol, colstride, st, roots, fp.L); break;
+        default: dif_stage_dealt<2>(buf, ncol, colstride, st, roots, fp.L); break;
         }
         __syncthreads();
     }

@@ -14,6 +14,9 @@ constexpr int kTw4Bits = 12;      // four-step twiddle table split: W^p = lo[p %
 constexpr int kThreadsA = 256;
 constexpr size_t kSmemOptinBytes = 232448;   // opt-in shared memory per block (227 KB)
 constexpr int kThreadsB = 256;
+// Pass-B blocks of the FP32 path where shared memory holds two blocks per SM:
+// 12 warps each (the row transforms deal their butterflies to all of them).
+constexpr int kThreadsBWide = 384;
 constexpr int kMinN1 = 32;        // keeps every kernel footprint (w <= 16) within two columns
 
 // Device status word bits (sticky until ls_sync).
@@ -84,7 +87,7 @@ template <typename T> struct PointSet {
 // series s of a launch owns the chunk rows chunk_row0(s) .. of the chunk
 // histogram, so rows never overlap: (rec_off + nd) / kChunk - rec_off / kChunk
 // + 1 >= ceil(nd / kChunk).
-constexpr int kChunk = 2048;
+constexpr int kChunk = 4096;
 constexpr int kThreadsPts = 256;
 __host__ __device__ inline int64_t chunk_row0(int64_t rec_off, int s) { return rec_off / kChunk + s; }
 // Chunk-histogram entries a launch of S series over `points` records needs.

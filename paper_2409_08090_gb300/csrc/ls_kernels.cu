@@ -235,7 +235,7 @@ __device__ __forceinline__ void split_fixed(u128 F, const Geometry &g, uint32_t 
     if (c0 >= (int)g.n) c0 -= (int)g.n;
     const int bb = c0 / g.N1;
     ab = (uint32_t)(c0 - bb * g.N1) | ((uint32_t)bb << 16);
-    if (sizeof(T) == 4) roff = (T)((float)(uint64_t)(R >> 40) * 0x1p-24f);
+    if (sizeof(T) == 4) roff = (T)((float)(uint32_t)(uint64_t)(R >> 40) * 0x1p-24f);   // R <= 2^64
     else roff = (T)((double)(uint64_t)(R >> 11) * 0x1p-53);
 }
 
@@ -251,17 +251,19 @@ template <> struct Cis<double> {
     }
 };
 
-// FP32 path: the phase c (in cycles, [-1/2, 1/2)) is split as cf + dc with cf
-// its nearest float; sincospif(2 cf) is corrected to first order in 2 pi dc
-// (|dc| < 3e-8, neglected term < 1e-14).
+// FP32 path: the phase c = s 2^-64 (in cycles, [-1/2, 1/2)) is split as
+// cf + dc with cf = floor(c 2^24) 2^-24 (exact in FP32) and dc the remainder
+// (in radians, 0 <= dc < 2 pi 2^-24, its 32 leading bits converted);
+// sincospif(2 cf) is corrected to first order in dc (neglected term
+// dc^2 / 2 < 7e-14).  Only 32-bit conversions: this part converts 64-bit
+// integers at its FP64 rate.
 template <> struct Cis<float> {
     __device__ __forceinline__ static float2 of(u128 F) {
         const long long s = (long long)(uint64_t)(F >> 64);
-        const float sf = (float)s;
-        const long long back = (sf >= 9.2233720368547758e18f) ? 0x7fffffffffffffffll
-                                                               : (long long)sf;
-        const float cf = sf * 0x1p-64f;
-        const float dc = 6.2831853071795865f * ((float)(s - back) * 0x1p-64f);
+        const int hi = (int)(s >> 40);                                         // |hi| <= 2^23
+        const unsigned rem = (unsigned)(((unsigned long long)s & 0xFFFFFFFFFFull) >> 8);
+        const float cf = (float)hi * 0x1p-24f;
+        const float dc = 6.2831853071795865f * ((float)rem * 0x1p-56f);
         float sn, co;
         sincospif(2.0f * cf, &sn, &co);
         return make_float2(fmaf(-dc, sn, co), fmaf(dc, co, sn));
@@ -1508,12 +1510,15 @@ __device__ __forceinline__ ff two_prod(float a, float b)
     const float p = a * b;
     return {p, fmaf(a, b, -p)};
 }
+// Sum with Dekker's add (no second renormalisation): error below about
+// 2^-47 (|x| + |y|), the error model of an FP64 add of the same operands (2^-53
+// (|x| + |y|)) at 48 bits.  The ratio's inputs are FP32 sums whose own errors
+// scale with the same magnitudes, so a bound relative to |x + y| (the longer
+// two-sum-of-low-parts form) buys nothing here.
 __device__ __forceinline__ ff ff_add(ff x, ff y)
 {
     const ff s = two_sum(x.hi, y.hi);
-    const ff t = two_sum(x.lo, y.lo);
-    ff u = fast_two_sum(s.hi, s.lo + t.hi);
-    return fast_two_sum(u.hi, u.lo + t.lo);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
 }
 __device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ ff ff_mul(ff x, ff y)
@@ -1521,24 +1526,44 @@ __device__ __forceinline__ ff ff_mul(ff x, ff y)
     const ff p = two_prod(x.hi, y.hi);
     return fast_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
 }
-// Sum of two double-float values of equal sign (no cancellation possible).
-__device__ __forceinline__ ff ff_add_same_sign(ff x, ff y)
-{
-    const ff s = two_sum(x.hi, y.hi);
-    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
-}
-// x / y with a float reciprocal and one correction: ~2^-46 relative.
+// x / y: the float quotient q1 = x.hi / y.hi, corrected by the remainder
+// x - q1 y formed exactly up to the low parts (q1 y.hi = p exactly by the fma
+// two-product, and x.hi - p.hi is exact since p.hi is within a few ulp of
+// x.hi): relative error about 2^-45.
 __device__ __forceinline__ ff ff_div(ff x, ff y)
 {
     const float ry = __frcp_rn(y.hi);
     const float q1 = x.hi * ry;
-    const ff r = ff_add(x, ff_neg(ff_mul(y, ff{q1, 0.f})));
-    return fast_two_sum(q1, r.hi * ry);
+    const ff p = two_prod(q1, y.hi);
+    const float r = fmaf(-q1, y.lo, ((x.hi - p.hi) - p.lo) + x.lo);
+    return fast_two_sum(q1, r * ry);
+}
+
+// hi + lo (|lo| <= ulp(hi) / 2) rounded to the nearest double, from the bit
+// patterns on the integer pipe: hi widens exactly (exponent rebiased, mantissa
+// shifted up 29 bits) and lo, in units of that double's ulp 2^(e - 52) (e the
+// unbiased exponent of hi, |lo| <= 2^28 units), is rounded to an integer (ties
+// to even, the rounding of the FP64 add) and added to the bits.  The sum stays
+// in hi's binade except where hi is a power of two and lo points towards zero,
+// and for hi zero, subnormal, non-finite or below 2^-75: those take the FP64
+// conversions and add, which give the same value.
+__device__ __forceinline__ double ff_to_double(ff p)
+{
+    const unsigned hb = __float_as_uint(p.hi);
+    const unsigned e = (hb >> 23) & 0xffu;
+    if (e < 52u || e == 255u || (hb & 0x7fffffu) == 0u) return (double)p.hi + (double)p.lo;
+    const float units = __uint_as_float((306u - e) << 23);          // 2^(52 - (e - 127))
+    int r = __float2int_rn(p.lo * units);
+    if (hb >> 31) r = -r;
+    const unsigned long long mag = ((unsigned long long)(hb & 0x7fffffffu) + (896ull << 23)) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)(hb >> 31) << 63) |
+                                            (mag + (unsigned long long)(long long)r)));
 }
 
 // FP32 path: the sums arrive as FP32 values (exact inputs here); the ratio is
-// evaluated in double-float, whose rounding (~1e-14 relative) is far below
-// the FP32 sums' own error, and falls back to FP64 for a nearly singular M.
+// evaluated in double-float, whose rounding (~1e-13 of the terms' magnitudes)
+// is far below the FP32 sums' own error, and falls back to FP64 for a nearly
+// singular M.
 __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float S, float C2,
                                               float S2, ff YY, double YYd, float lam_tol)
 {
@@ -1549,14 +1574,9 @@ __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float
     if (!(D.hi > lam_tol * (CC.hi + SS.hi) && CC.hi > 0.f && SS.hi > 0.f))
         return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd, (double)lam_tol);
     const ff ChSh = two_prod(Ch, Sh);
-    // CC, SS > 0 here, so the first two terms add without cancellation.
-    const ff N = ff_add(ff_add_same_sign(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
+    const ff N = ff_add(ff_add(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
                         ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, CS)));
-    const ff P = ff_div(N, ff_mul(D, YY));
-    // Two conversions and an FP64 add: measured faster than assembling the
-    // double from the bit patterns on the integer pipe (the FP64 work overlaps
-    // the FP32 arithmetic of other warps; integer work competes with it).
-    return (double)P.hi + (double)P.lo;
+    return ff_to_double(ff_div(N, ff_mul(D, YY)));
 }
 
 // ---------------------------------------------------------------------------
@@ -1650,8 +1670,11 @@ template <> struct PowerOut<float> {
 
 // kStage is PassBArgs::stage as a template parameter: each launch carries only
 // its own code (fewer instruction-fetch stalls than one kernel for all stages).
-template <typename T, int kStage, int kMinB>
-__global__ void __launch_bounds__(kThreadsB, kMinB) k_passB(PassBArgs<T> B)
+// kThr: threads per block; above kThreadsB the row transforms deal their
+// (row, butterfly) pairs to all threads (more warps per SM where shared memory
+// allows only two blocks).
+template <typename T, int kStage, int kMinB, int kThr = kThreadsB>
+__global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
 {
     using V = Cplx<T>;
     using F = typename FftOf<T>::type;   // the transform's type (double-float for FP64)
@@ -1714,7 +1737,10 @@ __global__ void __launch_bounds__(kThreadsB, kMinB) k_passB(PassBArgs<T> B)
         }
         continue;
     }
-    if (B.nofit) {                          // rows 0 and 2
+    if constexpr (kThr > kThreadsB) {
+        if (B.nofit) fft_dif_dealt(buf, 2, 2 * Lp, g.fb, roots);   // rows 0 and 2
+        else fft_dif_dealt(buf, 3, Lp, g.fb, roots);
+    } else if (B.nofit) {                   // rows 0 and 2
         if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
         else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
     } else {
@@ -2269,8 +2295,9 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     {
-        const void *fns[4] = {(const void *)k_passB<T, 0, 2>, (const void *)k_passB<T, 1, 2>,
-                              (const void *)k_passB<T, 0, 3>, (const void *)k_passB<T, 1, 3>};
+        const void *fns[5] = {(const void *)k_passB<T, 0, 2>, (const void *)k_passB<T, 1, 2>,
+                              (const void *)k_passB<T, 0, 3>, (const void *)k_passB<T, 1, 3>,
+                              (const void *)k_passB<T, 0, 2, kThreadsBWide>};
         for (const void *f : fns)
             if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
     }
@@ -2305,6 +2332,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
                                passB_group_smem_bytes(g, sizeof(Cplx<T>), GB, nr), st>>>(B);
         } else {
             if (threeB) k_passB<T, 0, 3><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
+            else if (sizeof(T) == 4)
+                k_passB<T, 0, 2, kThreadsBWide><<<dim3(g.N2, gyB), kThreadsBWide, smB, st>>>(B);
             else k_passB<T, 0, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
         }
     }
