@@ -60,6 +60,7 @@ struct BatchWorkspace {
 // Offsets of one launch's buffers inside a lane arena (256-byte aligned).
 struct LaunchCarve {
     size_t H, pts[4], hist, binstart, chist, bytes;
+    size_t perm = 0, wts = 0, cvals = 0;   // shared-times launches only
 };
 
 LaunchCarve carve_launch(int64_t n, int nbins, size_t cx, size_t recb, int64_t S, int64_t points,
@@ -698,9 +699,9 @@ ls_status execute_impl(ls_plan_s *p, const double *t, const double *y, const dou
     }
     e = (p->prec == LS_FP32)
             ? launch_pipeline<float>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
-                                     dev_in[2], dpow, dsums, nred, st, ev, 0, norm)
+                                     dev_in[2], dpow, dsums, nred, st, ev, norm)
             : launch_pipeline<double>(p->g, p->ws, p->max_nd, bt, nd, dev_in[0], dev_in[1],
-                                      dev_in[2], dpow, dsums, nred, st, ev, 0, norm);
+                                      dev_in[2], dpow, dsums, nred, st, ev, norm);
     if (e != cudaSuccess) return cuda_status(e);
     if (host_power || host_sums) {
         if (host_power) {
@@ -795,6 +796,11 @@ Workspace lane_workspace(const BatchWorkspace &b, const LaunchCarve &c, int *sta
     ws.hist = reinterpret_cast<int *>(a + c.hist);
     ws.binstart = reinterpret_cast<int *>(a + c.binstart);
     ws.chist = reinterpret_cast<int *>(a + c.chist);
+    if (c.perm) {
+        ws.perm = reinterpret_cast<int *>(a + c.perm);
+        ws.wts = reinterpret_cast<double *>(a + c.wts);
+        ws.cvals = a + c.cvals;
+    }
     ws.partials = b.partials;
     ws.counter = b.counter;
     ws.stats = b.stats;
@@ -1029,12 +1035,47 @@ int batch_nred(const ls_plan_s *p, int S, int64_t max_nd)
 
 // Arena carve of a launch of S series over `points` records on a grid of n
 // cells and nbins bins.
-LaunchCarve carve_for(int prec, int64_t n, int nbins, int64_t S, int64_t points, int shared)
+// A shared-times launch of S series of nd points each: H for the two common
+// grids and one chunk of series grids, the common record sets and one
+// series' bin tables, the sort permutation and weights (nd each), and the
+// series' scalars c_i (S x nd).
+LaunchCarve carve_shared(int prec, int64_t n, int nbins, int64_t S, int64_t nd)
 {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     const size_t recb = prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
-    const int64_t grids = shared ? S + 2 : 3 * S;
-    return carve_launch(n, nbins, cx, recb, S, points, grids);
+    const size_t tb = prec == LS_FP32 ? sizeof(float) : sizeof(double);
+    LaunchCarve c;
+    size_t off = 0;
+    c.H = off;
+    off = al(off + cx * (size_t)n * (size_t)(2 + shared_chunk_series(n, cx, S)));
+    const size_t rec = recb * (size_t)nd + 5 * 256;
+    for (int i = 0; i < 4; ++i) {
+        c.pts[i] = off;
+        off = al(off + rec);
+    }
+    c.hist = off;
+    off = al(off + sizeof(int) * 2 * (size_t)nbins);
+    c.binstart = off;
+    off = al(off + sizeof(int) * 2 * ((size_t)nbins + 1));
+    c.chist = off;
+    off = al(off + sizeof(int) * (size_t)chunk_hist_entries(nd, 1, nbins));
+    c.perm = off;
+    off = al(off + sizeof(int) * (size_t)nd);
+    c.wts = off;
+    off = al(off + sizeof(double) * (size_t)nd);
+    c.cvals = off;
+    off = al(off + tb * (size_t)S * (size_t)nd);
+    c.bytes = off;
+    return c;
+}
+
+LaunchCarve carve_for(int prec, int64_t n, int nbins, int64_t S, int64_t points, int shared)
+{
+    if (shared) return carve_shared(prec, n, nbins, S, points / (S > 0 ? S : 1));
+    const size_t cx = prec == LS_FP32 ? 8 : 16;
+    const size_t recb = prec == LS_FP32 ? point_record_bytes<float>() : point_record_bytes<double>();
+    return carve_launch(n, nbins, cx, recb, S, points, 3 * S);
 }
 
 LaunchCarve launch_carve(const ls_plan_s *sub, int64_t S, int64_t points, int shared)
@@ -1048,7 +1089,8 @@ int64_t shared_launch_size(int prec, int64_t n, int nbins, int64_t nd, int64_t l
                            int64_t lane_budget)
 {
     int64_t S = 1;
-    while (S < kMaxBatchS && S < left &&
+    // (the common entry of the Stats and tickets takes slot S)
+    while (S < kMaxBatchS - 1 && S < left &&
            (int64_t)carve_for(prec, n, nbins, S + 1, (S + 1) * nd, 1).bytes <= lane_budget)
         ++S;
     return S;
@@ -1072,8 +1114,11 @@ ls_status enqueue_batch(const BatchWorkspace &b, int *status, cudaStream_t st, c
     ws.tw4 = sub->ws.tw4;
     ws.deconv = sub->ws.deconv;
     ws.deconv_slot = sub->ws.deconv_slot;
+    if (shared)
+        return cuda_status(launch_shared_pipeline<T>(sub->g, ws, bt, max_nd, t, y, dy, power,
+                                                     nred, st, mode));
     return cuda_status(launch_pipeline<T>(sub->g, ws, points, bt, max_nd, t, y, dy, power,
-                                          nullptr, nred, st, nullptr, shared, mode));
+                                          nullptr, nred, st, nullptr, mode));
 }
 
 template <typename T>

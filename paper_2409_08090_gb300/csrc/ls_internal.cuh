@@ -126,7 +126,27 @@ struct Workspace {
     void *tw4;            // four-step table for n: lo (4096) then hi (ceil(n/4096))
     void *deconv;         // 1/phi_hat(k'), k' = 0 .. K0max
     void *deconv_slot;    // the same in pass-B order: [d * N1 + slot], n entries
+    // shared-times batches (launch_shared_pipeline)
+    int *perm;            // common sorted order -> input index (geometry x)
+    double *wts;          // common weights 1/dy^2
+    void *cvals;          // per series, c_i = scale (y - ybar) in the sorted order
 };
+
+// Series grids per pass-A/pass-B round of a shared-times batch: a chunk's fine
+// grids (kSharedChunkBytes) are written by pass A and read back by pass B, and
+// the next chunk reuses their slots of H.  Measured on 4096 series of 1.8e5
+// cells (FP32): chunks of 48 MB (L2-resident between the passes) 28.0 ms per
+// batch, 192 MB 24.7 ms, one chunk 21.1 ms: the passes are not HBM-bound, and
+// every chunk adds the launches' tails and per-block set-up, so chunks only
+// bound the workspace.
+constexpr int64_t kSharedChunkBytes = 4ll << 30;
+
+inline int64_t shared_chunk_series(int64_t n, size_t cx, int64_t S)
+{
+    int64_t c = kSharedChunkBytes / (n * (int64_t)cx);
+    if (c < 1) c = 1;
+    return c < S ? c : S;
+}
 
 // Frequencies of one series, decomposed for the exact phase reduction:
 // df = df_m 2^df_e, f0 = (-1)^f0_neg f0_m 2^f0_e, centre mode K0.
@@ -145,8 +165,6 @@ struct SeriesDesc {
     PhaseArgs ph;
 };
 
-// `shared` = 1: all series share t and dy (uniform batch); the s2 and s3
-// transforms of series 0 serve every series and H holds S + 2 grids.
 // S series launched together (grid dimension y): `many` points to S device
 // descriptors, or is null and the single series is `one`.  Per-series
 // workspace: stats[s], counter[2s .. 2s+1], partials[s * 3 * nred ...],
@@ -172,7 +190,15 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &b, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev, int shared = 0, int mode = 0);
+                            cudaStream_t st, cudaEvent_t *ev, int mode = 0);
+
+// Shared-times batch (one time array and one dy for all bt.S series): see
+// the definition.  Stats and tickets hold S + 1 entries.
+template <typename T>
+cudaError_t launch_shared_pipeline(const Geometry &g, const Workspace &ws, const Batch &bt,
+                                   int64_t nd, const double *t, const double *Y,
+                                   const double *dy, double *power, int nred, cudaStream_t st,
+                                   int mode);
 
 template <typename T>
 cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,

@@ -553,7 +553,7 @@ __global__ void k_scan(const int *__restrict__ hist, int nbins, int *binstart)
 template <typename T>
 __global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
                           PointSet<T> sx, PointSet<T> s2, const int *__restrict__ binstart,
-                          const int *__restrict__ chist)
+                          const int *__restrict__ chist, int *perm)
 {
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
@@ -580,6 +580,7 @@ __global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
         s2.ab[d2] = c2;
         s2.roff[d2] = r2.roff[j];
         s2.s[0][d2] = r2.s[0][j];
+        if (perm) perm[d1] = (int)j;      // shared-times batches: sorted -> input index
     }
 }
 
@@ -732,7 +733,9 @@ struct PassAArgs {
     Cplx<T> *H;
     int cs;                // blocks per thread-block cluster along the columns (1: none)
     int ny;                // instances (transforms of series) along the grid's y
-    int group;             // instances per block iteration of k_passA_group
+    int group;             // instances per block iteration of k_passA_group / k_passA_sh
+    const T *cv;           // k_passA_sh: c_i of series s at cv[s * cstride + i] (sorted order)
+    int64_t cstride;
 };
 
 template <typename T>
@@ -1170,11 +1173,10 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
     const dfl beta_dfl(g.beta);
     const bool dfl_ok = g.eps >= 1e-11;
     const int nbb = (g.w - 1 + BA - 1) >> g.logBA;
-    // instances taken here: shared times -> the series grids (H slot 2 + s);
-    // otherwise every transform of every series, without the w^ grid when the
-    // model has no offset
-    const int S = A.shared ? A.ny - 2 : A.ny / 3;
-    const int ni = A.shared ? S : (A.nofit ? 2 * S : 3 * S);
+    // instances taken here: every transform of every series, without the w^
+    // grid when the model has no offset
+    const int S = A.ny / 3;
+    const int ni = A.nofit ? 2 * S : 3 * S;
 
     signed char *rexp = reinterpret_cast<signed char *>(dtab + (N2 >> g.fa.logRlast));   // G x N2
 
@@ -1195,11 +1197,7 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
             const int r = threadIdx.x;
             const int idx = s0 + r;
             int ser, grid, slot;
-            if (A.shared) {
-                ser = idx;
-                grid = 0;
-                slot = 2 + idx;
-            } else if (A.nofit) {
+            if (A.nofit) {
                 ser = idx >> 1;
                 grid = (idx & 1) ? 2 : 0;
                 slot = 3 * ser + grid;
@@ -1398,6 +1396,427 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-times batches (series with one time array and one dy: the batched
+// mode of Sec. 2).  Positions, pre-phases and weights are the same for every
+// series, so they are reduced, sorted and transformed once (the w^ transforms
+// at f and 2f); a series contributes only its data: its weighted mean, its YY
+// and one scalar per point, c_i = scale (y - ybar) at the i-th record of the
+// common sorted order, from which pass A forms s1_i = c_i s2_i (s2 = w^ p, the
+// common strength).  k_passA_sh then evaluates each record's kernel values
+// once for a group of series.  Per-launch layout: Stats and tickets of series
+// s at s (common: at S), partials reused kernel after kernel.
+// ---------------------------------------------------------------------------
+
+// Weights w_j = 1/dy_j^2 (FP64, kept for the series' sums), W = sum w_j into
+// the common Stats entry, and the checks of t and dy.
+__global__ void k_sh_weights(const double *__restrict__ t, const double *__restrict__ dy,
+                             int64_t nd, double *wts, double *partials, unsigned int *counter,
+                             Stats *stc, int *status)
+{
+    __shared__ double sh[32];
+    double sw = 0.0;
+    bool ok = true;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double d = dy ? dy[j] : 1.0;
+        ok &= finite_bits(d) && finite_bits(t[j]) && __double_as_longlong(d) > 0;
+        const double w = rcp_fp64(d * d);
+        wts[j] = w;
+        sw += w;
+    }
+    if (!ok) atomicOr(status, kStatBadInput);
+    const double a = block_sum(sw, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+    if (last_block(counter)) {
+        double r[1];
+        reduce_partials(partials, gridDim.x, 1, r, sh);
+        if (threadIdx.x == 0) {
+            stc->W = r[0];
+            stc->invW = 1.0 / r[0];
+            stc->smax[0] = stc->smax[1] = stc->smax[2] = 0u;
+            *counter = 0u;
+        }
+    }
+}
+
+// Common records: cells, kernel offsets and the strengths of the w^
+// transforms (s2 = w^ p at x, s3 = w^ p^2 at 2x) from the exact phase
+// reduction, formed as k_points forms them; the two grids' strength maxima.
+template <typename T>
+__global__ void k_sh_points(const double *__restrict__ t, int64_t nd, PhaseArgs ph, Geometry g,
+                            const double *__restrict__ wts, PointSet<T> px, PointSet<T> p2,
+                            Stats *stc)
+{
+    const double invW = stc->invW;
+    unsigned m2 = 0u, m3 = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double tj = t[j];
+        const double wh = wts[j] * invW;
+        const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);
+        const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj) + (u128)(uint64_t)ph.K0 * Fx;
+        uint32_t ab1, ab2;
+        T r1, r2;
+        split_fixed<T>(Fx, g, ab1, r1);
+        split_fixed<T>(Fx << 1, g, ab2, r2);
+        const Cplx<T> p = Cis<T>::of(Fc);
+        const Cplx<T> q = Cis<T>::of(Fc << 1);
+        const T wt = (T)wh;
+        const Cplx<T> s2 = mk2(wt * p.x, wt * p.y), s3 = mk2(wt * q.x, wt * q.y);
+        px.ab[j] = ab1;
+        px.roff[j] = r1;
+        px.s[1][j] = s2;
+        p2.ab[j] = ab2;
+        p2.roff[j] = r2;
+        p2.s[0][j] = s3;
+        m2 = max(m2, strength_bound_bits(s2));
+        m3 = max(m3, strength_bound_bits(s3));
+    }
+    m2 = __reduce_max_sync(0xffffffffu, m2);
+    m3 = __reduce_max_sync(0xffffffffu, m3);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&stc->smax[1], m2);
+        atomicMax(&stc->smax[2], m3);
+    }
+}
+
+// Per series (blockIdx.y): WY = sum w_j y_j and WY2 = sum w_j y_j^2 with the
+// common weights, then ybar and the strength scale as k_stats sets them.
+__global__ void k_sh_stats(const double *__restrict__ y, Batch bt, const double *__restrict__ wts,
+                           const Stats *stc, double *partials, unsigned int *counter, Stats *st,
+                           int *status, int center)
+{
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    y += sd.y_off;
+    const int64_t nd = sd.nd;
+    partials += (size_t)ser * 3 * gridDim.x;
+    counter += 2 * ser;
+    st += ser;
+    __shared__ double sh[32];
+    double swy = 0.0, swy2 = 0.0;
+    bool ok = true;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double yj = y[j];
+        ok &= finite_bits(yj);
+        const double wy = wts[j] * yj;
+        swy += wy;
+        swy2 = fma(wy, yj, swy2);
+    }
+    if (!ok) atomicOr(status, kStatBadInput);
+    const double b = block_sum(swy, sh);
+    const double c = block_sum(swy2, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = b;
+        partials[2 * blockIdx.x + 1] = c;
+    }
+    if (last_block(counter)) {
+        double r[2];
+        reduce_partials(partials, gridDim.x, 2, r, sh);
+        if (threadIdx.x == 0) {
+            const double W = stc->W, WY = r[0], WY2 = r[1];
+            st->W = W;
+            st->WY = WY;
+            st->WY2 = WY2;
+            st->ybar = center ? WY / W : 0.0;
+            st->invW = stc->invW;
+            const double m2 = WY2 / W;
+            const double var = fmax(m2 - st->ybar * st->ybar, 1e-20 * m2);
+            st->scale = (var > 0.0 && isfinite(var)) ? 1.0 / sqrt(var) : 1.0;
+            st->smax[0] = st->smax[1] = st->smax[2] = 0u;
+            *counter = 0u;
+        }
+    }
+}
+
+// Per series (blockIdx.y): YY = sum w^_j (scale (y_j - ybar))^2 (FP64, the
+// exact second pass, input order), and c_i = scale (y_perm(i) - ybar) in the
+// common sorted order with the maximum of the s1 strength c_i s2_i as pass A
+// forms it (the series' fixed-point grid bound).
+template <typename T>
+__global__ void k_sh_series(const double *__restrict__ y, Batch bt, const double *__restrict__ wts,
+                            const int *__restrict__ perm, const Cplx<T> *__restrict__ s2sorted,
+                            T *cvals, double *partials, unsigned int *counter, Stats *st,
+                            int *status)
+{
+    const int ser = blockIdx.y;
+    const SeriesDesc sd = series_of(bt, ser);
+    y += sd.y_off;
+    const int64_t nd = sd.nd;
+    cvals += (size_t)ser * (size_t)nd;
+    partials += (size_t)ser * 3 * gridDim.x;
+    counter += 2 * ser + 1;
+    st += ser;
+    __shared__ double sh[32];
+    const double ybar = st->ybar, scale = st->scale;
+    double syy = 0.0;
+    unsigned m1 = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double yc = y[j] - ybar;
+        syy = fma(wts[j] * yc, yc, syy);
+        const T c = (T)(scale * (y[perm[j]] - ybar));   // j as a sorted index here
+        cvals[j] = c;
+        const Cplx<T> s2 = s2sorted[j];
+        m1 = max(m1, strength_bound_bits(mk2(c * s2.x, c * s2.y)));
+    }
+    m1 = __reduce_max_sync(0xffffffffu, m1);
+    if ((threadIdx.x & 31) == 0) atomicMax(&st->smax[0], m1);
+    const double a = block_sum(syy, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+    if (last_block(counter)) {
+        double r[1];
+        reduce_partials(partials, gridDim.x, 1, r, sh);
+        if (threadIdx.x == 0) {
+            const double YY = r[0] * st->invW, Y2 = st->WY2 * st->invW;
+            st->YY = YY * scale * scale;
+            st->Y2 = Y2;
+            // A constant series: variance zero up to the rounding of the mean.
+            if (!(YY > 1e-24 * Y2)) atomicOr(status, kStatDegenerate);
+            *counter = 0u;
+        }
+    }
+}
+
+// Pass A for the series grids of a shared-times batch: a block takes column
+// block blk of `group` series at a time (member r owns columns r BA .. r BA +
+// BA - 1, its s1 grid in H slot 2 + r of the chunk).  The series share the
+// records, so each record's footprint and kernel values are computed once and
+// applied to every member's strength c_i s2_i; the row counts are common and
+// the strength units per member (FP32 fixed-point grids).  No cluster pairs.
+// kKv: bound of min(BA, w), the cells of a record in the block's columns
+// (8 for tiles of up to 8 columns, else 16), the kernel values kept in registers.
+template <typename T, int kKv>
+__global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassAArgs<T> A)
+{
+    using V = Cplx<T>;
+    using F = typename FftOf<T>::type;
+    using I = typename Fixed<T>::I;
+    __shared__ unsigned g_mbits[kMaxGroup];    // members' strength maxima (bits)
+    __shared__ float g_invm[kMaxGroup];        // and 2^16 over them, rounded up
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geometry &g = A.g;
+    const int N1 = g.N1, N2 = g.N2, BA = g.BA;
+    const int Lp = padded_len(N2);
+    const int nhi = (N2 + 63) >> 6;
+    const int G = A.group;
+    V *buf = reinterpret_cast<V *>(smem_raw);
+    F *bufF = reinterpret_cast<F *>(buf);
+    F *alo = bufF + (size_t)G * BA * Lp;
+    F *ahi = alo + BA * 64;
+    F *roots = ahi + BA * nhi;
+    int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);
+    signed char *rexp = reinterpret_cast<signed char *>(dtab + (N2 >> g.fa.logRlast));   // G x N2
+    const int blk = blockIdx.x;
+    const int a0 = blk * BA;
+    load_roots(roots, A.twA, N2);
+    fill_slot_table(dtab, g.fa);
+    for (int i = threadIdx.x; i < BA * 64; i += blockDim.x)
+        alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a0 + (i >> 6)) * (i & 63)));
+    for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
+        const int col = i / nhi;
+        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * (i - col * nhi)) % g.n));
+    }
+    const T halfw = T(0.5) * T(g.w);
+    const T zscale = T(2) / T(g.w);
+    const T beta = T(g.beta);
+    const dfl beta_dfl(g.beta);
+    const bool dfl_ok = g.eps >= 1e-11;
+    // the block's records (common to all series): bins blk - nbb .. blk of geometry x
+    const PointSet<T> P = A.px;
+    const int *bs = A.binstart;
+    const int nbb = (g.w - 1 + BA - 1) >> g.logBA;
+    int r0s, r0e, r1s = 0, r1e = 0;
+    if (nbb + 1 >= g.nbins) {
+        r0s = bs[0];
+        r0e = bs[g.nbins];
+    } else if (blk - nbb >= 0) {
+        r0s = bs[blk - nbb];
+        r0e = bs[blk + 1];
+    } else {
+        r0s = bs[blk - nbb + g.nbins];
+        r0e = bs[g.nbins];
+        r1s = bs[0];
+        r1e = bs[blk + 1];
+    }
+    const int cnt0 = r0e - r0s;
+    const int total = cnt0 + (r1e - r1s);
+    const V *s2r = P.s[1];
+    const int S = A.ny;
+    // member r's grid region holds, before it is zeroed for the spread, the
+    // common row counts (member 0) and the member's row strength units
+    auto rows_of = [&](int r) { return reinterpret_cast<uint32_t *>(buf + (size_t)r * BA * Lp); };
+
+    for (int s0 = blockIdx.y * G; s0 < S; s0 += gridDim.y * G) {
+        const int gact = min(G, S - s0);
+        const T *cv = A.cv + (size_t)s0 * A.cstride;     // member r: cv + r * cstride
+        __syncthreads();                  // tables ready / the previous group is stored
+        for (int i = threadIdx.x; i < N2; i += blockDim.x) rows_of(0)[i] = 0u;
+        for (int r = 0; r < gact; ++r)
+            for (int i = threadIdx.x; i < N2; i += blockDim.x) rows_of(r)[N2 + i] = 0u;
+        if ((int)threadIdx.x < gact) {
+            const int r = threadIdx.x;
+            g_mbits[r] = A.st[s0 + r].smax[0];
+            g_invm[r] = __fdiv_ru(65536.0f, __uint_as_float(g_mbits[r]));
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            // pass 1: common row counts, per-member strength units
+            constexpr int kRow = 4;
+            for (int e0 = threadIdx.x; e0 < total; e0 += kRow * blockDim.x) {
+                uint32_t abq[kRow];
+                V sq[kRow];
+                int jq[kRow];
+#pragma unroll
+                for (int q = 0; q < kRow; ++q) {
+                    const int e = e0 + q * (int)blockDim.x;
+                    jq[q] = -1;
+                    if (e < total) {
+                        const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
+                        abq[q] = __ldg(P.ab + j);
+                        sq[q] = __ldg(s2r + j);
+                        jq[q] = j;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kRow; ++q) {
+                    if (jq[q] < 0) break;
+                    const Foot f = footprint(abq[q], a0, BA, N1, N2, g.w);
+                    if (f.cnt <= 0) continue;
+                    atomicAdd(rows_of(0) + f.row, 1u);
+                    for (int r = 0; r < gact; ++r) {
+                        const T c = __ldg(cv + (size_t)r * A.cstride + jq[q]);
+                        atomicAdd(rows_of(r) + N2 + f.row,
+                                  row_units(strength_bound_bits(mk2(c * sq[q].x, c * sq[q].y)),
+                                            g_invm[r]));
+                    }
+                }
+            }
+            __syncthreads();
+            for (int r = 0; r < gact; ++r)
+                for (int b = threadIdx.x; b < N2; b += blockDim.x)
+                    rexp[r * N2 + b] = row_exponent_sum(g_mbits[r], rows_of(r)[N2 + b], rows_of(0)[b]);
+        } else {
+            for (int r = 0; r < gact; ++r) {
+                const signed char eb = block_exponent(g_mbits[r], total);
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) rexp[r * N2 + b] = eb;
+            }
+        }
+        __syncthreads();
+        I *ibuf = reinterpret_cast<I *>(buf);
+        if constexpr (sizeof(T) == 4) {
+            for (int r = 0; r < gact; ++r) {
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+                    if (rexp[r * N2 + b] == kRowEmpty) continue;
+                    for (int col = 0; col < BA; ++col) {
+                        I *c = ibuf + 2 * ((size_t)(r * BA + col) * Lp + pad16(b));
+                        c[0] = 0;
+                        c[1] = 0;
+                    }
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < 2 * gact * BA * Lp; i += blockDim.x) ibuf[i] = 0;
+        }
+        __syncthreads();
+        // spread: a record's kernel values once, then every member's strength
+        constexpr int kPre = 2;
+        for (int e0 = threadIdx.x; e0 < total; e0 += kPre * blockDim.x) {
+            uint32_t abv[kPre];
+            T rv[kPre];
+            V sv[kPre];
+            int jv[kPre];
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                const int e = e0 + q * (int)blockDim.x;
+                jv[q] = -1;
+                if (e < total) {
+                    const int j = (e < cnt0) ? (r0s + e) : (r1s + e - cnt0);
+                    abv[q] = __ldg(P.ab + j);
+                    rv[q] = __ldg(P.roff + j);
+                    sv[q] = __ldg(s2r + j);
+                    jv[q] = j;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPre; ++q) {
+                if (jv[q] < 0) break;
+                const Foot f = footprint(abv[q], a0, BA, N1, N2, g.w);
+                if (f.cnt <= 0) continue;
+                T kv[kKv];
+#pragma unroll
+                for (int u = 0; u < kKv; ++u) {
+                    if (u < f.cnt) {
+                        const T z = (rv[q] - halfw + T(f.i0 + u)) * zscale;
+                        if constexpr (sizeof(T) == 8) kv[u] = dfl_ok ? es_kernel_dfl(z, beta_dfl) : es_kernel(z, beta);
+                        else kv[u] = es_kernel(z, beta);
+                    }
+                }
+                for (int r = 0; r < gact; ++r) {
+                    const T c = __ldg(cv + (size_t)r * A.cstride + jv[q]);
+                    const V s1 = mk2(c * sv[q].x, c * sv[q].y);
+                    const T fs = fixed_scale(T(0), rexp[r * N2 + f.row]);
+                    const V sq = mk2(s1.x * fs, s1.y * fs);     // exact: a power of two
+                    I *dst = ibuf + 2 * ((size_t)(r * BA + f.cs) * Lp + pad16(f.row));
+#pragma unroll
+                    for (int u = 0; u < kKv; ++u) {
+                        if (u < f.cnt) {
+                            Fixed<T>::add(dst, Fixed<T>::of(sq.x * kv[u]));
+                            Fixed<T>::add(dst + 1, Fixed<T>::of(sq.y * kv[u]));
+                            dst += 2 * (size_t)Lp;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 8) {
+            for (int c = 0; c < gact * BA; ++c) {
+                const signed char *re = rexp + (c / BA) * N2;
+                for (int b = threadIdx.x; b < N2; b += blockDim.x) {
+                    const size_t i = (size_t)c * Lp + pad16(b);
+                    const T unit = fixed_unit(T(0), re[b]);
+                    bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
+                                         Fixed<T>::to(ibuf[2 * i + 1], unit)));
+                }
+            }
+            __syncthreads();
+        }
+        if constexpr (sizeof(T) == 4)
+            fft_dif_fixed<2>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
+        else
+            fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
+        // twiddle exp(2 pi i a d / n) and store H[2 + s][d][a], slot order
+        for (int pos = threadIdx.x; pos < N2; pos += blockDim.x) {
+            const int d = slot_freq_tab(pos, dtab, g.fa);
+            const int sp = pad16(pos);
+            for (int r = 0; r < gact; ++r) {
+                F *dst = reinterpret_cast<F *>(A.H + (size_t)(2 + s0 + r) * (size_t)g.n +
+                                               (size_t)d * N1 + a0);
+                if constexpr (sizeof(F) == 8) {
+                    if ((BA & 1) == 0) {
+                        for (int c0 = 0; c0 < BA; c0 += 2) {
+                            const F v0 = cmul(bufF[(size_t)(r * BA + c0) * Lp + sp],
+                                              cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]));
+                            const F v1 = cmul(bufF[(size_t)(r * BA + c0 + 1) * Lp + sp],
+                                              cmul(alo[(c0 + 1) * 64 + (d & 63)],
+                                                   ahi[(c0 + 1) * nhi + (d >> 6)]));
+                            reinterpret_cast<float4 *>(dst)[c0 >> 1] =
+                                make_float4(v0.x, v0.y, v1.x, v1.y);
+                        }
+                        continue;
+                    }
+                }
+                for (int col = 0; col < BA; ++col)
+                    dst[col] = cmul(bufF[(size_t)(r * BA + col) * Lp + sp],
+                                    cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]));
+            }
+        }
+    }
+}
+
 // One instance per block (blockIdx.y), the usual launch (two blocks per SM:
 // with three, 80 registers, small grids ran 4-12% slower).
 template <typename T, bool kCluster>
@@ -1420,7 +1839,7 @@ __global__ void __launch_bounds__(kThreadsA, kMinB) k_passA_loop(PassAArgs<T> A)
     bool first = true;
     for (int y = blockIdx.y; y < A.ny; y += gridDim.y) {
         if (A.nofit) {
-            const int grid = A.shared ? (y < 2 ? y + 1 : 0) : y % 3;
+            const int grid = y % 3;
             if (grid == 1) continue;
         }
         if (!first) __syncthreads();      // the previous instance is done with the buffer
@@ -1563,20 +1982,40 @@ __device__ __forceinline__ double ff_to_double(ff p)
 // FP32 path: the sums arrive as FP32 values (exact inputs here); the ratio is
 // evaluated in double-float, whose rounding (~1e-13 of the terms' magnitudes)
 // is far below the FP32 sums' own error, and falls back to FP64 for a nearly
-// singular M.
+// singular M.  The terms of M (from C, S, C2, S2) are formed apart from those
+// of the data (Ch, Sh), so series that share their times share them.
+struct PowerM {
+    ff CC, SS, CS, D;
+    float C, S, C2, S2;
+    bool regular;          // the closed form applies (M clearly nonsingular)
+};
+__device__ __forceinline__ PowerM power_m_ff(float C, float S, float C2, float S2, float lam_tol)
+{
+    PowerM m;
+    m.C = C;
+    m.S = S;
+    m.C2 = C2;
+    m.S2 = S2;
+    m.CC = ff_add(two_sum(0.5f, 0.5f * C2), ff_neg(two_prod(C, C)));
+    m.SS = ff_add(two_sum(0.5f, -0.5f * C2), ff_neg(two_prod(S, S)));
+    m.CS = ff_add(ff{0.5f * S2, 0.f}, ff_neg(two_prod(C, S)));
+    m.D = ff_add(ff_mul(m.CC, m.SS), ff_neg(ff_mul(m.CS, m.CS)));
+    m.regular = m.D.hi > lam_tol * (m.CC.hi + m.SS.hi) && m.CC.hi > 0.f && m.SS.hi > 0.f;
+    return m;
+}
+__device__ __forceinline__ double power_data_ff(const PowerM &m, float Ch, float Sh, ff YY,
+                                                double YYd, float lam_tol)
+{
+    if (!m.regular) return ls_power_tau(Ch, Sh, m.C, m.S, m.C2, m.S2, YYd, (double)lam_tol);
+    const ff ChSh = two_prod(Ch, Sh);
+    const ff N = ff_add(ff_add(ff_mul(two_prod(Ch, Ch), m.SS), ff_mul(two_prod(Sh, Sh), m.CC)),
+                        ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, m.CS)));
+    return ff_to_double(ff_div(N, ff_mul(m.D, YY)));
+}
 __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float S, float C2,
                                               float S2, ff YY, double YYd, float lam_tol)
 {
-    const ff CC = ff_add(two_sum(0.5f, 0.5f * C2), ff_neg(two_prod(C, C)));
-    const ff SS = ff_add(two_sum(0.5f, -0.5f * C2), ff_neg(two_prod(S, S)));
-    const ff CS = ff_add(ff{0.5f * S2, 0.f}, ff_neg(two_prod(C, S)));
-    const ff D = ff_add(ff_mul(CC, SS), ff_neg(ff_mul(CS, CS)));
-    if (!(D.hi > lam_tol * (CC.hi + SS.hi) && CC.hi > 0.f && SS.hi > 0.f))
-        return ls_power_tau(Ch, Sh, C, S, C2, S2, YYd, (double)lam_tol);
-    const ff ChSh = two_prod(Ch, Sh);
-    const ff N = ff_add(ff_add(ff_mul(two_prod(Ch, Ch), SS), ff_mul(two_prod(Sh, Sh), CC)),
-                        ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, CS)));
-    return ff_to_double(ff_div(N, ff_mul(D, YY)));
+    return power_data_ff(power_m_ff(C, S, C2, S2, lam_tol), Ch, Sh, YY, YYd, lam_tol);
 }
 
 // ---------------------------------------------------------------------------
@@ -1869,13 +2308,26 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
             const int sp = pad16(pos);
             const T dc = __ldg(dcrow + pos);
             const V g2 = bufV[sp], g3 = bufV[Lp + sp];
-            for (int r = 0; r < gact; ++r) {
-                const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
-                ff YYf;
-                YYf.hi = (float)sc[4 * r + 2];
-                YYf.lo = (float)sc[4 * r + 3];
-                const double P = PowerOut<T>::eval(g1, g2, g3, T(1), sc[4 * r], YYf, lam_tol_t);
-                B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
+            if constexpr (sizeof(T) == 4) {
+                // the terms of M are the same for every series of the group
+                const PowerM m = power_m_ff(g2.x, g2.y, g3.x, g3.y, lam_tol_t);
+                for (int r = 0; r < gact; ++r) {
+                    const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
+                    ff YYf;
+                    YYf.hi = (float)sc[4 * r + 2];
+                    YYf.lo = (float)sc[4 * r + 3];
+                    const double P = power_data_ff(m, g1.x, g1.y, YYf, sc[4 * r], lam_tol_t);
+                    B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
+                }
+            } else {
+                for (int r = 0; r < gact; ++r) {
+                    const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
+                    ff YYf;
+                    YYf.hi = (float)sc[4 * r + 2];
+                    YYf.lo = (float)sc[4 * r + 3];
+                    const double P = PowerOut<T>::eval(g1, g2, g3, T(1), sc[4 * r], YYf, lam_tol_t);
+                    B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
+                }
             }
         }
     }
@@ -2132,7 +2584,7 @@ template <typename T>
 cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capacity,
                             const Batch &bt, int64_t max_nd, const double *t, const double *y,
                             const double *dy, double *power, double *sums, int nred,
-                            cudaStream_t st, cudaEvent_t *ev, int shared, int mode)
+                            cudaStream_t st, cudaEvent_t *ev, int mode)
 {
     int nk = 6;    // kernels enqueued: stats, points, rank, chunk scan, scan, scatter, then the passes
     const int nofit = (mode & kModeNoFit) ? 1 : 0;
@@ -2167,13 +2619,14 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     k_scan<<<S, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart);
     int nsc = (int)((max_nd + 255) / 256);
     if (nsc > 4096) nsc = 4096;
-    k_scatter<T><<<dim3(nsc, S), 256, 0, st>>>(bt, g, rx, r2, sx, s2, ws.binstart, ws.chist);
+    k_scatter<T><<<dim3(nsc, S), 256, 0, st>>>(bt, g, rx, r2, sx, s2, ws.binstart, ws.chist,
+                                               nullptr);
 
     if (ev) cudaEventRecord(ev[2], st);
     PassAArgs<T> A;
     A.g = g;
     A.bt = bt;
-    A.shared = shared;
+    A.shared = 0;
     A.nofit = nofit;
     A.px = sx;
     A.p2 = s2;
@@ -2210,10 +2663,9 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // keeps the launch within about eight blocks per SM; beyond that the blocks
     // loop over instances (tables built once per block).
     const int target = 8 * nsm;
-    A.ny = shared ? S + 2 : 3 * S;
+    A.ny = 3 * S;
     // Small grids: the instances go through k_passA_group, `group` per block
-    // iteration (in a shared-times batch only the series grids; the common
-    // grids through the usual kernel first).
+    // iteration.
     const size_t cxA = sizeof(Cplx<T>);
     // a member's columns and its rows' exponent bytes
     const size_t colA = (size_t)g.BA * padded_len(g.N2) * cxA + (size_t)g.N2;
@@ -2221,7 +2673,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
                         sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
     int groupA = (int)((kGroupSmemBudget - tabA) / colA);
     groupA = groupA > 8 ? 8 : groupA;
-    const int ninst = shared ? S : (nofit ? 2 * S : 3 * S);
+    const int ninst = nofit ? 2 * S : 3 * S;
     // a launch whose instances all fit the two-block budget takes them in one
     // block iteration (2 blocks per SM then)
     if (ninst <= 8 && groupA < ninst && (size_t)ninst * colA + tabA <= 100 * 1024) groupA = ninst;
@@ -2231,7 +2683,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     // column blocks of FP64 ran 17% faster grouped)
     const bool grouped = cs == 1 && g.BA >= 2 && groupA >= 2 && ninst >= 2 &&
                          (ninst > 3 || g.nbins >= nsm);
-    if (grouped) A.ny = shared ? 2 : 0;
+    if (grouped) A.ny = 0;
     int gyA = (target + g.nbins - 1) / g.nbins;
     if (gyA < 3) gyA = 3;
     if (gyA > A.ny) gyA = A.ny;
@@ -2263,7 +2715,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         if (err != cudaSuccess) return err;
     }
     if (grouped) {
-        A.ny = shared ? S + 2 : 3 * S;
+        A.ny = 3 * S;
         A.group = groupA;
         const size_t smS = (size_t)groupA * colA + tabA;
         if ((err = allow_max_dynamic_smem((const void *)k_passA_group<T>)) != cudaSuccess)
@@ -2279,7 +2731,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     PassBArgs<T> B;
     B.g = g;
     B.bt = bt;
-    B.shared = shared;
+    B.shared = 0;
     B.twB = static_cast<const Cplx<T> *>(ws.twB);
     B.H = static_cast<Cplx<T> *>(ws.H);
     B.deconv = static_cast<const T *>(ws.deconv_slot);
@@ -2302,22 +2754,11 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
     }
     const bool threeB = blocks_per_sm(smB) >= 3;
-    if ((err = allow_max_dynamic_smem((const void *)k_passB_series<T>)) != cudaSuccess) return err;
     B.nser = S;
     int gyB = (target + g.N2 - 1) / g.N2;
     if (gyB < 1) gyB = 1;
     if (gyB > S) gyB = S;
-    if (shared) {
-        B.stage = 1;
-        if (threeB) k_passB<T, 1, 3><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
-        else k_passB<T, 1, 2><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
-        B.stage = 2;
-        B.group = passB_group(g, sizeof(Cplx<T>));
-        int gy2 = (S + B.group - 1) / B.group;
-        if (gy2 > gyB) gy2 = gyB;
-        k_passB_series<T><<<dim3(g.N2, gy2), kThreadsB,
-                            passB_series_smem_bytes(g, sizeof(Cplx<T>), B.group), st>>>(B);
-    } else {
+    {
         B.stage = 0;
         // Small rows: `group` series per block iteration (power output only).
         const int nr = nofit ? 2 : 3;
@@ -2337,8 +2778,206 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             else k_passB<T, 0, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
         }
     }
-    nk += shared ? 2 : 1;
+    ++nk;
     if (ev) cudaEventRecord(ev[4], st);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) g_pipeline_kernels.fetch_add(nk, std::memory_order_relaxed);
+    return err;
+}
+
+// Shared memory of k_passA_sh for G members: their columns and row exponent
+// bytes, the column tables, the root and slot tables.
+static size_t passA_sh_smem_bytes(const Geometry &g, size_t cx, int G)
+{
+    const size_t nhi = (size_t)(g.N2 + 63) / 64;
+    return (size_t)G * ((size_t)g.BA * padded_len(g.N2) * cx + (size_t)g.N2) +
+           cx * ((size_t)g.BA * (64 + nhi) + 64 + nhi) + sizeof(int) * (size_t)(g.N2 / g.fa.Rlast);
+}
+
+// Shared-times batch of bt.S series (one time array t and one dy, series s's
+// data at Y + y_off of its descriptor, all of nd points): the common weights,
+// records, sort and w^ transforms once; per series its sums and scalars; then
+// the series grids in chunks of shared_chunk_series() series, pass A and pass
+// B of a chunk back to back (its grids in slots 2 .. of H, reused by every
+// chunk).  ws: H of 2 + chunk grids, the common record
+// sets for nd points, one series' bin tables, perm, wts, cvals (S x nd), and
+// Stats / tickets for S + 1 entries (the common entry at S).
+template <typename T>
+cudaError_t launch_shared_pipeline(const Geometry &g, const Workspace &ws, const Batch &bt,
+                                   int64_t nd, const double *t, const double *Y,
+                                   const double *dy, double *power, int nred, cudaStream_t st,
+                                   int mode)
+{
+    int nk = 0;
+    cudaError_t err;
+    const int nofit = (mode & kModeNoFit) ? 1 : 0;
+    const int center = (!nofit || !(mode & kModeNoCenter)) ? 1 : 0;
+    const int S = bt.S;
+    const size_t cx = sizeof(Cplx<T>);
+    int nsm = 0, dev_id = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+    if (nsm <= 0) nsm = 152;
+    Stats *stc = ws.stats + S;
+    PointSet<T> rx = carve<T>(ws.pts_raw[0], nd), r2 = carve<T>(ws.pts_raw[1], nd);
+    PointSet<T> sx = carve<T>(ws.pts_sorted[0], nd), s2 = carve<T>(ws.pts_sorted[1], nd);
+    T *cvals = static_cast<T *>(ws.cvals);
+    // the common records as a one-series batch
+    Batch bc;
+    bc.S = 1;
+    bc.many = nullptr;
+    bc.one = bt.one;
+    bc.one.pt_off = 0;
+    bc.one.y_off = 0;
+    bc.one.rec_off = 0;
+    bc.one.nd = nd;
+    int nredc = (int)((nd + 255) / 256);
+    if (nredc > 8 * nsm) nredc = 8 * nsm;
+    k_sh_weights<<<nredc, 256, 0, st>>>(t, dy, nd, ws.wts, ws.partials, ws.counter + 2 * S, stc,
+                                        ws.status);
+    k_sh_points<T><<<nredc, 256, 0, st>>>(t, nd, bc.one.ph, g, ws.wts, rx, r2, stc);
+    nk += 2;
+    {
+        const size_t smR = sizeof(unsigned short) * 2 * (kThreadsPts / 32) * (size_t)g.nbins;
+        if ((err = allow_max_dynamic_smem((const void *)k_rank)) != cudaSuccess) return err;
+        int64_t nrk = (nd + kChunk - 1) / kChunk;
+        if (nrk > 8 * (int64_t)nsm) nrk = 8 * (int64_t)nsm;
+        k_rank<<<dim3((unsigned)nrk, 1), kThreadsPts, smR, st>>>(bc, g, rx.ab, r2.ab, rx.rank,
+                                                               ws.chist);
+        k_chunk_scan<<<dim3((2 * g.nbins + 31) / 32, 1), 256, 0, st>>>(bc, g.nbins, ws.chist,
+                                                                       ws.hist);
+        k_scan<<<1, 1024, 0, st>>>(ws.hist, g.nbins, ws.binstart);
+        int nsc = (int)((nd + 255) / 256);
+        if (nsc > 4096) nsc = 4096;
+        k_scatter<T><<<dim3(nsc, 1), 256, 0, st>>>(bc, g, rx, r2, sx, s2, ws.binstart, ws.chist,
+                                                   ws.perm);
+        nk += 4;
+    }
+    k_sh_stats<<<dim3(nred, S), 256, 0, st>>>(Y, bt, ws.wts, stc, ws.partials, ws.counter,
+                                              ws.stats, ws.status, center);
+    k_sh_series<T><<<dim3(nred, S), 256, 0, st>>>(Y, bt, ws.wts, ws.perm, sx.s[1], cvals,
+                                                  ws.partials, ws.counter, ws.stats, ws.status);
+    nk += 2;
+
+    // the common w^ transforms at f and 2f (H slots 0 and 1; slot 0 is not
+    // needed without a fitted mean), stage 1 of pass B deconvolves them in place
+    PassAArgs<T> A;
+    A.g = g;
+    A.bt = bc;
+    A.shared = 1;
+    A.nofit = nofit;
+    A.px = sx;
+    A.p2 = s2;
+    A.binstart = ws.binstart;
+    A.st = stc;
+    A.twA = static_cast<const Cplx<T> *>(ws.twA);
+    A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
+    A.H = static_cast<Cplx<T> *>(ws.H);
+    A.ny = 2;
+    A.group = 1;
+    A.cv = nullptr;
+    A.cstride = 0;
+    {
+        int cs = g.nbins >= 512 ? 2 : 1;
+        while (cs > 1 && (cs * g.BA * (int)cx) % 16) cs >>= 1;
+        size_t smA = passA_smem_bytes(g, cx, cs);
+        if (cs > 1 && smA + 1024 > kSmemOptinBytes) {
+            cs = 1;
+            smA = passA_smem_bytes(g, cx, cs);
+        }
+        A.cs = cs;
+        if ((err = allow_max_dynamic_smem((const void *)k_passA<T, false>)) != cudaSuccess ||
+            (err = allow_max_dynamic_smem((const void *)k_passA<T, true>)) != cudaSuccess)
+            return err;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g.nbins, 2);
+        cfg.blockDim = dim3(kThreadsA);
+        cfg.dynamicSmemBytes = smA;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA<T, true>, A)
+                     : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
+        if (err != cudaSuccess) return err;
+        ++nk;
+    }
+    PassBArgs<T> B;
+    B.g = g;
+    B.bt = bc;
+    B.shared = 1;
+    B.stage = 1;
+    B.twB = static_cast<const Cplx<T> *>(ws.twB);
+    B.H = static_cast<Cplx<T> *>(ws.H);
+    B.deconv = static_cast<const T *>(ws.deconv_slot);
+    B.st = stc;
+    B.power = power;
+    B.sums = nullptr;
+    B.nofit = nofit;
+    B.norm = mode & kModeNormMask;
+    B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
+    B.nser = 1;
+    B.group = 1;
+    {
+        const size_t smB = passB_smem_bytes(g, cx);
+        if ((err = allow_max_dynamic_smem((const void *)k_passB<T, 1, 2>)) != cudaSuccess ||
+            (err = allow_max_dynamic_smem((const void *)k_passB<T, 1, 3>)) != cudaSuccess)
+            return err;
+        if (blocks_per_sm(smB) >= 3) k_passB<T, 1, 3><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        else k_passB<T, 1, 2><<<dim3(g.N2, 1), kThreadsB, smB, st>>>(B);
+        ++nk;
+    }
+
+    // the series grids, chunk by chunk through H
+    const size_t colA = (size_t)g.BA * padded_len(g.N2) * cx + (size_t)g.N2;
+    const size_t tabA = passA_sh_smem_bytes(g, cx, 0);
+    int GA = tabA + colA <= kGroupSmemBudget ? (int)((kGroupSmemBudget - tabA) / colA) : 1;
+    if (GA > kMaxGroup) GA = kMaxGroup;
+    const size_t smS = passA_sh_smem_bytes(g, cx, GA);
+    if ((err = allow_max_dynamic_smem((const void *)k_passA_sh<T, 8>)) != cudaSuccess ||
+        (err = allow_max_dynamic_smem((const void *)k_passA_sh<T, 16>)) != cudaSuccess)
+        return err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passB_series<T>)) != cudaSuccess) return err;
+    const int GB = passB_group(g, cx);
+    const size_t smBS = passB_series_smem_bytes(g, cx, GB);
+    const int64_t C = shared_chunk_series(g.n, cx, S);
+    const int target = 8 * nsm;
+    for (int64_t c0 = 0; c0 < S; c0 += C) {
+        const int Sc = (int)(S - c0 < C ? S - c0 : C);
+        Batch bk;
+        bk.S = Sc;
+        bk.many = bt.many ? bt.many + c0 : nullptr;
+        bk.one = bt.one;
+        PassAArgs<T> Ak = A;
+        Ak.bt = bk;
+        Ak.st = ws.stats + c0;
+        Ak.ny = Sc;
+        Ak.group = GA;
+        Ak.cs = 1;
+        Ak.cv = cvals + (size_t)c0 * (size_t)nd;
+        Ak.cstride = nd;
+        int gyA = (Sc + GA - 1) / GA;
+        const int capA = (target + g.nbins - 1) / g.nbins;
+        if (gyA > capA) gyA = capA;
+        if (g.BA <= 8) k_passA_sh<T, 8><<<dim3(g.nbins, gyA), kThreadsA, smS, st>>>(Ak);
+        else k_passA_sh<T, 16><<<dim3(g.nbins, gyA), kThreadsA, smS, st>>>(Ak);
+        PassBArgs<T> Bk = B;
+        Bk.bt = bk;
+        Bk.st = ws.stats + c0;
+        Bk.stage = 2;
+        Bk.nser = Sc;
+        Bk.group = GB;
+        int gyB = (Sc + GB - 1) / GB;
+        const int capB = (target + g.N2 - 1) / g.N2;
+        if (gyB > capB) gyB = capB;
+        if (gyB < 1) gyB = 1;
+        k_passB_series<T><<<dim3(g.N2, gyB), kThreadsB, smBS, st>>>(Bk);
+        nk += 2;
+    }
     err = cudaGetLastError();
     if (err == cudaSuccess) g_pipeline_kernels.fetch_add(nk, std::memory_order_relaxed);
     return err;
@@ -2359,11 +2998,19 @@ cudaError_t launch_deconv_table(const Geometry &g, void *deconv, int64_t count,
 template cudaError_t launch_pipeline<float>(const Geometry &, const Workspace &, int64_t,
                                             const Batch &, int64_t, const double *,
                                             const double *, const double *, double *, double *,
-                                            int, cudaStream_t, cudaEvent_t *, int, int);
+                                            int, cudaStream_t, cudaEvent_t *, int);
 template cudaError_t launch_pipeline<double>(const Geometry &, const Workspace &, int64_t,
                                              const Batch &, int64_t, const double *,
                                              const double *, const double *, double *, double *,
-                                             int, cudaStream_t, cudaEvent_t *, int, int);
+                                             int, cudaStream_t, cudaEvent_t *, int);
+template cudaError_t launch_shared_pipeline<float>(const Geometry &, const Workspace &,
+                                                   const Batch &, int64_t, const double *,
+                                                   const double *, const double *, double *, int,
+                                                   cudaStream_t, int);
+template cudaError_t launch_shared_pipeline<double>(const Geometry &, const Workspace &,
+                                                    const Batch &, int64_t, const double *,
+                                                    const double *, const double *, double *, int,
+                                                    cudaStream_t, int);
 cudaError_t launch_kernel_eval_pair(int n, double beta, double *dfl_out, double *fp64_out,
                                     cudaStream_t st)
 {
