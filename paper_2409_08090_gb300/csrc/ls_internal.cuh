@@ -12,6 +12,15 @@ namespace nls {
 constexpr int kMaxStages = 8;     // stages of one sub-FFT
 constexpr int kTw4Bits = 12;      // four-step twiddle table split: W^p = lo[p % 4096] * hi[p / 4096]
 constexpr int kThreadsA = 256;
+// Single-instance pass-A blocks of the FP32 path: 12 warps (two blocks per SM,
+// 80 registers; on the 1.9e7-cell grid 0.68 ms against 0.72 ms with 8 warps).
+constexpr int kThreadsAWide = 384;
+// FP64 path (one block per SM on the large grids): threads of the single-
+// instance pass-A block and of the pass-B block where only one fits an SM
+// (1.9e7-cell grid: pass A 4.17 ms with 256 threads, 5.12 ms with 512; pass B
+// 3.36 ms with 256, 3.28 ms with 512 or 768).
+constexpr int kThreadsAF64 = 256;
+constexpr int kThreadsBF64 = 512;
 constexpr size_t kSmemOptinBytes = 232448;   // opt-in shared memory per block (227 KB)
 constexpr int kThreadsB = 256;
 // Pass-B blocks of the FP32 path where shared memory holds two blocks per SM:

@@ -1818,9 +1818,10 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassA
 }
 
 // One instance per block (blockIdx.y), the usual launch (two blocks per SM:
-// with three, 80 registers, small grids ran 4-12% slower).
-template <typename T, bool kCluster>
-__global__ void __launch_bounds__(kThreadsA, 2) k_passA(PassAArgs<T> A)
+// with three, 80 registers, small grids ran 4-12% slower).  kThr threads per
+// block: the FP32 path takes kThreadsAWide.
+template <typename T, bool kCluster, int kThr = kThreadsA, int kMinB = 2>
+__global__ void __launch_bounds__(kThr, kMinB) k_passA(PassAArgs<T> A)
 {
     passA_instance<T, kCluster>(A, (int)blockIdx.y, true);
 }
@@ -2575,6 +2576,25 @@ static cudaError_t allow_max_dynamic_smem(const void *fn)
     return cudaSuccess;
 }
 
+// Launch k_passA (one instance per block) with cfg's grid, shared memory and
+// cluster attribute: FP32 blocks of kThreadsAWide threads, FP64 blocks of
+// kThreadsAF64 (compiled for one block per SM when wider than kThreadsA: the
+// FP64 columns leave room for one).
+template <typename T>
+static cudaError_t launch_passA_single(cudaLaunchConfig_t cfg, int cs, const PassAArgs<T> &A)
+{
+    constexpr int kThr = sizeof(T) == 4 ? kThreadsAWide : kThreadsAF64;
+    constexpr int kMinB = (sizeof(T) == 8 && kThr > kThreadsA) ? 1 : 2;
+    cudaError_t err;
+    if ((err = allow_max_dynamic_smem((const void *)k_passA<T, false, kThr, kMinB>)) !=
+            cudaSuccess ||
+        (err = allow_max_dynamic_smem((const void *)k_passA<T, true, kThr, kMinB>)) != cudaSuccess)
+        return err;
+    cfg.blockDim = dim3(kThr);
+    return cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA<T, true, kThr, kMinB>, A)
+                  : cudaLaunchKernelEx(&cfg, k_passA<T, false, kThr, kMinB>, A);
+}
+
 // Kernels launch_pipeline has enqueued (or recorded into graphs) in this process.
 static std::atomic<long long> g_pipeline_kernels{0};
 
@@ -2636,8 +2656,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     A.tw4 = static_cast<const Cplx<T> *>(ws.tw4);
     A.H = static_cast<Cplx<T> *>(ws.H);
     {
-        const void *fns[6] = {(const void *)k_passA<T, false>, (const void *)k_passA<T, true>,
-                              (const void *)k_passA_loop<T, false, 2>,
+        const void *fns[4] = {(const void *)k_passA_loop<T, false, 2>,
                               (const void *)k_passA_loop<T, true, 2>,
                               (const void *)k_passA_loop<T, false, 3>,
                               (const void *)k_passA_loop<T, true, 3>};
@@ -2704,8 +2723,7 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
         const bool three = blocks_per_sm(smA) >= 3;
         ++nk;
         if (!loop)
-            err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA<T, true>, A)
-                         : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
+            err = launch_passA_single<T>(cfg, cs, A);
         else if (three)
             err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA_loop<T, true, 3>, A)
                          : cudaLaunchKernelEx(&cfg, k_passA_loop<T, false, 3>, A);
@@ -2747,9 +2765,10 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     B.lam_tol = 10.0 * fmax(g.eps, sizeof(T) == 4 ? 1e-7 : 1e-16);
     const size_t smB = passB_smem_bytes(g, sizeof(Cplx<T>));
     {
-        const void *fns[5] = {(const void *)k_passB<T, 0, 2>, (const void *)k_passB<T, 1, 2>,
+        const void *fns[6] = {(const void *)k_passB<T, 0, 2>, (const void *)k_passB<T, 1, 2>,
                               (const void *)k_passB<T, 0, 3>, (const void *)k_passB<T, 1, 3>,
-                              (const void *)k_passB<T, 0, 2, kThreadsBWide>};
+                              (const void *)k_passB<T, 0, 2, kThreadsBWide>,
+                              (const void *)k_passB<T, 0, 1, kThreadsBF64>};
         for (const void *f : fns)
             if ((err = allow_max_dynamic_smem(f)) != cudaSuccess) return err;
     }
@@ -2775,6 +2794,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
             if (threeB) k_passB<T, 0, 3><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
             else if (sizeof(T) == 4)
                 k_passB<T, 0, 2, kThreadsBWide><<<dim3(g.N2, gyB), kThreadsBWide, smB, st>>>(B);
+            else if (kThreadsBF64 > kThreadsB && blocks_per_sm(smB) < 2)
+                k_passB<T, 0, 1, kThreadsBF64><<<dim3(g.N2, gyB), kThreadsBF64, smB, st>>>(B);
             else k_passB<T, 0, 2><<<dim3(g.N2, gyB), kThreadsB, smB, st>>>(B);
         }
     }
@@ -2886,12 +2907,8 @@ cudaError_t launch_shared_pipeline(const Geometry &g, const Workspace &ws, const
             smA = passA_smem_bytes(g, cx, cs);
         }
         A.cs = cs;
-        if ((err = allow_max_dynamic_smem((const void *)k_passA<T, false>)) != cudaSuccess ||
-            (err = allow_max_dynamic_smem((const void *)k_passA<T, true>)) != cudaSuccess)
-            return err;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(g.nbins, 2);
-        cfg.blockDim = dim3(kThreadsA);
         cfg.dynamicSmemBytes = smA;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -2901,9 +2918,7 @@ cudaError_t launch_shared_pipeline(const Geometry &g, const Workspace &ws, const
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        err = cs > 1 ? cudaLaunchKernelEx(&cfg, k_passA<T, true>, A)
-                     : cudaLaunchKernelEx(&cfg, k_passA<T, false>, A);
-        if (err != cudaSuccess) return err;
+        if ((err = launch_passA_single<T>(cfg, cs, A)) != cudaSuccess) return err;
         ++nk;
     }
     PassBArgs<T> B;
