@@ -461,13 +461,13 @@ __device__ __forceinline__ void dif_stage_cols(V *buf, int ncol, int colstride, 
 
 // In-place DIF FFT of `ncol` transforms of length fp.L in shared memory
 // (padded layout, columns colstride apart), up to NC of them per thread at a
-// time (at most 2 for radix 16, to stay within 128 registers in FP32).
-// Ends with a barrier; output in digit-reversed order (see slot_to_freq).
-template <int NC, typename V>
+// time, NC16 for radix 16 (at most 2 by default, to stay within 128 registers
+// in FP32; 1 for blocks compiled for 80).  Ends with a barrier; output in
+// digit-reversed order (see slot_to_freq).
+template <int NC, int NC16 = (NC < 2 ? NC : 2), typename V>
 __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, const V *roots,
                         int first = 0)
 {
-    constexpr int NC16 = NC < 2 ? NC : 2;
     for (int s = first; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
@@ -507,11 +507,10 @@ __device__ void fft_dif_dealt(V *buf, int ncol, int colstride, const FftPlan &fp
 // fft_dif over FP32 columns holding the spread's fixed-point pairs: the
 // first stage converts as it loads (dif_stage_first_fixed), the rest run as
 // usual.  Ends with a barrier.
-template <int NC>
+template <int NC, int NC16 = (NC < 2 ? NC : 2)>
 __device__ void fft_dif_fixed(float2 *buf, int ncol, int colstride, const FftPlan &fp,
                               const float2 *roots, const signed char *rexp, int BA, int rstride)
 {
-    constexpr int NC16 = NC < 2 ? NC : 2;
     const FftStage &st = fp.st[0];
     switch (st.R) {
     case 16: first_stage_fixed_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
@@ -523,7 +522,7 @@ __device__ void fft_dif_fixed(float2 *buf, int ncol, int colstride, const FftPla
     default: first_stage_fixed_cols<2, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
     }
     __syncthreads();
-    fft_dif<NC>(buf, ncol, colstride, fp, roots, 1);
+    fft_dif<NC, NC16>(buf, ncol, colstride, fp, roots, 1);
 }
 
 }  // namespace nls

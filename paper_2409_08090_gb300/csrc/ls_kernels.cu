@@ -802,7 +802,7 @@ __global__ void k_kernel_eval_pair(int n, double beta, double *dfl_out, double *
 // One instance (a transform of a series) of one column block; the tables are
 // built when build_tables is set (the first instance a block takes).  kCluster:
 // the launch pairs column blocks in clusters (A.cs > 1), the store path then.
-template <typename T, bool kCluster>
+template <typename T, bool kCluster, int kNC16 = 2>
 __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int y,
                                                const bool build_tables)
 {
@@ -997,7 +997,7 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     // pairs, converts them with their rows' units and skips empty rows' loads.
     // FP64: convert in place first (same 16 bytes per cell) ----
     if constexpr (sizeof(T) == 4) {
-        if ((BA & 1) == 0) fft_dif_fixed<2>(bufF, BA, Lp, g.fa, roots, rexp, BA, 0);
+        if ((BA & 1) == 0) fft_dif_fixed<2, kNC16>(bufF, BA, Lp, g.fa, roots, rexp, BA, 0);
         else fft_dif_fixed<1>(bufF, BA, Lp, g.fa, roots, rexp, BA, 0);
     } else {
         for (int col = 0; col < BA; ++col) {
@@ -1032,9 +1032,12 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int sub_row = lane / lr, u0 = lane - sub_row * lr;
         F *Hc = reinterpret_cast<F *>(A.H + (size_t)slot * (size_t)g.n + (size_t)(blk - rank) * BA);
-        const F *peer[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) peer[q] = q < cs ? cluster.map_shared_rank(bufF, q) : bufF;
+        // the block holding column c of the cluster: c / BA (its own columns are
+        // read directly, the others through the cluster's shared-memory window)
+        auto col_base = [&](int c) -> const F * {
+            const int q = c / BA;
+            return (q == rank ? bufF : cluster.map_shared_rank(bufF, q)) + (size_t)(c - q * BA) * Lp;
+        };
         const int nwarps = (int)(blockDim.x >> 5);
         const int rows = (N2 - rank + cs - 1) / cs;               // rows this block writes
         const int step = nwarps * rpw;
@@ -1045,6 +1048,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
             for (int u = u0; u < ur; u += lr) {
                 F va[kRows], vb[kRows];
                 int dd[kRows];
+                const int c0 = sizeof(V) == 8 ? 2 * u : u, c1 = c0 + 1;
+                const F *pa = col_base(c0);
+                const F *pb = sizeof(V) == 8 ? col_base(c1) : pa;
 #pragma unroll
                 for (int r = 0; r < kRows; ++r) {
                     const int i = i0 + r * step;
@@ -1054,16 +1060,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
                         dd[r] = slot_freq_tab(pos, dtab, g.fa);
                         const int sp = pad16(pos);
                         const int dl = dd[r] & 63, dh = dd[r] >> 6;
-                        if constexpr (sizeof(V) == 8) {
-                            const int c0 = 2 * u, c1 = 2 * u + 1;
-                            va[r] = cmul(peer[c0 / BA][(size_t)(c0 % BA) * Lp + sp],
-                                         cmul(alo[c0 * 64 + dl], ahi[c0 * nhi + dh]));
-                            vb[r] = cmul(peer[c1 / BA][(size_t)(c1 % BA) * Lp + sp],
-                                         cmul(alo[c1 * 64 + dl], ahi[c1 * nhi + dh]));
-                        } else {
-                            va[r] = cmul(peer[u / BA][(size_t)(u % BA) * Lp + sp],
-                                         cmul(alo[u * 64 + dl], ahi[u * nhi + dh]));
-                        }
+                        va[r] = cmul(pa[sp], cmul(alo[c0 * 64 + dl], ahi[c0 * nhi + dh]));
+                        if constexpr (sizeof(V) == 8)
+                            vb[r] = cmul(pb[sp], cmul(alo[c1 * 64 + dl], ahi[c1 * nhi + dh]));
                     }
                 }
 #pragma unroll
@@ -1823,7 +1822,10 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassA
 template <typename T, bool kCluster, int kThr = kThreadsA, int kMinB = 2>
 __global__ void __launch_bounds__(kThr, kMinB) k_passA(PassAArgs<T> A)
 {
-    passA_instance<T, kCluster>(A, (int)blockIdx.y, true);
+    // blocks compiled for 80 registers take the radix-16 stages one column at
+    // a time (fewer live values; on the 1.9e7-cell grid 0.647 -> 0.637 ms)
+    constexpr int kNC16 = (kThr > kThreadsA && sizeof(T) == 4) ? 1 : 2;
+    passA_instance<T, kCluster, kNC16>(A, (int)blockIdx.y, true);
 }
 
 // Many instances per block: y = blockIdx.y, + gridDim.y, ... of the block's
