@@ -1365,7 +1365,7 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
             __syncthreads();
         }
         if constexpr (sizeof(T) == 4)
-            fft_dif_fixed<2>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
+            fft_dif_fixed<2, 1>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
         else
             fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
         // twiddle exp(2 pi i a d / n) and store H[2 + s][d][a], slot order; the
@@ -1784,7 +1784,7 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassA
             __syncthreads();
         }
         if constexpr (sizeof(T) == 4)
-            fft_dif_fixed<2>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
+            fft_dif_fixed<2, 1>(bufF, gact * BA, Lp, g.fa, roots, rexp, BA, N2);
         else
             fft_dif<1>(bufF, gact * BA, Lp, g.fa, roots);
         // twiddle exp(2 pi i a d / n) and store H[2 + s][d][a], slot order
@@ -1846,7 +1846,7 @@ __global__ void __launch_bounds__(kThreadsA, kMinB) k_passA_loop(PassAArgs<T> A)
             if (grid == 1) continue;
         }
         if (!first) __syncthreads();      // the previous instance is done with the buffer
-        passA_instance<T, kCluster>(A, y, first);
+        passA_instance<T, kCluster, (kMinB >= 3 && sizeof(T) == 4) ? 1 : 2>(A, y, first);
         first = false;
     }
 }
