@@ -354,6 +354,20 @@ double ls_kernel_ft(double k, int64_t n, int32_t width, double beta);
 ls_status ls_selftest_kernel_eval(double beta, int n, int device, double *max_abs_err);
 
 /*
+ * ls_selftest_double_assembly: checks, on `device`, the FP32 path's assembly
+ * of the double-float power ratio hi + lo into a double on the integer pipe
+ * (the power of Sec. 1 is written as FP64) against the FP64 conversions and
+ * add it replaces, on n pairs (1 <= n <= 2^32) with |lo| <= ulp(hi)/2 drawn
+ * from a counter-based generator seeded by `seed`: values over every exponent
+ * and both signs, powers of two, the fast path's exponent bound, ties at the
+ * double's rounding position, zero, subnormal and non-finite hi.  Writes the
+ * number of pairs whose results differ in any bit to *mismatches (NaN against
+ * NaN counts as equal).  Synchronous on the legacy default stream; allocates 8
+ * bytes.
+ */
+ls_status ls_selftest_double_assembly(int64_t n, uint64_t seed, int device, int64_t *mismatches);
+
+/*
  * ls_execute_noalloc: the periodogram of one small series without allocating
  * any memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- programs whose device memory

@@ -76,6 +76,8 @@ _SIGS = {
     "ls_plan_ex": (ctypes.c_int, [ctypes.POINTER(_c_void_p), _i64, _i64, _dbl, ctypes.c_int,
                                   ctypes.c_int, _c_void_p, ctypes.c_void_p]),
     "ls_kernel_ft": (_dbl, [_dbl, _i64, _i32, _dbl]),
+    "ls_selftest_double_assembly": (ctypes.c_int, [_i64, ctypes.c_uint64, ctypes.c_int,
+                                                   ctypes.POINTER(_i64)]),
     "ls_selftest_kernel_eval": (ctypes.c_int, [_dbl, ctypes.c_int, ctypes.c_int,
                                                ctypes.POINTER(_dbl)]),
     "ls_execute_batch": (ctypes.c_int, [_c_void_p, _i64, _c_void_p, _c_void_p, _c_void_p,

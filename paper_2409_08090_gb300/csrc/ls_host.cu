@@ -49,7 +49,6 @@ constexpr int kMaxBatchS = 16384;   // series per batch launch
 struct BatchWorkspace {
     void *arena = nullptr;
     int64_t arena_bytes = 0;
-    double *partials = nullptr;        // 3 (8 nsm + kMaxBatchS) reduction partials
     unsigned int *counter = nullptr;   // 2 kMaxBatchS last-block tickets
     Stats *stats = nullptr;            // kMaxBatchS
     SeriesDesc *desc = nullptr;        // kMaxBatchS
@@ -59,7 +58,7 @@ struct BatchWorkspace {
 
 // Offsets of one launch's buffers inside a lane arena (256-byte aligned).
 struct LaunchCarve {
-    size_t H, pts[4], hist, binstart, chist, bytes;
+    size_t H, pts[4], hist, binstart, chist, partials, bytes;
     size_t perm = 0, wts = 0, cvals = 0;   // shared-times launches only
 };
 
@@ -82,6 +81,8 @@ LaunchCarve carve_launch(int64_t n, int nbins, size_t cx, size_t recb, int64_t S
     off = al(off + sizeof(int) * 2 * ((size_t)nbins + 1) * (size_t)S);
     c.chist = off;
     off = al(off + sizeof(int) * (size_t)chunk_hist_entries(points, (int)S, nbins));
+    c.partials = off;
+    off = al(off + sizeof(double) * 3 * (size_t)red_rows(points, S));
     c.bytes = off;
     return c;
 }
@@ -554,7 +555,8 @@ ls_status plan_workspace(ls_plan_s *p, bool tables_only)
         LS_OK)
         return s;
     p->ws.chist = static_cast<int *>(v);
-    if ((s = plan_alloc(p, &v, sizeof(double) * 3 * (size_t)p->nred)) != LS_OK) return s;
+    if ((s = plan_alloc(p, &v, sizeof(double) * 3 * (size_t)red_rows(p->max_nd, 1))) != LS_OK)
+        return s;
     p->ws.partials = static_cast<double *>(v);
     if ((s = plan_alloc(p, &v, 256)) != LS_OK) return s;
     p->ws.counter = static_cast<unsigned int *>(v);
@@ -742,10 +744,6 @@ ls_status reserve_ws(BatchWorkspace &b, cudaStream_t st, int nsm, int64_t arena_
     ls_status s;
     if (!b.stats) {
         void *v;
-        const size_t np = 3 * ((size_t)8 * nsm + kMaxBatchS);
-        if ((s = alloc(&v, sizeof(double) * np)) != LS_OK) return s;
-        b.allocs.push_back(v);
-        b.partials = static_cast<double *>(v);
         if ((s = alloc(&v, sizeof(unsigned int) * 2 * kMaxBatchS)) != LS_OK) return s;
         b.allocs.push_back(v);
         b.counter = static_cast<unsigned int *>(v);
@@ -801,7 +799,7 @@ Workspace lane_workspace(const BatchWorkspace &b, const LaunchCarve &c, int *sta
         ws.wts = reinterpret_cast<double *>(a + c.wts);
         ws.cvals = a + c.cvals;
     }
-    ws.partials = b.partials;
+    ws.partials = reinterpret_cast<double *>(a + c.partials);
     ws.counter = b.counter;
     ws.stats = b.stats;
     ws.status = status;
@@ -1066,6 +1064,8 @@ LaunchCarve carve_shared(int prec, int64_t n, int nbins, int64_t S, int64_t nd)
     off = al(off + sizeof(double) * (size_t)nd);
     c.cvals = off;
     off = al(off + tb * (size_t)S * (size_t)nd);
+    c.partials = off;
+    off = al(off + sizeof(double) * 3 * (size_t)red_rows(S * nd, S));
     c.bytes = off;
     return c;
 }
@@ -1709,6 +1709,24 @@ ls_status ls_selftest_kernel_eval(double beta, int n, int device, double *max_ab
         if (!(d <= worst)) worst = d;
     }
     *max_abs_err = worst;
+    return LS_OK;
+}
+
+ls_status ls_selftest_double_assembly(int64_t n, uint64_t seed, int device, int64_t *mismatches)
+{
+    if (!mismatches || n < 1 || n > ((int64_t)1 << 32)) return LS_ERR_ARG;
+    DeviceGuard guard(device);
+    if (!guard.ok) return LS_ERR_CUDA;
+    unsigned long long *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long));
+    if (e != cudaSuccess) return LS_ERR_NOMEM;
+    unsigned long long h = 0;
+    e = cudaMemset(d, 0, sizeof h);
+    if (e == cudaSuccess) e = launch_ff_assembly_check((long long)n, (unsigned long long)seed, d, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(e);
+    *mismatches = (int64_t)h;
     return LS_OK;
 }
 

@@ -105,6 +105,16 @@ __host__ __device__ inline int64_t chunk_hist_entries(int64_t points, int S, int
     return (points / kChunk + S) * 2 * (int64_t)nbins;
 }
 
+// FP64 reductions are summed per fixed chunk of kRedChunk consecutive points
+// (a block of 256 threads in a fixed order), and the chunk partials in a fixed
+// tree, so a series' sums do not depend on how many blocks or series a launch
+// has.  Series s of a launch owns the partial rows red_row0(rec_off, s) .. (3
+// doubles each); a launch of S series over `points` records needs
+// red_rows(points, S) rows.
+constexpr int kRedChunk = 2048;
+__host__ __device__ inline int64_t red_row0(int64_t rec_off, int s) { return rec_off / kRedChunk + s; }
+__host__ __device__ inline int64_t red_rows(int64_t points, int64_t S) { return points / kRedChunk + S + 1; }
+
 struct Stats {            // FP64 reductions, in device memory
     double W;             // sum of w_j
     double WY;            // sum of w_j y_j
@@ -126,7 +136,7 @@ struct Workspace {
     int *binstart;        // 2 * (nbins + 1), per series
     int *chist;           // chunk histograms, then their prefixes over chunks:
                           // rows of 2 * nbins (chunk_row0, chunk_hist_entries)
-    double *partials;     // reduction partials
+    double *partials;     // reduction partials: 3 doubles per row (red_rows)
     unsigned int *counter;// last-block tickets (2)
     Stats *stats;
     int *status;          // device status word
@@ -223,6 +233,11 @@ cudaError_t launch_deconv_slot(const Geometry &g, void *out, const void *compact
 
 // Self-test: the FP64 path's double-float kernel evaluation and the FP64 one
 // at n points of [-1, 1] (device buffers of n doubles each).
+// Self-test: the FP32 path's integer-pipe double assembly against the FP64
+// conversions and add on n generated pairs; *bad (device) counts mismatches.
+cudaError_t launch_ff_assembly_check(long long n, unsigned long long seed, unsigned long long *bad,
+                                     cudaStream_t st);
+
 cudaError_t launch_kernel_eval_pair(int n, double beta, double *dfl_out, double *fp64_out,
                                     cudaStream_t st);
 

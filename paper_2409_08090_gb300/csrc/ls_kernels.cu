@@ -140,35 +140,39 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
     y += sd.y_off;
     if (dy) dy += sd.pt_off;
     const int64_t nd = sd.nd;
-    partials += (size_t)ser * 3 * gridDim.x;
+    const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
+    partials += 3 * red_row0(sd.rec_off, ser);
     counter += 2 * ser;
     st += ser;
     __shared__ double sh[32];
-    double sw = 0.0, swy = 0.0, swy2 = 0.0;
     bool ok = true;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double d = dy ? dy[j] : 1.0;
-        const double yj = y[j];
-        ok &= finite_bits(d) && finite_bits(yj) && finite_bits(t[j]) && __double_as_longlong(d) > 0;
-        const double w = rcp_fp64(d * d);
-        const double wy = w * yj;
-        sw += w;
-        swy += wy;
-        swy2 = fma(wy, yj, swy2);
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        double sw = 0.0, swy = 0.0, swy2 = 0.0;
+        const int64_t j1 = min(nd, (c + 1) * kRedChunk);
+        for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
+            const double d = dy ? dy[j] : 1.0;
+            const double yj = y[j];
+            ok &= finite_bits(d) && finite_bits(yj) && finite_bits(t[j]) &&
+                  __double_as_longlong(d) > 0;
+            const double w = rcp_fp64(d * d);
+            const double wy = w * yj;
+            sw += w;
+            swy += wy;
+            swy2 = fma(wy, yj, swy2);
+        }
+        const double a = block_sum(sw, sh);
+        const double b = block_sum(swy, sh);
+        const double q = block_sum(swy2, sh);
+        if (threadIdx.x == 0) {
+            partials[3 * c] = a;
+            partials[3 * c + 1] = b;
+            partials[3 * c + 2] = q;
+        }
     }
     if (!ok) atomicOr(status, kStatBadInput);
-    double a = block_sum(sw, sh);
-    double b = block_sum(swy, sh);
-    double c = block_sum(swy2, sh);
-    if (threadIdx.x == 0) {
-        partials[3 * blockIdx.x] = a;
-        partials[3 * blockIdx.x + 1] = b;
-        partials[3 * blockIdx.x + 2] = c;
-    }
     if (last_block(counter)) {
         double r[3];
-        reduce_partials(partials, gridDim.x, 3, r, sh);
+        reduce_partials(partials, (int)nch, 3, r, sh);
         if (threadIdx.x == 0) {
             const double W = r[0], WY = r[1], WY2 = r[2];
             st->W = W;
@@ -321,46 +325,55 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
     const PhaseArgs ph = sd.ph;
     px = shifted(px, sd.rec_off);
     p2 = shifted(p2, sd.rec_off);
-    partials += (size_t)ser * 3 * gridDim.x;
+    const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
+    partials += 3 * red_row0(sd.rec_off, ser);
     counter += 2 * ser + 1;
     st += ser;
     __shared__ double sh[32];
     const double invW = st->invW;
     const double ybar = st->ybar;
     const double scale = st->scale;
-    double syy = 0.0, sy2 = 0.0;
     unsigned m1 = 0u, m2 = 0u, m3 = 0u;   // strength bounds (bits), this thread's records
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double tj = t[j], yj = y[j];
-        const double d = dy ? dy[j] : 1.0;
-        const double wh = rcp_fp64(d * d) * invW;
-        const double yc = yj - ybar;
-        const double wyc = wh * yc;
-        syy = fma(wyc, yc, syy);
-        sy2 = fma(wh * yj, yj, sy2);
-        const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);          // frac(df t)
-        const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj)
-                      + (u128)(uint64_t)ph.K0 * Fx;                   // frac(fc t)
-        uint32_t ab1, ab2;
-        T r1, r2;
-        split_fixed<T>(Fx, g, ab1, r1);
-        split_fixed<T>(Fx << 1, g, ab2, r2);
-        const Cplx<T> p = Cis<T>::of(Fc);
-        const Cplx<T> q = Cis<T>::of(Fc << 1);
-        const T at = (T)(wyc * scale), wt = (T)wh;
-        const Cplx<T> s1 = mk2(at * p.x, at * p.y), s2 = mk2(wt * p.x, wt * p.y),
-                      s3 = mk2(wt * q.x, wt * q.y);
-        px.ab[j] = ab1;
-        px.roff[j] = r1;
-        px.s[0][j] = s1;
-        px.s[1][j] = s2;
-        p2.ab[j] = ab2;
-        p2.roff[j] = r2;
-        p2.s[0][j] = s3;
-        m1 = max(m1, strength_bound_bits(s1));
-        m2 = max(m2, strength_bound_bits(s2));
-        m3 = max(m3, strength_bound_bits(s3));
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        double syy = 0.0, sy2 = 0.0;
+        const int64_t j1 = min(nd, (c + 1) * kRedChunk);
+        for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
+            const double tj = t[j], yj = y[j];
+            const double d = dy ? dy[j] : 1.0;
+            const double wh = rcp_fp64(d * d) * invW;
+            const double yc = yj - ybar;
+            const double wyc = wh * yc;
+            syy = fma(wyc, yc, syy);
+            sy2 = fma(wh * yj, yj, sy2);
+            const u128 Fx = frac_fixed(ph.df_m, ph.df_e, 0, tj);          // frac(df t)
+            const u128 Fc = frac_fixed(ph.f0_m, ph.f0_e, ph.f0_neg, tj)
+                          + (u128)(uint64_t)ph.K0 * Fx;                   // frac(fc t)
+            uint32_t ab1, ab2;
+            T r1, r2;
+            split_fixed<T>(Fx, g, ab1, r1);
+            split_fixed<T>(Fx << 1, g, ab2, r2);
+            const Cplx<T> p = Cis<T>::of(Fc);
+            const Cplx<T> q = Cis<T>::of(Fc << 1);
+            const T at = (T)(wyc * scale), wt = (T)wh;
+            const Cplx<T> s1 = mk2(at * p.x, at * p.y), s2 = mk2(wt * p.x, wt * p.y),
+                          s3 = mk2(wt * q.x, wt * q.y);
+            px.ab[j] = ab1;
+            px.roff[j] = r1;
+            px.s[0][j] = s1;
+            px.s[1][j] = s2;
+            p2.ab[j] = ab2;
+            p2.roff[j] = r2;
+            p2.s[0][j] = s3;
+            m1 = max(m1, strength_bound_bits(s1));
+            m2 = max(m2, strength_bound_bits(s2));
+            m3 = max(m3, strength_bound_bits(s3));
+        }
+        const double a = block_sum(syy, sh);
+        const double b = block_sum(sy2, sh);
+        if (threadIdx.x == 0) {
+            partials[2 * c] = a;
+            partials[2 * c + 1] = b;
+        }
     }
     {
         m1 = __reduce_max_sync(0xffffffffu, m1);
@@ -372,15 +385,9 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
             atomicMax(&st->smax[2], m3);
         }
     }
-    double a = block_sum(syy, sh);
-    double b = block_sum(sy2, sh);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = b;
-    }
     if (last_block(counter)) {
         double r[2];
-        reduce_partials(partials, gridDim.x, 2, r, sh);
+        reduce_partials(partials, (int)nch, 2, r, sh);
         if (threadIdx.x == 0) {
             const double YY = r[0], Y2 = r[1];
             st->YY = YY * st->scale * st->scale;
@@ -1414,22 +1421,25 @@ __global__ void k_sh_weights(const double *__restrict__ t, const double *__restr
                              Stats *stc, int *status)
 {
     __shared__ double sh[32];
-    double sw = 0.0;
+    const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
     bool ok = true;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double d = dy ? dy[j] : 1.0;
-        ok &= finite_bits(d) && finite_bits(t[j]) && __double_as_longlong(d) > 0;
-        const double w = rcp_fp64(d * d);
-        wts[j] = w;
-        sw += w;
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        double sw = 0.0;
+        const int64_t j1 = min(nd, (c + 1) * kRedChunk);
+        for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
+            const double d = dy ? dy[j] : 1.0;
+            ok &= finite_bits(d) && finite_bits(t[j]) && __double_as_longlong(d) > 0;
+            const double w = rcp_fp64(d * d);
+            wts[j] = w;
+            sw += w;
+        }
+        const double a = block_sum(sw, sh);
+        if (threadIdx.x == 0) partials[c] = a;
     }
     if (!ok) atomicOr(status, kStatBadInput);
-    const double a = block_sum(sw, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = a;
     if (last_block(counter)) {
         double r[1];
-        reduce_partials(partials, gridDim.x, 1, r, sh);
+        reduce_partials(partials, (int)nch, 1, r, sh);
         if (threadIdx.x == 0) {
             stc->W = r[0];
             stc->invW = 1.0 / r[0];
@@ -1490,30 +1500,33 @@ __global__ void k_sh_stats(const double *__restrict__ y, Batch bt, const double 
     const SeriesDesc sd = series_of(bt, ser);
     y += sd.y_off;
     const int64_t nd = sd.nd;
-    partials += (size_t)ser * 3 * gridDim.x;
+    const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
+    partials += 3 * red_row0(sd.rec_off, ser);
     counter += 2 * ser;
     st += ser;
     __shared__ double sh[32];
-    double swy = 0.0, swy2 = 0.0;
     bool ok = true;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double yj = y[j];
-        ok &= finite_bits(yj);
-        const double wy = wts[j] * yj;
-        swy += wy;
-        swy2 = fma(wy, yj, swy2);
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        double swy = 0.0, swy2 = 0.0;
+        const int64_t j1 = min(nd, (c + 1) * kRedChunk);
+        for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
+            const double yj = y[j];
+            ok &= finite_bits(yj);
+            const double wy = wts[j] * yj;
+            swy += wy;
+            swy2 = fma(wy, yj, swy2);
+        }
+        const double b = block_sum(swy, sh);
+        const double q = block_sum(swy2, sh);
+        if (threadIdx.x == 0) {
+            partials[2 * c] = b;
+            partials[2 * c + 1] = q;
+        }
     }
     if (!ok) atomicOr(status, kStatBadInput);
-    const double b = block_sum(swy, sh);
-    const double c = block_sum(swy2, sh);
-    if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = b;
-        partials[2 * blockIdx.x + 1] = c;
-    }
     if (last_block(counter)) {
         double r[2];
-        reduce_partials(partials, gridDim.x, 2, r, sh);
+        reduce_partials(partials, (int)nch, 2, r, sh);
         if (threadIdx.x == 0) {
             const double W = stc->W, WY = r[0], WY2 = r[1];
             st->W = W;
@@ -1545,29 +1558,32 @@ __global__ void k_sh_series(const double *__restrict__ y, Batch bt, const double
     y += sd.y_off;
     const int64_t nd = sd.nd;
     cvals += (size_t)ser * (size_t)nd;
-    partials += (size_t)ser * 3 * gridDim.x;
+    const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
+    partials += 3 * red_row0(sd.rec_off, ser);
     counter += 2 * ser + 1;
     st += ser;
     __shared__ double sh[32];
     const double ybar = st->ybar, scale = st->scale;
-    double syy = 0.0;
     unsigned m1 = 0u;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nd;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const double yc = y[j] - ybar;
-        syy = fma(wts[j] * yc, yc, syy);
-        const T c = (T)(scale * (y[perm[j]] - ybar));   // j as a sorted index here
-        cvals[j] = c;
-        const Cplx<T> s2 = s2sorted[j];
-        m1 = max(m1, strength_bound_bits(mk2(c * s2.x, c * s2.y)));
+    for (int64_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        double syy = 0.0;
+        const int64_t j1 = min(nd, (c + 1) * kRedChunk);
+        for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
+            const double yc = y[j] - ybar;
+            syy = fma(wts[j] * yc, yc, syy);
+            const T cj = (T)(scale * (y[perm[j]] - ybar));   // j as a sorted index here
+            cvals[j] = cj;
+            const Cplx<T> s2 = s2sorted[j];
+            m1 = max(m1, strength_bound_bits(mk2(cj * s2.x, cj * s2.y)));
+        }
+        const double a = block_sum(syy, sh);
+        if (threadIdx.x == 0) partials[c] = a;
     }
     m1 = __reduce_max_sync(0xffffffffu, m1);
     if ((threadIdx.x & 31) == 0) atomicMax(&st->smax[0], m1);
-    const double a = block_sum(syy, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = a;
     if (last_block(counter)) {
         double r[1];
-        reduce_partials(partials, gridDim.x, 1, r, sh);
+        reduce_partials(partials, (int)nch, 1, r, sh);
         if (threadIdx.x == 0) {
             const double YY = r[0] * st->invW, Y2 = st->WY2 * st->invW;
             st->YY = YY * scale * scale;
@@ -3028,6 +3044,61 @@ template cudaError_t launch_shared_pipeline<double>(const Geometry &, const Work
                                                     const Batch &, int64_t, const double *,
                                                     const double *, const double *, double *, int,
                                                     cudaStream_t, int);
+// Self-test support: ff_to_double against the FP64 conversions and add on n
+// pairs (hi, lo), lo within half an ulp of hi, drawn from a counter-based
+// generator (splitmix64 of seed + i): general values over every exponent and
+// both signs, powers of two (the binade-crossing branch), exponents next to
+// the fast path's lower bound, ties at the double's rounding position, zero,
+// subnormal and non-finite hi.  Counts the pairs whose bits differ.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__global__ void k_ff_assembly_check(long long n, unsigned long long seed, unsigned long long *bad)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long r = splitmix64(seed + (unsigned long long)i);
+        const unsigned long long r2 = splitmix64(r);
+        const unsigned sign = (unsigned)(r >> 63) << 31;
+        unsigned e = 1u + (unsigned)((r >> 40) % 254u);          // biased exponent of hi
+        unsigned mant = (unsigned)(r & 0x7FFFFFu);
+        const int kind = (int)(i & 7);
+        if (kind == 5) mant = 0u;                                    // a power of two
+        if (kind == 6) e = 49u + (unsigned)((r >> 40) % 8u);         // around 2^-75
+        if (kind == 4 && (r2 & 3u) == 0u) e = (r2 & 4u) ? 255u : 0u; // non-finite / zero, subnormal
+        const float hi = __uint_as_float(sign | (e << 23) | mant);
+        float lo;
+        if (kind == 7 && e >= 80u && e < 255u) {
+            // (k + 1/2) units of the double's ulp 2^(e - 179): a tie, |k| < 2^22
+            const int k = (int)((r2 >> 8) & 0x3FFFFFu) - (1 << 21);
+            lo = ((float)k + 0.5f) * __uint_as_float((e - 52u) << 23);
+        } else {
+            // u in [-1, 1) times ulp(hi) / 2 = 2^(e - 151) (exact scaling)
+            const float u = (float)(int)(r2 >> 40) * 0x1p-23f - 1.0f;
+            const float half_ulp = e >= 25u ? __uint_as_float((e - 24u) << 23)   // 2^(e - 151)
+                                            : ldexpf(1.0f, (int)e - 151);
+            lo = (e == 0u || e == 255u) ? u * 0x1p-149f : u * half_ulp;
+        }
+        const double a = ff_to_double(ff{hi, lo});
+        const double b = (double)hi + (double)lo;
+        if (__double_as_longlong(a) != __double_as_longlong(b) && !(a != a && b != b))
+            atomicAdd(bad, 1ull);
+    }
+}
+
+cudaError_t launch_ff_assembly_check(long long n, unsigned long long seed, unsigned long long *bad,
+                                     cudaStream_t st)
+{
+    int nb = (int)((n + 255) / 256);
+    if (nb > 4096) nb = 4096;
+    k_ff_assembly_check<<<nb, 256, 0, st>>>(n, seed, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kernel_eval_pair(int n, double beta, double *dfl_out, double *fp64_out,
                                     cudaStream_t st)
 {

@@ -137,7 +137,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     Carver c;
     const size_t o_counter = c.take(256);
     const size_t o_stats = c.take(sizeof(Stats));
-    const size_t o_partials = c.take(sizeof(double) * 3 * (size_t)nred);
+    const size_t o_partials = c.take(sizeof(double) * 3 * (size_t)red_rows(nd, 1));
     const size_t o_hist = c.take(sizeof(int) * 2 * (size_t)g.nbins);
     const size_t o_binstart = c.take(sizeof(int) * 2 * ((size_t)g.nbins + 1));
     const size_t o_chist = c.take(sizeof(int) * (size_t)chunk_hist_entries(nd, 1, g.nbins));

@@ -162,3 +162,43 @@ def test_shared_times_batch_matches_replicated_batch(nl, oracle_mod, prec, eps):
             assert np.max(np.abs(Pshared[i] - P_o)) <= 1e-9
         else:
             assert np.linalg.norm(Pshared[i] - P_o) / np.linalg.norm(P_o) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-9)])
+def test_series_same_bits_alone_and_in_a_wide_batch(nl, prec, eps):
+    # 300 series share one launch, so each gets few reduction blocks, against
+    # many alone: the FP64 sums go per fixed chunk of points, so the launch
+    # shape cannot change a series' bits
+    rng = np.random.default_rng(17)
+    series = []
+    for i in range(300):
+        nd = int(rng.integers(1500, 6000))
+        t = np.sort(rng.uniform(0.0, 500.0, nd))
+        y = np.sin(2 * np.pi * t / rng.uniform(0.5, 50.0)) + rng.normal(0.0, 1.0, nd)
+        dy = rng.uniform(0.5, 2.0, nd)
+        series.append(W.Series(t, y, dy, 1e-3, 1e-3, 3000 + 7 * i))
+    got = _run_batch(nl, series, eps, prec)
+    for i in (0, 149, 299):
+        assert_identical(got[i], _run_single(nl, series[i], eps, prec), i)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-9)])
+def test_shared_times_series_same_bits_alone_and_in_the_batch(nl, prec, eps):
+    # a series of a shared-times batch gives the same bits in a shared-times
+    # batch of its own and when the batch is cut into several launches: the
+    # common transforms are recomputed identically and each series keeps its
+    # own fixed-point grids whatever the grouping
+    import torch
+    t, Y, dy, f0, df, nf = W.uniform_batch(seed=12, nseries=24, nd=1200, nf=7000)
+    dev = torch.device("cuda:0")
+    tt, yy, dd = (torch.tensor(a, device=dev) for a in (t, Y, dy))
+    plan = nl.Plan(2, 1, eps, prec)
+    P = plan.execute_shared(tt, yy, dd, f0, df, nf).cpu().numpy()
+    small = nl.Plan(2, 1, eps, prec, batch_workspace_bytes=3_000_000)
+    Psplit = small.execute_shared(tt, yy, dd, f0, df, nf).cpu().numpy()
+    for i in (0, 11, 23):
+        Pi = plan.execute_shared(tt, yy[i:i + 1].contiguous(), dd, f0, df, nf).cpu().numpy()[0]
+        assert_identical(P[i], Pi, i)
+    plan.close()
+    small.close()
+    assert_identical(P, Psplit)

@@ -224,3 +224,13 @@ def test_log_normalisation_keeps_relative_accuracy_at_small_power(nl, oracle_mod
     assert float(np.max(rel_log)) <= bound, (float(np.max(rel_log)), bound)
     if prec == "fp64":
         assert float(np.max(rel_log)) <= 1e-5
+
+
+def test_double_assembly_matches_fp64_add(nl):
+    # the FP32 path writes its double-float power as a double assembled on the
+    # integer pipe: bit for bit the FP64 conversions and add, on 2^24 generated
+    # pairs including powers of two, ties and non-finite values
+    import ctypes
+    bad = ctypes.c_int64(-1)
+    st = nl._lib.ls_selftest_double_assembly(1 << 24, 20240914, 0, ctypes.byref(bad))
+    assert st == 0 and bad.value == 0, (st, bad.value)
