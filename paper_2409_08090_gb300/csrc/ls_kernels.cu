@@ -1985,11 +1985,17 @@ __device__ __forceinline__ ff ff_div(ff x, ff y)
 // in hi's binade except where hi is a power of two and lo points towards zero,
 // and for hi zero, subnormal, non-finite or below 2^-75: those take the FP64
 // conversions and add, which give the same value.
+// The rare operands' FP64 conversions and add, out of line so that the common
+// path does not issue them predicated.
+__device__ __noinline__ double ff_to_double_fp64(float hi, float lo)
+{
+    return (double)hi + (double)lo;
+}
 __device__ __forceinline__ double ff_to_double(ff p)
 {
     const unsigned hb = __float_as_uint(p.hi);
     const unsigned e = (hb >> 23) & 0xffu;
-    if (e < 52u || e == 255u || (hb & 0x7fffffu) == 0u) return (double)p.hi + (double)p.lo;
+    if (e < 52u || e == 255u || (hb & 0x7fffffu) == 0u) return ff_to_double_fp64(p.hi, p.lo);
     const float units = __uint_as_float((306u - e) << 23);          // 2^(52 - (e - 127))
     int r = __float2int_rn(p.lo * units);
     if (hb >> 31) r = -r;
