@@ -126,6 +126,12 @@ struct Stats {            // FP64 reductions, in device memory
     double Y2;            // sum of w^_j y_j^2 (scale for the degeneracy test)
     unsigned smax[3];     // per transform (s1, s2, s3): bits of an FP32 upper bound of the
                           // largest strength component magnitude (the FP64 spread's grid)
+    // set with YY, for pass B: the psd factor W YY / (2 scale^2), 1 / scale, and
+    // YY as a double-float pair (one evaluation per series instead of one FP64
+    // division per thread of every pass-B block)
+    double psd;
+    double unscale;
+    float yy_hi, yy_lo;
 };
 
 struct Workspace {

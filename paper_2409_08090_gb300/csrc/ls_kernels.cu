@@ -189,6 +189,16 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
     }
 }
 
+// The pass-B scalars of a series, once YY (scaled) is known.
+__device__ __forceinline__ void finish_series_stats(Stats *st)
+{
+    const double YY = st->YY;
+    st->psd = 0.5 * st->W * YY / (st->scale * st->scale);
+    st->unscale = 1.0 / st->scale;
+    st->yy_hi = (float)YY;
+    st->yy_lo = (float)(YY - (double)st->yy_hi);
+}
+
 // ---------------------------------------------------------------------------
 // Exact phase reduction in integer arithmetic.  A double f = +-m 2^e (m < 2^53)
 // times a double t is the 106-bit integer product of the mantissas times a
@@ -392,6 +402,7 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
             const double YY = r[0], Y2 = r[1];
             st->YY = YY * st->scale * st->scale;
             st->Y2 = Y2;
+            finish_series_stats(st);
             // A constant series: variance zero up to the rounding of the mean.
             if (!(YY > 1e-24 * Y2)) atomicOr(status, kStatDegenerate);
             *counter = 0u;
@@ -589,6 +600,18 @@ __global__ void k_scatter(Batch bt, Geometry g, PointSet<T> rx, PointSet<T> r2,
         s2.s[0][d2] = r2.s[0][j];
         if (perm) perm[d1] = (int)j;      // shared-times batches: sorted -> input index
     }
+}
+
+// Integer division and remainder of non-negative 64-bit values by 32-bit
+// divisors through the 32-bit unit when the operands fit (a 64-bit division
+// is a long instruction sequence; these run in every thread of a block).
+__device__ __forceinline__ int div_u32(int64_t num, int den)
+{
+    return num < 0x100000000ll ? (int)((uint32_t)num / (uint32_t)den) : (int)(num / den);
+}
+__device__ __forceinline__ int64_t mod_u32(int64_t p, int64_t n)
+{
+    return (p < 0x100000000ll && n < 0x100000000ll) ? (int64_t)((uint32_t)p % (uint32_t)n) : p % n;
 }
 
 // exp(2 pi i p / n) from the two-level four-step table, p in [0, n).
@@ -893,7 +916,7 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
             const int col = i / nhi;
             const int dh = i - col * nhi;
-            ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a_base + col) * 64 * dh) % g.n));
+            ahi[i] = to_fft(tw4_root(A.tw4, mod_u32((int64_t)(a_base + col) * 64 * dh, g.n)));
         }
     }
     __syncthreads();
@@ -1171,7 +1194,7 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
         alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a0 + (i >> 6)) * (i & 63)));
     for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
         const int col = i / nhi;
-        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * (i - col * nhi)) % g.n));
+        ahi[i] = to_fft(tw4_root(A.tw4, mod_u32((int64_t)(a0 + col) * 64 * (i - col * nhi), g.n)));
     }
     const T halfw = T(0.5) * T(g.w);
     const T zscale = T(2) / T(g.w);
@@ -1588,6 +1611,7 @@ __global__ void k_sh_series(const double *__restrict__ y, Batch bt, const double
             const double YY = r[0] * st->invW, Y2 = st->WY2 * st->invW;
             st->YY = YY * scale * scale;
             st->Y2 = Y2;
+            finish_series_stats(st);
             // A constant series: variance zero up to the rounding of the mean.
             if (!(YY > 1e-24 * Y2)) atomicOr(status, kStatDegenerate);
             *counter = 0u;
@@ -1632,7 +1656,7 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassA
         alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a0 + (i >> 6)) * (i & 63)));
     for (int i = threadIdx.x; i < BA * nhi; i += blockDim.x) {
         const int col = i / nhi;
-        ahi[i] = to_fft(tw4_root(A.tw4, ((int64_t)(a0 + col) * 64 * (i - col * nhi)) % g.n));
+        ahi[i] = to_fft(tw4_root(A.tw4, mod_u32((int64_t)(a0 + col) * 64 * (i - col * nhi), g.n)));
     }
     const T halfw = T(0.5) * T(g.w);
     const T zscale = T(2) / T(g.w);
@@ -2076,8 +2100,11 @@ struct PassBArgs {
 // The FP32 path's log keeps FP32 relative accuracy over the whole range
 // without an FP64 logarithm: log1p(-P) for P < 1/2 (no cancellation in 1 - P
 // for small P), and the log of 1 - P, formed exactly in FP64, above.
+// The model, log and psd forms out of line (with them inline, the standard
+// form's hot loop issued their FP64 work predicated: pass B of the 1.9e7-cell
+// grid 0.449 against 0.422 ms).
 template <typename T>
-__device__ __forceinline__ double ls_normalise(double P, int norm, double psd_factor)
+__device__ __noinline__ double ls_normalise_other(double P, int norm, double psd_factor)
 {
     switch (norm) {
     case 1: return P * rcp_fp64(1.0 - P);
@@ -2088,6 +2115,11 @@ __device__ __forceinline__ double ls_normalise(double P, int norm, double psd_fa
     case 3: return P * psd_factor;
     default: return P;
     }
+}
+template <typename T>
+__device__ __forceinline__ double ls_normalise(double P, int norm, double psd_factor)
+{
+    return norm == 0 ? P : ls_normalise_other<T>(P, norm, psd_factor);
 }
 
 // Asynchronous global -> shared copies of one complex element (sm_80+):
@@ -2179,8 +2211,8 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
     cp_async_commit();
     // per-series scalars, loaded while the copies run
     const double YY = stat->YY;
-    const double psd_factor = 0.5 * stat->W * YY / (stat->scale * stat->scale);
-    const double unscale = 1.0 / stat->scale;
+    const double psd_factor = stat->psd;
+    const double unscale = stat->unscale;
     cp_async_wait_all();
     __syncthreads();
 
@@ -2214,13 +2246,13 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
 
     const T lam_tol_t = (T)B.lam_tol;
     ff YYf;
-    YYf.hi = (float)YY;
-    YYf.lo = (float)(YY - (double)YYf.hi);
+    YYf.hi = stat->yy_hi;
+    YYf.lo = stat->yy_lo;
     const int64_t n = g.n;
     const int64_t hi_start = n - K0;       // k >= hi_start -> k' = k - n < 0
     const int64_t lo_end = nf - K0;        // k <  lo_end   -> k' = k >= 0
-    const int c1 = (lo_end > d) ? (int)((lo_end - d + N2 - 1) / N2) : 0;
-    const int c2 = (int)((hi_start - d + N2 - 1) / N2);
+    const int c1 = (lo_end > d) ? div_u32(lo_end - d + N2 - 1, N2) : 0;
+    const int c2 = div_u32(hi_start - d + N2 - 1, N2);
     // kDc deconvolution factors per thread are loaded (coalesced, pass-B order)
     // before any is used, so their latency is paid once per group.
     constexpr int kDc = 4;
@@ -2295,8 +2327,8 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
     const SeriesDesc sd0 = series_of(B.bt, 0);
     const int64_t nf = sd0.nf, K0 = sd0.ph.K0;
     const int64_t n = g.n;
-    const int c1 = (nf - K0 > d) ? (int)((nf - K0 - d + N2 - 1) / N2) : 0;
-    const int c2 = (int)((n - K0 - d + N2 - 1) / N2);
+    const int c1 = (nf - K0 > d) ? div_u32(nf - K0 - d + N2 - 1, N2) : 0;
+    const int c2 = div_u32(n - K0 - d + N2 - 1, N2);
     const T lam_tol_t = (T)B.lam_tol;
     const T *dcrow = B.deconv + (size_t)d * N1;
 
@@ -2314,10 +2346,9 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
             const Stats *stat = B.st + s0 + r;
             const double YY = stat->YY;
             sc[4 * r] = YY;
-            sc[4 * r + 1] = 0.5 * stat->W * YY / (stat->scale * stat->scale);
-            const float hi = (float)YY;
-            sc[4 * r + 2] = hi;
-            sc[4 * r + 3] = (float)(YY - (double)hi);
+            sc[4 * r + 1] = stat->psd;
+            sc[4 * r + 2] = stat->yy_hi;
+            sc[4 * r + 3] = stat->yy_lo;
             soff[r] = series_of(B.bt, s0 + r).out_off;
         }
         cp_async_wait_all();
@@ -2410,10 +2441,9 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
             const Stats *stat = B.st + s0 + r;
             const double YY = stat->YY;
             sc[4 * r] = YY;
-            sc[4 * r + 1] = 0.5 * stat->W * YY / (stat->scale * stat->scale);
-            const float hi = (float)YY;
-            sc[4 * r + 2] = hi;
-            sc[4 * r + 3] = (float)(YY - (double)hi);
+            sc[4 * r + 1] = stat->psd;
+            sc[4 * r + 2] = stat->yy_hi;
+            sc[4 * r + 3] = stat->yy_lo;
             const int64_t nf = sd.nf, K0 = sd.ph.K0;
             cr[2 * r] = (nf - K0 > d) ? (int)((nf - K0 - d + N2 - 1) / N2) : 0;
             cr[2 * r + 1] = (int)((n - K0 - d + N2 - 1) / N2);
