@@ -71,9 +71,37 @@ template <> struct FftOf<double> { using type = dfl2; };
 __device__ __forceinline__ float2 to_fft(float2 v) { return v; }
 __device__ __forceinline__ dfl2 to_fft(double2 v) { return mk2(dfl(v.x), dfl(v.y)); }
 __device__ __forceinline__ float2 from_fft(float2 v) { return v; }
+// hi + lo rounded to the nearest double, from the bit patterns on the integer
+// pipe (for |lo| <= ulp(hi) / 2, as double-float values are kept; others take
+// the FP64 path below):
+// hi widens exactly (exponent rebiased, mantissa shifted up 29 bits) and lo,
+// in units of that double's ulp 2^(e - 52) (e the unbiased exponent of hi,
+// |lo| <= 2^28 units), is rounded to an integer (ties to even, the rounding of
+// the FP64 add) and added to the bits.  The sum stays in hi's binade except
+// where hi is a power of two and lo points towards zero, and for hi zero,
+// subnormal, non-finite or below 2^-75: those take the FP64 conversions and
+// add (same value), out of line so that the common path does not issue them
+// predicated.  This part converts and adds FP64 at 1/64 of the FP32 rate.
+__device__ __noinline__ double hl_to_double_fp64(float hi, float lo)
+{
+    return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double hl_to_double(float hi, float lo)
+{
+    const unsigned hb = __float_as_uint(hi);
+    const unsigned e = (hb >> 23) & 0xffu;
+    if (e < 52u || e == 255u || (hb & 0x7fffffu) == 0u) return hl_to_double_fp64(hi, lo);
+    const float units = __uint_as_float((306u - e) << 23);          // 2^(52 - (e - 127))
+    int r = __float2int_rn(lo * units);
+    if (r > (1 << 28) || r < -(1 << 28)) return hl_to_double_fp64(hi, lo);   // |lo| > ulp(hi)/2
+    if (hb >> 31) r = -r;
+    const unsigned long long mag = ((unsigned long long)(hb & 0x7fffffffu) + (896ull << 23)) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)(hb >> 31) << 63) |
+                                            (mag + (unsigned long long)(long long)r)));
+}
 __device__ __forceinline__ double2 from_fft(dfl2 v)
 {
-    return make_double2((double)v.x.hi + (double)v.x.lo, (double)v.y.hi + (double)v.y.lo);
+    return make_double2(hl_to_double(v.x.hi, v.x.lo), hl_to_double(v.y.hi, v.y.lo));
 }
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk2(a.x + b.x, a.y + b.y); }

@@ -642,7 +642,6 @@ template <> struct Fixed<float> {
     static constexpr int kBits = 30;
     __device__ static int of(float x) { return __float2int_rn(x); }
     __device__ static void add(int *a, int v) { atomicAdd(a, v); }
-    __device__ static float to(int v, float lsb) { return __int2float_rn(v) * lsb; }
 };
 template <> struct Fixed<double> {
     using I = long long;
@@ -652,8 +651,36 @@ template <> struct Fixed<double> {
     {
         atomicAdd(reinterpret_cast<unsigned long long *>(a), (unsigned long long)v);
     }
-    __device__ static double to(long long v, double lsb) { return __ll2double_rn(v) * lsb; }
 };
+
+// x 2^k for a float x, by the exponent bits where 2^k is a normal float.
+__device__ __forceinline__ float scale_pow2(float x, int k)
+{
+    return (k >= -126 && k <= 127) ? x * __int_as_float((k + 127) << 23) : ldexpf(x, k);
+}
+
+// The FP64 grid's cell v 2^(e - 62) as a double-float, on the integer and FP32
+// pipes (this part converts and multiplies FP64 at 1/64 of the FP32 rate): the
+// leading 24 bits of |v| and the next 24, rounded to nearest on the bit below
+// them, as two exactly scaled floats, renormalised.  Relative error below 2^-48,
+// the double-float's own precision.
+__device__ __forceinline__ dfl fixed_to_dfl(long long v, int e)
+{
+    if (v == 0) return dfl(0.0f, 0.0f);
+    const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)m);
+    const unsigned long long mn = m << lz;                   // leading bit at 63
+    const unsigned h = (unsigned)(mn >> 40);                 // [2^23, 2^24)
+    const unsigned l = (unsigned)((mn >> 16) & 0xFFFFFFull) + (unsigned)((mn >> 15) & 1ull);
+    float hi = scale_pow2((float)h, e - 22 - lz);            // h 2^40 2^(e - 62 - lz)
+    float lo = scale_pow2((float)l, e - 46 - lz);            // l 2^16 2^(e - 62 - lz)
+    if (v < 0) {
+        hi = -hi;
+        lo = -lo;
+    }
+    const float s = hi + lo;
+    return dfl(s, lo - (s - hi));
+}
 
 // Exponent e with 2^e above a nonnegative bound held as a float, read off its
 // bits (FP32 and integer operations only: this part issues FP64 at 1/64 of the
@@ -674,7 +701,8 @@ __device__ __forceinline__ signed char row_exponent(unsigned maxbits, unsigned c
     return exponent_above(__fmul_ru(__uint_as_float(maxbits), __uint2float_ru(count)));
 }
 
-// 2^(kBits - e) and 2^(e - kBits), built from the exponent bits.
+// 2^(kBits - e), built from the exponent bits (the units are converted back by
+// the FP32 path's first FFT stage and by fixed_to_dfl).
 __device__ __forceinline__ float fixed_scale(float, int e)
 {
     return __int_as_float((127 + Fixed<float>::kBits - e) << 23);
@@ -682,14 +710,6 @@ __device__ __forceinline__ float fixed_scale(float, int e)
 __device__ __forceinline__ double fixed_scale(double, int e)
 {
     return __longlong_as_double((long long)(1023 + Fixed<double>::kBits - e) << 52);
-}
-__device__ __forceinline__ float fixed_unit(float, int e)
-{
-    return __int_as_float((127 - Fixed<float>::kBits + e) << 23);
-}
-__device__ __forceinline__ double fixed_unit(double, int e)
-{
-    return __longlong_as_double((long long)(1023 - Fixed<double>::kBits + e) << 52);
 }
 
 // Exponent of the FP64 path's grid, one per block: every cell is a sum of at
@@ -1033,9 +1053,8 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         for (int col = 0; col < BA; ++col) {
             for (int b = threadIdx.x; b < N2; b += blockDim.x) {
                 const size_t i = (size_t)col * Lp + pad16(b);
-                const T unit = fixed_unit(T(0), rexp[b]);
-                bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
-                                     Fixed<T>::to(ibuf[2 * i + 1], unit)));
+                bufF[i] = mk2(fixed_to_dfl(ibuf[2 * i], rexp[b]),
+                              fixed_to_dfl(ibuf[2 * i + 1], rexp[b]));
             }
         }
         __syncthreads();
@@ -1387,9 +1406,8 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_group(Pa
                 const signed char *re = rexp + (c / BA) * N2;
                 for (int b = threadIdx.x; b < N2; b += blockDim.x) {
                     const size_t i = (size_t)c * Lp + pad16(b);
-                    const T unit = fixed_unit(T(0), re[b]);
-                    bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
-                                         Fixed<T>::to(ibuf[2 * i + 1], unit)));
+                    bufF[i] = mk2(fixed_to_dfl(ibuf[2 * i], re[b]),
+                                  fixed_to_dfl(ibuf[2 * i + 1], re[b]));
                 }
             }
             __syncthreads();
@@ -1816,9 +1834,8 @@ __global__ void __launch_bounds__(kThreadsA, kGroupBlocksPerSM) k_passA_sh(PassA
                 const signed char *re = rexp + (c / BA) * N2;
                 for (int b = threadIdx.x; b < N2; b += blockDim.x) {
                     const size_t i = (size_t)c * Lp + pad16(b);
-                    const T unit = fixed_unit(T(0), re[b]);
-                    bufF[i] = to_fft(mk2(Fixed<T>::to(ibuf[2 * i], unit),
-                                         Fixed<T>::to(ibuf[2 * i + 1], unit)));
+                    bufF[i] = mk2(fixed_to_dfl(ibuf[2 * i], re[b]),
+                                  fixed_to_dfl(ibuf[2 * i + 1], re[b]));
                 }
             }
             __syncthreads();
@@ -2001,32 +2018,8 @@ __device__ __forceinline__ ff ff_div(ff x, ff y)
     return fast_two_sum(q1, r * ry);
 }
 
-// hi + lo (|lo| <= ulp(hi) / 2) rounded to the nearest double, from the bit
-// patterns on the integer pipe: hi widens exactly (exponent rebiased, mantissa
-// shifted up 29 bits) and lo, in units of that double's ulp 2^(e - 52) (e the
-// unbiased exponent of hi, |lo| <= 2^28 units), is rounded to an integer (ties
-// to even, the rounding of the FP64 add) and added to the bits.  The sum stays
-// in hi's binade except where hi is a power of two and lo points towards zero,
-// and for hi zero, subnormal, non-finite or below 2^-75: those take the FP64
-// conversions and add, which give the same value.
-// The rare operands' FP64 conversions and add, out of line so that the common
-// path does not issue them predicated.
-__device__ __noinline__ double ff_to_double_fp64(float hi, float lo)
-{
-    return (double)hi + (double)lo;
-}
-__device__ __forceinline__ double ff_to_double(ff p)
-{
-    const unsigned hb = __float_as_uint(p.hi);
-    const unsigned e = (hb >> 23) & 0xffu;
-    if (e < 52u || e == 255u || (hb & 0x7fffffu) == 0u) return ff_to_double_fp64(p.hi, p.lo);
-    const float units = __uint_as_float((306u - e) << 23);          // 2^(52 - (e - 127))
-    int r = __float2int_rn(p.lo * units);
-    if (hb >> 31) r = -r;
-    const unsigned long long mag = ((unsigned long long)(hb & 0x7fffffffu) + (896ull << 23)) << 29;
-    return __longlong_as_double((long long)(((unsigned long long)(hb >> 31) << 63) |
-                                            (mag + (unsigned long long)(long long)r)));
-}
+// hi + lo rounded to the nearest double, on the integer pipe (hl_to_double).
+__device__ __forceinline__ double ff_to_double(ff p) { return hl_to_double(p.hi, p.lo); }
 
 // FP32 path: the sums arrive as FP32 values (exact inputs here); the ratio is
 // evaluated in double-float, whose rounding (~1e-13 of the terms' magnitudes)
