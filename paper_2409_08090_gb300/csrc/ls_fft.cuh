@@ -4,8 +4,8 @@
 // sign of the type-1 transform (Eq. 2), so Re g = C and Im g = S.
 //
 // Each transform runs in place as a decimation-in-frequency (Gentleman-Sande)
-// sequence of radix-R stages, R in {9, 3, 5} first and then {16, 8, 4, 2}, each
-// butterfly an R-point DFT in registers.  Every butterfly reads and writes the
+// sequence of radix-R stages, R in {18, 9, 3, 5} first and then {16, 8, 4, 2},
+// each butterfly an R-point DFT in registers.  Every butterfly reads and writes the
 // same R slots, so one buffer suffices and a stage needs only a barrier at its
 // end.  The output is left in digit-reversed order; slot_to_freq() gives the
 // frequency index each slot holds.  Twiddles exp(2 pi i j k / Ls) =
@@ -218,6 +218,41 @@ template <> struct Dft<9> {
             Dft<3>::run(b);
 #pragma unroll
             for (int k2 = 0; k2 < 3; ++k2) v[k1 + 3 * k2] = b[k2];
+        }
+    }
+};
+
+// 18 = 2 x 9: x index n = 9 n1 + n2, output k = k1 + 2 k2: radix-2 butterflies
+// over n1, the twiddles exp(+2 pi i n2 k1 / 18), two 9-point DFTs over n2 (one
+// stage where a radix-9 and a radix-2 stage would each read and write the
+// whole transform).
+template <> struct Dft<18> {
+    template <typename V> __device__ __forceinline__ static void run(V *v) {
+        using T = decltype(v[0].x);
+        const T c20 = T(0.93969262078590838405), s20 = T(0.34202014332566873304);
+        const T c40 = T(0.76604444311897803520), s40 = T(0.64278760968653932632);
+        const T c80 = T(0.17364817766693034885), s80 = T(0.98480775301220805936);
+        const T s60 = T(0.86602540378443864676);
+        V a[9], b[9];
+#pragma unroll
+        for (int n2 = 0; n2 < 9; ++n2) {
+            a[n2] = cadd(v[n2], v[n2 + 9]);
+            b[n2] = csub(v[n2], v[n2 + 9]);
+        }
+        b[1] = cmul(b[1], mk2(c20, s20));
+        b[2] = cmul(b[2], mk2(c40, s40));
+        b[3] = cmul(b[3], mk2(T(0.5), s60));
+        b[4] = cmul(b[4], mk2(c80, s80));
+        b[5] = cmul(b[5], mk2(-c80, s80));
+        b[6] = cmul(b[6], mk2(T(-0.5), s60));
+        b[7] = cmul(b[7], mk2(-c40, s40));
+        b[8] = cmul(b[8], mk2(-c20, s20));
+        Dft<9>::run(a);
+        Dft<9>::run(b);
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) {
+            v[2 * k2] = a[k2];
+            v[2 * k2 + 1] = b[k2];
         }
     }
 };
@@ -499,6 +534,7 @@ __device__ void fft_dif(V *buf, int ncol, int colstride, const FftPlan &fp, cons
     for (int s = first; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
+        case 18: dif_stage_cols<18, 1>(buf, ncol, colstride, st, roots, fp.L); break;
         case 16: dif_stage_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L); break;
         case 9: dif_stage_cols<9, NC>(buf, ncol, colstride, st, roots, fp.L); break;
         case 8: dif_stage_cols<8, NC>(buf, ncol, colstride, st, roots, fp.L); break;
@@ -520,6 +556,7 @@ __device__ void fft_dif_dealt(V *buf, int ncol, int colstride, const FftPlan &fp
     for (int s = 0; s < fp.nstages; ++s) {
         const FftStage &st = fp.st[s];
         switch (st.R) {
+        case 18: dif_stage_dealt<18>(buf, ncol, colstride, st, roots, fp.L); break;
         case 16: dif_stage_dealt<16>(buf, ncol, colstride, st, roots, fp.L); break;
         case 9: dif_stage_dealt<9>(buf, ncol, colstride, st, roots, fp.L); break;
         case 8: dif_stage_dealt<8>(buf, ncol, colstride, st, roots, fp.L); break;
@@ -541,6 +578,7 @@ __device__ void fft_dif_fixed(float2 *buf, int ncol, int colstride, const FftPla
 {
     const FftStage &st = fp.st[0];
     switch (st.R) {
+    case 18: first_stage_fixed_cols<18, 1>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
     case 16: first_stage_fixed_cols<16, NC16>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
     case 9: first_stage_fixed_cols<9, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
     case 8: first_stage_fixed_cols<8, NC>(buf, ncol, colstride, st, roots, fp.L, rexp, BA, rstride); break;
