@@ -83,6 +83,8 @@ LaunchCarve carve_launch(int64_t n, int nbins, size_t cx, size_t recb, int64_t S
     off = al(off + sizeof(int) * (size_t)chunk_hist_entries(points, (int)S, nbins));
     c.partials = off;
     off = al(off + sizeof(double) * 3 * (size_t)red_rows(points, S));
+    c.wts = off;
+    off = al(off + sizeof(double) * (size_t)points);
     c.bytes = off;
     return c;
 }
@@ -571,6 +573,8 @@ ls_status plan_workspace(ls_plan_s *p, bool tables_only)
     if ((s = plan_alloc(p, &v, sizeof(double) * 3 * (size_t)red_rows(p->max_nd, 1))) != LS_OK)
         return s;
     p->ws.partials = static_cast<double *>(v);
+    if ((s = plan_alloc(p, &v, sizeof(double) * (size_t)p->max_nd)) != LS_OK) return s;
+    p->ws.wts = static_cast<double *>(v);
     if ((s = plan_alloc(p, &v, 256)) != LS_OK) return s;
     p->ws.counter = static_cast<unsigned int *>(v);
     p->ws.status = reinterpret_cast<int *>(static_cast<char *>(v) + 64);
@@ -807,9 +811,9 @@ Workspace lane_workspace(const BatchWorkspace &b, const LaunchCarve &c, int *sta
     ws.hist = reinterpret_cast<int *>(a + c.hist);
     ws.binstart = reinterpret_cast<int *>(a + c.binstart);
     ws.chist = reinterpret_cast<int *>(a + c.chist);
+    ws.wts = reinterpret_cast<double *>(a + c.wts);
     if (c.perm) {
         ws.perm = reinterpret_cast<int *>(a + c.perm);
-        ws.wts = reinterpret_cast<double *>(a + c.wts);
         ws.cvals = a + c.cvals;
     }
     ws.partials = reinterpret_cast<double *>(a + c.partials);

@@ -124,15 +124,15 @@ __device__ void reduce_partials(const double *partials, int nparts, int width, d
 }
 
 // ---------------------------------------------------------------------------
-// K1a: weights and weighted mean (FP64).  W = sum 1/dy^2, WY = sum y/dy^2,
-// WY2 = sum y^2/dy^2.  The one-pass variance WY2/W - ybar^2 only sets the
-// scale of the strengths (the power does not depend on it); the exact YY
-// comes from the second pass.  Without centring (center = 0) ybar is taken as
+// K1a: weights and weighted mean (FP64).  w_j = 1/dy_j^2 (kept for k_points),
+// W = sum w_j, WY = sum w_j y_j, WY2 = sum w_j y_j^2.  The one-pass variance
+// WY2/W - ybar^2 only sets the scale of the strengths (the power does not
+// depend on it); the exact YY comes from the second pass.  Without centring (center = 0) ybar is taken as
 // 0 and the scale follows the mean square.
 // ---------------------------------------------------------------------------
 __global__ void k_stats(const double *__restrict__ t, const double *__restrict__ y,
                         const double *__restrict__ dy, Batch bt, double *partials,
-                        unsigned int *counter, Stats *st, int *status, int center)
+                        unsigned int *counter, Stats *st, int *status, int center, double *wts)
 {
     const int ser = blockIdx.y;
     const SeriesDesc sd = series_of(bt, ser);
@@ -141,6 +141,7 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
     if (dy) dy += sd.pt_off;
     const int64_t nd = sd.nd;
     const int64_t nch = (nd + kRedChunk - 1) / kRedChunk;
+    wts += sd.rec_off;                    // w_j at the series' records, for k_points
     partials += 3 * red_row0(sd.rec_off, ser);
     counter += 2 * ser;
     st += ser;
@@ -155,6 +156,7 @@ __global__ void k_stats(const double *__restrict__ t, const double *__restrict__
             ok &= finite_bits(d) && finite_bits(yj) && finite_bits(t[j]) &&
                   __double_as_longlong(d) > 0;
             const double w = rcp_fp64(d * d);
+            wts[j] = w;
             const double wy = w * yj;
             sw += w;
             swy += wy;
@@ -322,7 +324,7 @@ __device__ __forceinline__ unsigned strength_bound_bits(double2 s)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_points(const double *__restrict__ t, const double *__restrict__ y,
-                         const double *__restrict__ dy, Batch bt, Geometry g, PointSet<T> px,
+                         const double *__restrict__ wts, Batch bt, Geometry g, PointSet<T> px,
                          PointSet<T> p2, double *partials, unsigned int *counter, Stats *st,
                          int *status)
 {
@@ -330,7 +332,7 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
     const SeriesDesc sd = series_of(bt, ser);
     t += sd.pt_off;
     y += sd.y_off;
-    if (dy) dy += sd.pt_off;
+    wts += sd.rec_off;                    // w_j = 1/dy_j^2 from k_stats
     const int64_t nd = sd.nd;
     const PhaseArgs ph = sd.ph;
     px = shifted(px, sd.rec_off);
@@ -349,8 +351,7 @@ __global__ void k_points(const double *__restrict__ t, const double *__restrict_
         const int64_t j1 = min(nd, (c + 1) * kRedChunk);
         for (int64_t j = c * kRedChunk + threadIdx.x; j < j1; j += blockDim.x) {
             const double tj = t[j], yj = y[j];
-            const double d = dy ? dy[j] : 1.0;
-            const double wh = rcp_fp64(d * d) * invW;
+            const double wh = wts[j] * invW;
             const double yc = yj - ybar;
             const double wyc = wh * yc;
             syy = fma(wyc, yc, syy);
@@ -2667,8 +2668,8 @@ cudaError_t launch_pipeline(const Geometry &g, const Workspace &ws, int64_t capa
     if (nsm <= 0) nsm = 152;
     if (ev) cudaEventRecord(ev[0], st);
     k_stats<<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, ws.partials, ws.counter, ws.stats,
-                                           ws.status, center);
-    k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, dy, bt, g, rx, r2, ws.partials, ws.counter,
+                                           ws.status, center, ws.wts);
+    k_points<T><<<dim3(nred, S), 256, 0, st>>>(t, y, ws.wts, bt, g, rx, r2, ws.partials, ws.counter,
                                                ws.stats, ws.status);
     if (ev) cudaEventRecord(ev[1], st);
     // stable ranks and chunk histograms: at most one block per chunk of the

@@ -138,6 +138,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     const size_t o_counter = c.take(256);
     const size_t o_stats = c.take(sizeof(Stats));
     const size_t o_partials = c.take(sizeof(double) * 3 * (size_t)red_rows(nd, 1));
+    const size_t o_wts = c.take(sizeof(double) * (size_t)nd);
     const size_t o_hist = c.take(sizeof(int) * 2 * (size_t)g.nbins);
     const size_t o_binstart = c.take(sizeof(int) * 2 * ((size_t)g.nbins + 1));
     const size_t o_chist = c.take(sizeof(int) * (size_t)chunk_hist_entries(nd, 1, g.nbins));
@@ -159,6 +160,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     ws.status = reinterpret_cast<int *>(base + o_counter + 64);
     ws.stats = reinterpret_cast<Stats *>(base + o_stats);
     ws.partials = reinterpret_cast<double *>(base + o_partials);
+    ws.wts = reinterpret_cast<double *>(base + o_wts);
     ws.hist = reinterpret_cast<int *>(base + o_hist);
     ws.binstart = reinterpret_cast<int *>(base + o_binstart);
     ws.chist = reinterpret_cast<int *>(base + o_chist);
