@@ -155,7 +155,7 @@ ls_status run_noalloc(unsigned char *base, const double *t, const double *y, con
     const size_t o_quad = c.take(sizeof(double) * 2 * kMaxQuad);
     if (c.off > kNoallocScratchBytes) return LS_ERR_UNSUPPORTED;
 
-    Workspace ws;
+    Workspace ws = {};
     ws.counter = reinterpret_cast<unsigned int *>(base + o_counter);
     ws.status = reinterpret_cast<int *>(base + o_counter + 64);
     ws.stats = reinterpret_cast<Stats *>(base + o_stats);
