@@ -774,7 +774,7 @@ template <typename T>
 struct PassAArgs {
     Geometry g;
     Batch bt;
-    int shared;            // 1: series share t and dy, so s2 and s3 are transformed once
+    int shared;            // 1: the common s2 and s3 transforms of a shared-times batch
     int nofit;             // 1: the model has no offset; s2 is not needed
     PointSet<T> px, p2;
     const int *binstart;   // 2 * (nbins + 1)
@@ -878,8 +878,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
     // Instance -> (series, transform 0: s1, 1: s2, 2: s3) and its slot of H.
-    // Independent series: 3 per series.  Shared t and dy: slots 0, 1 hold s2, s3
-    // of series 0, slot 2 + s the s1 of series s.
+    // Independent series: 3 per series.  Shared t and dy (the common transforms
+    // of launch_shared_pipeline, instances 0 and 1): slots 0, 1 hold s2 and s3
+    // of the common records.
     int ser, grid, slot;
     if (A.shared) {
         slot = y;
@@ -1164,10 +1165,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
 }
 
 
-// Pass A for many small grids of one batch launch: a block takes column block
-// blk of `group` instances at a time (instances: the transforms of the series;
-// in a shared-times batch only the series grids, the common grids go through
-// the usual kernel first), their columns side by side in shared memory
+// Pass A for many small grids of one batch launch of independent series: a
+// block takes column block blk of `group` instances at a time (instances: the
+// transforms of the series), their columns side by side in shared memory
 // (member r owns columns r BA .. r BA + BA - 1), so the tables, the
 // transforms' barriers and the stores are shared by the group.  No cluster
 // pairs (small grids only).
