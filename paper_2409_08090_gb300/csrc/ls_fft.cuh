@@ -312,6 +312,46 @@ __device__ __forceinline__ V root_tw(const V *roots, int p)
     return cmul(roots[p & 63], roots[64 + (p >> 6)]);
 }
 
+// The twiddles W_L^(k step), k = 1 .. R-1, of one butterfly.  FP32: from two
+// table lookups, W^step and W^(4 step): with k = 4a + b, W^(k step) is
+// W^(4a step) W^(b step), and each factor is a power of its looked-up root
+// formed by at most two products, so every twiddle is within a few rounded
+// products of the table; fifteen lookups of the table's two levels per
+// radix-16 butterfly become two, with as many complex products as before.
+// Double-float: one lookup per twiddle (the six double-float powers held at
+// once cost the 80-register kernels spills).
+template <int R, typename V>
+struct Twiddles {
+    static constexpr bool kPow = sizeof(V) == 8;
+    static constexpr int kA = (R - 1) / 4;   // largest a
+    V wb[4];                                 // W^(b step), b = 1 .. 3
+    V wa[kA + 1];                            // W^(4 a step), a = 1 .. kA
+    const V *roots;
+    int step;
+    __device__ __forceinline__ Twiddles(const V *roots_, int step_) : roots(roots_), step(step_)
+    {
+        if constexpr (kPow) {
+            wb[1] = root_tw(roots, step);
+            if constexpr (R > 2) wb[2] = cmul(wb[1], wb[1]);
+            if constexpr (R > 3) wb[3] = cmul(wb[2], wb[1]);
+            if constexpr (kA >= 1) wa[1] = root_tw(roots, 4 * step);
+            if constexpr (kA >= 2) wa[2] = cmul(wa[1], wa[1]);
+            if constexpr (kA >= 3) wa[3] = cmul(wa[2], wa[1]);
+            if constexpr (kA >= 4) wa[4] = cmul(wa[2], wa[2]);
+            static_assert(kA <= 4, "radix above 20");
+        }
+    }
+    // k is a constant after unrolling
+    __device__ __forceinline__ V get(int k) const
+    {
+        if constexpr (!kPow) return root_tw(roots, k * step);
+        const int a = k >> 2, b = k & 3;
+        if (a == 0) return wb[b];
+        if (b == 0) return wa[a];
+        return cmul(wa[a], wb[b]);
+    }
+};
+
 // Load the two-level root table of length L into shared memory in the
 // transform's type (no barrier).
 template <typename W, typename V>
@@ -386,10 +426,10 @@ __device__ __forceinline__ void dif_butterfly(V *buf, int colstride, const FftSt
 #pragma unroll
     for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
     if (j != 0) {
-        const int step = j * tmul;             // W_Ls^(j k) = W_L^(k step)
+        const Twiddles<R, V> tw(roots, j * tmul);   // W_Ls^(j k) = W_L^(k j tmul)
 #pragma unroll
         for (int k = 1; k < R; ++k) {
-            const V w = root_tw(roots, k * step);
+            const V w = tw.get(k);
 #pragma unroll
             for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
         }
@@ -477,10 +517,10 @@ __device__ __forceinline__ void dif_stage_first_fixed(float2 *buf, int colstride
 #pragma unroll
         for (int c = 0; c < NC; ++c) Dft<R>::run(v[c]);
         if (j != 0) {
-            const int step = j * tmul;
+            const Twiddles<R, float2> tw(roots, j * tmul);
 #pragma unroll
             for (int k = 1; k < R; ++k) {
-                const float2 w = root_tw(roots, k * step);
+                const float2 w = tw.get(k);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) v[c][k] = cmul(v[c][k], w);
             }
