@@ -2061,6 +2061,61 @@ __device__ __forceinline__ double ls_power_ff(float Ch, float Sh, float C, float
     return power_data_ff(power_m_ff(C, S, C2, S2, lam_tol), Ch, Sh, YY, YYd, lam_tol);
 }
 
+// FP64 path at tolerances of 1e-11 and above: the transforms deliver
+// double-float values, and the deconvolution and the ratio stay in double-float
+// on the FP32 units (rounding about 2^-46 of the terms' magnitudes, far below
+// the sums' own error of eps); the same ratio in FP64 took 40% of pass B on a
+// part whose FP64 rate is 1/64 of its FP32 rate (1.9e7-cell grid: 1.04 of
+// 2.65 ms).  A nearly singular M takes the FP64 rotation form.
+__device__ __noinline__ ff double_to_ff_fp64(double x)
+{
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+// A double as a double-float on the integer pipe: hi takes the top 24 bits of
+// the significand, lo the remaining 29 bits rounded to 24 (relative error
+// below 2^-48), then renormalised.  Exponents within 2^+-70 of 1 (the
+// deconvolution factors); others take the FP64 conversions out of line.
+__device__ __forceinline__ ff double_to_ff(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 70 || e > 1023 + 70) return double_to_ff_fp64(x);
+    const unsigned sgn = (unsigned)(b >> 63) << 31;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(sgn | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+    float lo = __uint2float_rn((unsigned)(m & 0x1FFFFFFFull)) *
+               __uint_as_float((unsigned)(e - 1023 - 52 + 127) << 23);
+    if (sgn) lo = -lo;
+    return fast_two_sum(hi, lo);
+}
+__device__ __noinline__ double power_dfl_singular(ff Ch, ff Sh, ff C, ff S, ff C2, ff S2, double YY,
+                                                  double lam_tol)
+{
+    return ls_power_fp64(ff_to_double(Ch), ff_to_double(Sh), ff_to_double(C), ff_to_double(S),
+                         ff_to_double(C2), ff_to_double(S2), YY, lam_tol);
+}
+__device__ __forceinline__ ff ff_half(ff x) { return {0.5f * x.hi, 0.5f * x.lo}; }   // exact
+__device__ __forceinline__ double ls_power_dfl(dfl2 a1, dfl2 a2, dfl2 a3, double dc, ff YY,
+                                               double YYd, float lam_tol, double lam_told)
+{
+    const ff d = double_to_ff(dc);
+    const ff Ch = ff_mul(ff{a1.x.hi, a1.x.lo}, d), Sh = ff_mul(ff{a1.y.hi, a1.y.lo}, d);
+    const ff C = ff_mul(ff{a2.x.hi, a2.x.lo}, d), S = ff_mul(ff{a2.y.hi, a2.y.lo}, d);
+    const ff C2 = ff_mul(ff{a3.x.hi, a3.x.lo}, d), S2 = ff_mul(ff{a3.y.hi, a3.y.lo}, d);
+    const ff hc2 = ff_half(C2);
+    const ff CC = ff_add(ff_add(ff{0.5f, 0.f}, hc2), ff_neg(ff_mul(C, C)));
+    const ff SS = ff_add(ff_add(ff{0.5f, 0.f}, ff_neg(hc2)), ff_neg(ff_mul(S, S)));
+    const ff CS = ff_add(ff_half(S2), ff_neg(ff_mul(C, S)));
+    const ff D = ff_add(ff_mul(CC, SS), ff_neg(ff_mul(CS, CS)));
+    if (!(D.hi > lam_tol * (CC.hi + SS.hi) && CC.hi > 0.f && SS.hi > 0.f))
+        return power_dfl_singular(Ch, Sh, C, S, C2, S2, YYd, lam_told);
+    const ff ChSh = ff_mul(Ch, Sh);
+    const ff N = ff_add(ff_add(ff_mul(ff_mul(Ch, Ch), SS), ff_mul(ff_mul(Sh, Sh), CC)),
+                        ff_neg(ff_mul(ff{2.f * ChSh.hi, 2.f * ChSh.lo}, CS)));
+    return ff_to_double(ff_div(N, ff_mul(D, YY)));
+}
+
 // ---------------------------------------------------------------------------
 // Pass B: for row d, FFT the three grids over a (length N1), deconvolve the
 // needed modes and evaluate the power.
@@ -2158,6 +2213,30 @@ template <> struct PowerOut<float> {
     }
 };
 
+// The power of one mode from its transform values a1, a2, a3 (a2 null without
+// a fitted mean: C = S = 0) and its deconvolution factor: FP32 grids through
+// PowerOut; FP64 grids in double-float where the tolerance allows (dfl_power)
+// and through PowerOut in FP64 below it.  Every pass-B kernel of independent
+// series evaluates a mode through this, so a series has the same bits alone
+// and in a batch.
+template <typename T>
+__device__ __forceinline__ double mode_power(const typename FftOf<T>::type &a1,
+                                             const typename FftOf<T>::type *a2,
+                                             const typename FftOf<T>::type &a3, T dc, double YY,
+                                             ff YYf, double lam_tol, bool dfl_power)
+{
+    using V = Cplx<T>;
+    if constexpr (sizeof(T) == 8) {
+        if (dfl_power) {
+            const dfl2 z = {dfl(0.f, 0.f), dfl(0.f, 0.f)};
+            return ls_power_dfl(a1, a2 ? *a2 : z, a3, dc, YYf, YY, (float)lam_tol, lam_tol);
+        }
+    }
+    const V g1 = from_fft(a1), g3 = from_fft(a3);
+    const V g2 = a2 ? from_fft(*a2) : mk2(T(0), T(0));
+    return PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, (T)lam_tol);
+}
+
 // kStage is PassBArgs::stage as a template parameter: each launch carries only
 // its own code (fewer instruction-fetch stalls than one kernel for all stages).
 // kThr: threads per block; above kThreadsB the row transforms deal their
@@ -2238,7 +2317,7 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
         else fft_dif<1>(buf, 3, Lp, g.fb, roots);
     }
 
-    const T lam_tol_t = (T)B.lam_tol;
+    const bool dfl_power = g.eps >= 1e-11;   // FP64 path: the ratio in double-float
     ff YYf;
     YYf.hi = stat->yy_hi;
     YYf.lo = stat->yy_lo;
@@ -2268,14 +2347,15 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
             const int64_t kp = (c < c1) ? k : k - n;
             const int sp = pad16(pos);
             const T dc = dcv[r];
-            const V g1 = from_fft(buf[sp]), g3 = from_fft(buf[2 * Lp + sp]);
-            const V g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[Lp + sp]);
             const int64_t out = kp + K0;
             if (power) {
-                const double P = PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, lam_tol_t);
+                const double P = mode_power<T>(buf[sp], B.nofit ? nullptr : &buf[Lp + sp],
+                                               buf[2 * Lp + sp], dc, YY, YYf, B.lam_tol, dfl_power);
                 power[out] = ls_normalise<T>(P, B.norm, psd_factor);
             }
             if (sums) {
+                const V g1 = from_fft(buf[sp]), g3 = from_fft(buf[2 * Lp + sp]);
+                const V g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[Lp + sp]);
                 // Ch, Sh were formed from scale * (y - ybar): report them unscaled.
                 double *o = sums + 6 * out;
                 o[0] = (double)(g1.x * dc) * unscale; o[1] = (double)(g1.y * dc) * unscale;
@@ -2414,7 +2494,7 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
     const int64_t n = g.n;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
-    const T lam_tol_t = (T)B.lam_tol;
+    const bool dfl_power = g.eps >= 1e-11;   // FP64 path: the ratio in double-float
     const T *dcrow = B.deconv + (size_t)d * N1;
 
     for (int s0 = blockIdx.y * G; s0 < B.nser; s0 += gridDim.y * G) {
@@ -2458,13 +2538,12 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
             const int sp = pad16(pos);
             const T dc = __ldg(dcrow + pos);
             const size_t base = (size_t)nr * r * Lp + sp;
-            const V g1 = from_fft(buf[base]);
-            const V g2 = B.nofit ? mk2(T(0), T(0)) : from_fft(buf[base + Lp]);
-            const V g3 = from_fft(buf[base + (size_t)(nr - 1) * Lp]);
             ff YYf;
             YYf.hi = (float)sc[4 * r + 2];
             YYf.lo = (float)sc[4 * r + 3];
-            const double P = PowerOut<T>::eval(g1, g2, g3, dc, sc[4 * r], YYf, lam_tol_t);
+            const double P = mode_power<T>(buf[base], B.nofit ? nullptr : &buf[base + Lp],
+                                           buf[base + (size_t)(nr - 1) * Lp], dc, sc[4 * r], YYf,
+                                           B.lam_tol, dfl_power);
             B.power[obase[r] + kp] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
         }
     }
