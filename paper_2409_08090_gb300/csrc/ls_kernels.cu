@@ -2213,6 +2213,17 @@ template <> struct PowerOut<float> {
     }
 };
 
+// The eigenvalue tolerance of M in the types the power evaluations take,
+// converted once per block (an FP64 conversion per mode would run on the slow
+// FP64 pipe).
+template <typename T>
+struct LamTol {
+    double d;
+    T t;
+    float f;
+    __device__ __forceinline__ explicit LamTol(double x) : d(x), t((T)x), f((float)x) {}
+};
+
 // The power of one mode from its transform values a1, a2, a3 (a2 null without
 // a fitted mean: C = S = 0) and its deconvolution factor: FP32 grids through
 // PowerOut; FP64 grids in double-float where the tolerance allows (dfl_power)
@@ -2223,18 +2234,18 @@ template <typename T>
 __device__ __forceinline__ double mode_power(const typename FftOf<T>::type &a1,
                                              const typename FftOf<T>::type *a2,
                                              const typename FftOf<T>::type &a3, T dc, double YY,
-                                             ff YYf, double lam_tol, bool dfl_power)
+                                             ff YYf, const LamTol<T> &lt, bool dfl_power)
 {
     using V = Cplx<T>;
     if constexpr (sizeof(T) == 8) {
         if (dfl_power) {
             const dfl2 z = {dfl(0.f, 0.f), dfl(0.f, 0.f)};
-            return ls_power_dfl(a1, a2 ? *a2 : z, a3, dc, YYf, YY, (float)lam_tol, lam_tol);
+            return ls_power_dfl(a1, a2 ? *a2 : z, a3, dc, YYf, YY, lt.f, lt.d);
         }
     }
     const V g1 = from_fft(a1), g3 = from_fft(a3);
     const V g2 = a2 ? from_fft(*a2) : mk2(T(0), T(0));
-    return PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, (T)lam_tol);
+    return PowerOut<T>::eval(g1, g2, g3, dc, YY, YYf, lt.t);
 }
 
 // kStage is PassBArgs::stage as a template parameter: each launch carries only
@@ -2318,6 +2329,7 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
     }
 
     const bool dfl_power = g.eps >= 1e-11;   // FP64 path: the ratio in double-float
+    const LamTol<T> lt(B.lam_tol);
     ff YYf;
     YYf.hi = stat->yy_hi;
     YYf.lo = stat->yy_lo;
@@ -2350,7 +2362,7 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
             const int64_t out = kp + K0;
             if (power) {
                 const double P = mode_power<T>(buf[sp], B.nofit ? nullptr : &buf[Lp + sp],
-                                               buf[2 * Lp + sp], dc, YY, YYf, B.lam_tol, dfl_power);
+                                               buf[2 * Lp + sp], dc, YY, YYf, lt, dfl_power);
                 power[out] = ls_normalise<T>(P, B.norm, psd_factor);
             }
             if (sums) {
@@ -2421,8 +2433,10 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
             const double YY = stat->YY;
             sc[4 * r] = YY;
             sc[4 * r + 1] = stat->psd;
-            sc[4 * r + 2] = stat->yy_hi;
-            sc[4 * r + 3] = stat->yy_lo;
+            // the YY pair's float bits (read per mode without FP64 conversions)
+            float *yyp = reinterpret_cast<float *>(sc + 4 * r + 2);
+            yyp[0] = stat->yy_hi;
+            yyp[1] = stat->yy_lo;
             soff[r] = series_of(B.bt, s0 + r).out_off;
         }
         cp_async_wait_all();
@@ -2443,18 +2457,16 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
                 const PowerM m = power_m_ff(g2.x, g2.y, g3.x, g3.y, lam_tol_t);
                 for (int r = 0; r < gact; ++r) {
                     const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
-                    ff YYf;
-                    YYf.hi = (float)sc[4 * r + 2];
-                    YYf.lo = (float)sc[4 * r + 3];
+                    const float2 yyp = *reinterpret_cast<const float2 *>(sc + 4 * r + 2);
+                    const ff YYf = {yyp.x, yyp.y};
                     const double P = power_data_ff(m, g1.x, g1.y, YYf, sc[4 * r], lam_tol_t);
                     B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
                 }
             } else {
                 for (int r = 0; r < gact; ++r) {
                     const V g1 = cscale(from_fft(buf[(size_t)(2 + r) * Lp + sp]), dc);
-                    ff YYf;
-                    YYf.hi = (float)sc[4 * r + 2];
-                    YYf.lo = (float)sc[4 * r + 3];
+                    const float2 yyp = *reinterpret_cast<const float2 *>(sc + 4 * r + 2);
+                    const ff YYf = {yyp.x, yyp.y};
                     const double P = PowerOut<T>::eval(g1, g2, g3, T(1), sc[4 * r], YYf, lam_tol_t);
                     B.power[soff[r] + out] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
                 }
@@ -2495,6 +2507,7 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
     const bool dfl_power = g.eps >= 1e-11;   // FP64 path: the ratio in double-float
+    const LamTol<T> lt(B.lam_tol);
     const T *dcrow = B.deconv + (size_t)d * N1;
 
     for (int s0 = blockIdx.y * G; s0 < B.nser; s0 += gridDim.y * G) {
@@ -2516,8 +2529,10 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
             const double YY = stat->YY;
             sc[4 * r] = YY;
             sc[4 * r + 1] = stat->psd;
-            sc[4 * r + 2] = stat->yy_hi;
-            sc[4 * r + 3] = stat->yy_lo;
+            // the YY pair's float bits (read per mode without FP64 conversions)
+            float *yyp = reinterpret_cast<float *>(sc + 4 * r + 2);
+            yyp[0] = stat->yy_hi;
+            yyp[1] = stat->yy_lo;
             const int64_t nf = sd.nf, K0 = sd.ph.K0;
             cr[2 * r] = (nf - K0 > d) ? (int)((nf - K0 - d + N2 - 1) / N2) : 0;
             cr[2 * r + 1] = (int)((n - K0 - d + N2 - 1) / N2);
@@ -2538,12 +2553,11 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
             const int sp = pad16(pos);
             const T dc = __ldg(dcrow + pos);
             const size_t base = (size_t)nr * r * Lp + sp;
-            ff YYf;
-            YYf.hi = (float)sc[4 * r + 2];
-            YYf.lo = (float)sc[4 * r + 3];
+            const float2 yyp = *reinterpret_cast<const float2 *>(sc + 4 * r + 2);
+            const ff YYf = {yyp.x, yyp.y};
             const double P = mode_power<T>(buf[base], B.nofit ? nullptr : &buf[base + Lp],
                                            buf[base + (size_t)(nr - 1) * Lp], dc, sc[4 * r], YYf,
-                                           B.lam_tol, dfl_power);
+                                           lt, dfl_power);
             B.power[obase[r] + kp] = ls_normalise<T>(P, B.norm, sc[4 * r + 1]);
         }
     }
