@@ -2267,6 +2267,9 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
     int *dtab = reinterpret_cast<int *>(roots + 64 + ((N1 + 63) >> 6));
     const int d = blockIdx.x;
     constexpr int stage = kStage;
+    // radix-16 stages one transform at a time in the 80-register (three blocks
+    // per SM) form: two at a time held 64 values and spilled
+    constexpr int kNC16B = kMinB >= 3 ? 1 : 2;
     load_roots(roots, B.twB, N1);
     fill_slot_table(dtab, g.fb);
     static_assert(stage == 0 || stage == 1, "stage 2 runs in k_passB_series");
@@ -2302,7 +2305,7 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
 
     if constexpr (stage == 1) {             // rows 1 and 2 (row 2 alone without a fitted mean)
         if (B.nofit) fft_dif<1>(buf + 2 * (size_t)Lp, 1, Lp, g.fb, roots);
-        else if (sizeof(T) == 4) fft_dif<2>(buf + Lp, 2, Lp, g.fb, roots);
+        else if (sizeof(T) == 4) fft_dif<2, kNC16B>(buf + Lp, 2, Lp, g.fb, roots);
         else fft_dif<1>(buf + Lp, 2, Lp, g.fb, roots);
         // write both rows back deconvolved, in slot order, over the same row d of
         // H slots 0 and 1 (this block read that row; no other block touches it)
@@ -2321,10 +2324,10 @@ __global__ void __launch_bounds__(kThr, kMinB) k_passB(PassBArgs<T> B)
         if (B.nofit) fft_dif_dealt(buf, 2, 2 * Lp, g.fb, roots);   // rows 0 and 2
         else fft_dif_dealt(buf, 3, Lp, g.fb, roots);
     } else if (B.nofit) {                   // rows 0 and 2
-        if (sizeof(T) == 4) fft_dif<2>(buf, 2, 2 * Lp, g.fb, roots);
+        if (sizeof(T) == 4) fft_dif<2, kNC16B>(buf, 2, 2 * Lp, g.fb, roots);
         else fft_dif<1>(buf, 2, 2 * Lp, g.fb, roots);
     } else {
-        if (sizeof(T) == 4) fft_dif<3>(buf, 3, Lp, g.fb, roots);
+        if (sizeof(T) == 4) fft_dif<3, kNC16B>(buf, 3, Lp, g.fb, roots);
         else fft_dif<1>(buf, 3, Lp, g.fb, roots);
     }
 
@@ -2441,7 +2444,7 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_series(P
         }
         cp_async_wait_all();
         __syncthreads();
-        if (sizeof(T) == 4) fft_dif<2>(buf + 2 * (size_t)Lp, gact, Lp, g.fb, roots);
+        if (sizeof(T) == 4) fft_dif<2, 1>(buf + 2 * (size_t)Lp, gact, Lp, g.fb, roots);
         else fft_dif<1>(buf + 2 * (size_t)Lp, gact, Lp, g.fb, roots);
 
         for (int pos = threadIdx.x; pos < N1; pos += blockDim.x) {
@@ -2540,7 +2543,7 @@ __global__ void __launch_bounds__(kThreadsB, kGroupBlocksPerSM) k_passB_group(Pa
         }
         cp_async_wait_all();
         __syncthreads();
-        if (sizeof(T) == 4) fft_dif<2>(buf, gact * nr, Lp, g.fb, roots);
+        if (sizeof(T) == 4) fft_dif<2, 1>(buf, gact * nr, Lp, g.fb, roots);
         else fft_dif<1>(buf, gact * nr, Lp, g.fb, roots);
 
         for (int e = threadIdx.x; e < gact * N1; e += blockDim.x) {
