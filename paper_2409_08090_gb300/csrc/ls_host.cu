@@ -194,7 +194,7 @@ bool passA_column_fits(int64_t N2, int prec)
     const size_t cx = prec == LS_FP32 ? 8 : 16;
     const size_t nhi = (size_t)(N2 + 63) / 64;
     const size_t padded = (size_t)N2 + (size_t)N2 / 16 + 1;   // pad16 layout of the column
-    const size_t bytes = cx * (padded + 2 * (64 + nhi)) +
+    const size_t bytes = cx * (padded + 2 * (kAloStride + ahi_stride((int)nhi))) +
                          sizeof(int) * (size_t)(N2 / last) + (size_t)N2 + 2048;   // + row exponents
     return bytes <= kSmemOptinBytes;
 }
@@ -869,7 +869,7 @@ void choose_tiling(int prec, int n1, int n2, int cols_req, int maxr_req, int *ba
         if (!radix_schedule(n2, rad, *maxrA)) return (size_t)-1;
         const size_t nhi = (size_t)(n2 + 63) / 64;
         const size_t padded = (size_t)n2 + n2 / 16 + 1;
-        return cx * ((size_t)ba * padded + (size_t)ba * (64 + nhi) + 64 + nhi) +
+        return cx * ((size_t)ba * padded + (size_t)ba * (kAloStride + ahi_stride((int)nhi)) + 64 + nhi) +
                sizeof(int) * (size_t)(n2 / rad.back()) + (size_t)n2 + 1024;
     };
     // radix-8 stages need a larger slot table: keep 16 where it would not fit

@@ -26,6 +26,13 @@ constexpr int kThreadsB = 256;
 // Pass-B blocks of the FP32 path where shared memory holds two blocks per SM:
 // 12 warps each (the row transforms deal their butterflies to all of them).
 constexpr int kThreadsBWide = 384;
+// Column strides of pass A's per-column four-step twiddle tables (low part: 64
+// entries, high part: nhi): padded so that a warp of the cluster store, whose
+// lanes read columns 0 .. 3 of the cluster at one or two entries each, spreads
+// the columns over the banks (a stride of 4 mod 8 entries of 8 bytes puts
+// neighbouring columns 8 banks apart) instead of stacking them in one bank.
+constexpr int kAloStride = 68;
+__host__ __device__ constexpr int ahi_stride(int nhi) { return nhi + ((4 - nhi) & 7); }
 constexpr int kMinN1 = 32;        // keeps every kernel footprint (w <= 16) within two columns
 
 // Device status word bits (sticky until ls_sync).

@@ -873,8 +873,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
     V *buf = reinterpret_cast<V *>(smem_raw);   // BA columns, padded layout
     F *bufF = reinterpret_cast<F *>(buf);       // the same columns once spread
     F *alo = bufF + (size_t)BA * Lp;            // W_n^{a dl}, dl < 64, per column
-    F *ahi = alo + tc * 64;                     // W_n^{64 a dh}, per column
-    F *roots = ahi + tc * nhi;                  // two-level root table of length N2
+    const int nhiP = ahi_stride(nhi);
+    F *ahi = alo + tc * kAloStride;             // W_n^{64 a dh}, per column
+    F *roots = ahi + tc * nhiP;                 // two-level root table of length N2
     int *dtab = reinterpret_cast<int *>(roots + 64 + nhi);   // slot -> frequency table
 
     // Instance -> (series, transform 0: s1, 1: s2, 2: s3) and its slot of H.
@@ -933,12 +934,14 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         fill_slot_table(dtab, g.fa);
         for (int i = threadIdx.x; i < tc * 64; i += blockDim.x) {
             const int col = i >> 6;
-            alo[i] = to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
+            alo[col * kAloStride + (i & 63)] =
+                to_fft(tw4_root(A.tw4, (int64_t)(a_base + col) * (i & 63)));
         }
         for (int i = threadIdx.x; i < tc * nhi; i += blockDim.x) {
             const int col = i / nhi;
             const int dh = i - col * nhi;
-            ahi[i] = to_fft(tw4_root(A.tw4, mod_u32((int64_t)(a_base + col) * 64 * dh, g.n)));
+            ahi[col * nhiP + dh] =
+                to_fft(tw4_root(A.tw4, mod_u32((int64_t)(a_base + col) * 64 * dh, g.n)));
         }
     }
     __syncthreads();
@@ -1111,9 +1114,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
                         dd[r] = slot_freq_tab(pos, dtab, g.fa);
                         const int sp = pad16(pos);
                         const int dl = dd[r] & 63, dh = dd[r] >> 6;
-                        va[r] = cmul(pa[sp], cmul(alo[c0 * 64 + dl], ahi[c0 * nhi + dh]));
+                        va[r] = cmul(pa[sp], cmul(alo[c0 * kAloStride + dl], ahi[c0 * nhiP + dh]));
                         if constexpr (sizeof(V) == 8)
-                            vb[r] = cmul(pb[sp], cmul(alo[c1 * 64 + dl], ahi[c1 * nhi + dh]));
+                            vb[r] = cmul(pb[sp], cmul(alo[c1 * kAloStride + dl], ahi[c1 * nhiP + dh]));
                     }
                 }
 #pragma unroll
@@ -1143,8 +1146,9 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
                 const int sp = pad16(pos);
                 float4 *dst = reinterpret_cast<float4 *>(H + (size_t)d * N1);
                 for (int c0 = 0; c0 < BA; c0 += 2) {
-                    const F t0 = cmul(alo[c0 * 64 + (d & 63)], ahi[c0 * nhi + (d >> 6)]);
-                    const F t1 = cmul(alo[(c0 + 1) * 64 + (d & 63)], ahi[(c0 + 1) * nhi + (d >> 6)]);
+                    const F t0 = cmul(alo[c0 * kAloStride + (d & 63)], ahi[c0 * nhiP + (d >> 6)]);
+                    const F t1 = cmul(alo[(c0 + 1) * kAloStride + (d & 63)],
+                                      ahi[(c0 + 1) * nhiP + (d >> 6)]);
                     const F v0 = cmul(bufF[(size_t)c0 * Lp + sp], t0);
                     const F v1 = cmul(bufF[(size_t)(c0 + 1) * Lp + sp], t1);
                     dst[c0 >> 1] = make_float4(v0.x, v0.y, v1.x, v1.y);
@@ -1158,7 +1162,7 @@ __device__ __forceinline__ void passA_instance(const PassAArgs<T> &A, const int 
         const int sp = pad16(pos);
         F *dst = H + (size_t)d * N1;
         for (int col = 0; col < BA; ++col) {
-            const F tw = cmul(alo[col * 64 + (d & 63)], ahi[col * nhi + (d >> 6)]);
+            const F tw = cmul(alo[col * kAloStride + (d & 63)], ahi[col * nhiP + (d >> 6)]);
             dst[col] = cmul(bufF[(size_t)col * Lp + sp], tw);
         }
     }
@@ -2622,7 +2626,8 @@ static int blocks_per_sm(size_t smem)
 size_t passA_smem_bytes(const Geometry &g, size_t cx, int cs)
 {
     const size_t nhi = (size_t)(g.N2 + 63) / 64;
-    return cx * ((size_t)g.BA * padded_len(g.N2) + (size_t)cs * g.BA * (64 + nhi) + 64 + nhi) +
+    return cx * ((size_t)g.BA * padded_len(g.N2) +
+                 (size_t)cs * g.BA * (kAloStride + ahi_stride((int)nhi)) + 64 + nhi) +
            sizeof(int) * (size_t)(g.N2 / g.fa.Rlast) + (size_t)g.N2;
 }
 
