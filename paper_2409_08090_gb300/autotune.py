@@ -90,7 +90,7 @@ def _measure_on_device(nf: int, eps: float, precision: str, nd: int, device: int
                        reps: int):
     """Returns measure(cfg) -> median ms of one ls_execute on a synthetic series
     of the request's shape (coordinates covering a fifth of the period, like a
-    survey baseline at the default frequency spacing) with the plan options
+    long observing span at the default frequency spacing) with the plan options
     in cfg."""
     import numpy as np
     import torch
